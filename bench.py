@@ -1,0 +1,323 @@
+"""Benchmark of the Hubbard exact-diagonalization hot path on one GB300.
+
+Workload: the 4x4 periodic square lattice (32 bonds), N_up = N_dn = 8
+(D = 12870^2 = 1.656e8), t = 1, U = 8, binary64 vectors, seeded
+uniform[-1, 1) start vector (SplitMix64, seed 1234).
+
+One timed step is one H*v (hubbard_apply) on inputs resident in HBM; the
+vectors (1.3 GB each) are larger than L2, so no flush is needed between
+steps.  value = algorithmic bytes / time, with algorithmic bytes per H*v =
+2*D*8 (read v, write w) + the per-spin tables.  The same run also times full
+ground-state solves (create + Lanczos to rho < 1e-10 + destroy) and reports
+solves/s and p50/p99 latency, each solve checked against the stored oracle
+energy (1e-9 relative).
+
+    python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain-C Kronecker-sum H*v) on the
+host cores for the same metric on a bounded sample.  With N > 1 (torchrun)
+every rank runs an independent replica (the path does not shard).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "H·v GB/s vs HBM peak; ground-state solves/s, p50/p99 at ≤1e-9 rel"
+WORKLOAD = dict(workload="sq4x4_n8_8_U8_f64", lattice="4x4 periodic square (32 bonds)", nup=8, ndn=8,
+                t=1.0, U=8.0, dim=12870 * 12870, vector_bytes=12870 * 12870 * 8, seed=1234,
+                l2_policy="inputs larger than L2 (1.3 GB vectors vs 129 MB L2); no flush")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "sq4x4_n8_8_U8.json")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def hv_bytes(D, tables_bytes, s=8):
+    """Algorithmic bytes of one H*v: read v, write w, read the tables once."""
+    return 2 * D * s + tables_bytes
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"], samples=0)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        return dict(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+
+    import paper_1204_3425_gb300 as hub
+    from paper_1204_3425_gb300 import build as hbuild
+    from workload import square, start_vector
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    hbuild.build()
+    hub.load_library()
+    stream = torch.cuda.current_stream()
+
+    bonds = square(4, 4)
+    H = hub.hubbard_sector_create(16, bonds, 8, 8, 1.0, 8.0)
+    D = H.D
+    tables = sum(int(hub.load_library().hubbard_table_nnz(H.handle, s)) * 4 + (H.Dup if s == 0 else H.Ddn) * 12
+                 for s in (0, 1))
+    nbytes = hv_bytes(D, tables)
+    v_host = torch.from_numpy(start_vector(D, seed=1234))
+    v_host /= v_host.norm()
+    v_pin = v_host.pin_memory()
+    v = v_pin.to(dev, non_blocking=True)
+    w = torch.empty_like(v)
+    torch.cuda.synchronize()
+
+    # ---- H*v steps (inputs resident) -------------------------------------
+    for _ in range(args.warmup):
+        hub.hubbard_apply(H, v, w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = hub.hubbard_kernel_launches()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for i in range(args.steps):
+        ev[i][0].record(stream)
+        hub.hubbard_apply(H, v, w)
+        ev[i][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    launches = hub.hubbard_kernel_launches() - launches0
+    total_ms = t_start.elapsed_time(t_end)
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    per = [a.elapsed_time(b) for a, b in ev]
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms = total_ms / args.steps
+    value = ws * nbytes * args.steps / (total_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers -------------------
+    w_pin = torch.empty(D, dtype=torch.float64).pin_memory()
+    e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    k_e2e = max(2, min(args.steps, 5))
+    hub.hubbard_apply(H, v_pin.to(dev, non_blocking=True), w)
+    torch.cuda.synchronize()
+    e2e_ev[0].record(stream)
+    for _ in range(k_e2e):
+        vd = v_pin.to(dev, non_blocking=True)
+        hub.hubbard_apply(H, vd, w)
+        w_pin.copy_(w, non_blocking=True)
+    e2e_ev[1].record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e2e_ev[0].elapsed_time(e2e_ev[1]) / k_e2e
+    e2e_val = ws * nbytes / (e2e_ms * 1e-3) / 1e9
+
+    # ---- ground-state solves ----------------------------------------------
+    golden = json.load(open(GOLDEN))["e0"]
+    n_solves = args.solves
+    lat, iters, errs = [], [], []
+    ws_buf = torch.empty(hub.lanczos_workspace_bytes(H, hub.HUB_F64), dtype=torch.uint8, device=dev)
+    v0 = torch.from_numpy(start_vector(D, seed=1234)).to(dev)
+    for k in range(n_solves + 1 if n_solves > 0 else 0):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Hs = hub.hubbard_sector_create(16, bonds, 8, 8, 1.0, 8.0)
+        r = hub.lanczos_ground_state(Hs, v0, 600, 1e-10, workspace=ws_buf)
+        Hs.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if k == 0:
+            continue                     # warm-up solve
+        lat.append(dt)
+        iters.append(r["iters"])
+        errs.append(abs(r["energy"] - golden) / abs(golden))
+    ok = [e <= 1e-9 for e in errs]
+    solve = dict(solves=n_solves, solves_per_s=sum(ok) / sum(lat) if lat else None,
+                 p50_ms=1e3 * float(np.percentile(lat, 50)) if lat else None,
+                 p99_ms=1e3 * float(np.percentile(lat, 99)) if lat else None,
+                 iters=iters, max_rel_err=max(errs) if errs else None, all_within_1e9=all(ok),
+                 tol="rho < 1e-10", includes="hubbard_sector_create + lanczos_ground_state + destroy")
+
+    peak, src = peaks()
+    avg_kernel_ms = float(np.mean(per))
+    achieved = nbytes / (avg_kernel_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "arith": "int32-pair fixed-point hop sums, binary64 storage and epilogue",
+        "data": "synthetic (seeded SplitMix64 start vector)",
+        "config": dict(WORKLOAD, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single"),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "peak_source": src,
+                     "algorithmic_bytes_per_launch": nbytes,
+                     "kernel": "hubbard_apply (k_max_exponent + k_to_fixed + k_hv_fixed)"},
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * 8, "d2h_bytes_per_step": D * 8,
+                "ms_per_step": e2e_ms},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "solve": solve,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    H.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def cpu_baseline(budget_s=15.0):
+    """The oracle's plain-C Kronecker H*v on this host's cores, bounded sample."""
+    from oracle.kron import KronHamiltonian
+    from workload import square, start_vector
+    t0 = time.perf_counter()
+    K = KronHamiltonian(16, square(4, 4), 8, 8, 1.0, 8.0)
+    build_s = time.perf_counter() - t0
+    x = start_vector(K.D, seed=1234)
+    y = np.zeros(K.D)
+    tables = sum(len(tg) * 4 + len(st) * 12 for (st, rp, tg, _) in K.tables)
+    nbytes = hv_bytes(K.D, tables)
+    K.hv_acc(x, y)                                   # warm-up
+    times = []
+    t_begin = time.perf_counter()
+    while time.perf_counter() - t_begin < budget_s or len(times) < 2:
+        t1 = time.perf_counter()
+        K.hv_acc(x, y)
+        times.append(time.perf_counter() - t1)
+    per = float(np.median(times))
+    return {"value": nbytes / per / 1e9, "unit": "GB/s", "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"{len(times)} Kronecker-sum H*v calls on the 4x4 (8,8) sector (plain C, OpenMP), "
+                      f"median {per:.3f} s each; table build {build_s:.1f} s not timed"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle.kron import KronHamiltonian
+    from workload import square, start_vector
+    K = KronHamiltonian(16, square(4, 4), 8, 8, 1.0, 8.0)
+    x = start_vector(K.D, seed=1234)
+    x /= np.linalg.norm(x)
+    y = np.zeros(K.D)
+    tables = sum(len(tg) * 4 + len(st) * 12 for (st, rp, tg, _) in K.tables)
+    nbytes = hv_bytes(K.D, tables)
+    for _ in range(args.warmup):
+        K.hv_acc(x, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        y[:] = 0.0
+        K.hv_acc(x, y)
+    dt = time.perf_counter() - t0
+    value = nbytes * args.steps / dt / 1e9
+    cores = len(os.sched_getaffinity(0))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded SplitMix64 start vector)",
+            "config": dict(WORKLOAD, step="one H*v (oracle Kronecker-sum, host cores)"),
+            "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} full H*v calls on the 4x4 (8,8) sector"},
+            "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--solves", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/* hubbard.h - C ABI of the GB300 Hubbard exact-diagonalization hot path.
+ *
+ * Method: T. Siro and A. Harju, "Exact diagonalization of the Hubbard model
+ * on graphics processing units" (arXiv:1204.3425).  The library computes,
+ * in one fixed (N_up, N_dn) sector of
+ *
+ *     H = -t sum_<ij> sum_sigma (c+_{i sigma} c_{j sigma} + h.c.)
+ *         + U sum_i n_{i up} n_{i dn}                              (Eq. 1)
+ *
+ * the product w = H v and the Lanczos ground state (Sec. 2.2, Algorithm 1).
+ *
+ * Conventions (Sec. 2.1):
+ *   - a spin configuration is an Ns-bit word, bit i set <=> site i occupied;
+ *   - i_sigma is the position of that word in the ascending list of Ns-bit
+ *     words with N_sigma bits set; the vector index is
+ *         J = i_up * D_dn + i_dn,   D_sigma = C(Ns, N_sigma)  (Eq. J-formula)
+ *     so a vector is a row-major D_up x D_dn matrix (the "subvectors" of
+ *     Fig. 2 are its rows);
+ *   - basis states put all up creators left of all down creators, sites in
+ *     ascending order; a hop of a spin-sigma electron picks up (-1) per
+ *     same-spin electron on sites strictly between origin and destination.
+ *
+ * General rules for every call:
+ *   - Return value: HUB_OK (0) or a positive hub_status code; a message is
+ *     then available from hubbard_last_error() (thread-local).  No call
+ *     aborts the process or throws across the ABI.
+ *   - Device pointers are plain CUDA device addresses on the current device,
+ *     owned by the caller unless stated.  They must be 16-byte aligned.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Calls that return only device results are asynchronous on
+ *     that stream; calls that return host results synchronise the stream.
+ *   - dtype: HUB_F64 (IEEE binary64 vectors) or HUB_F32 (binary32 vectors).
+ *     The F64 path keeps binary64 storage but accumulates hop sums in exact
+ *     integer fixed point (see hubbard_apply).
+ */
+#ifndef HUBBARD_H
+#define HUBBARD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hubbard_sector* hubbard_t;
+
+typedef enum {
+    HUB_OK = 0,
+    HUB_EINVAL = 1,    /* invalid argument (sizes, pointers, alignment, ranges)   */
+    HUB_ENOMEM = 2,    /* device or host allocation failed, or workspace too small */
+    HUB_ECUDA = 3,     /* a CUDA runtime call failed                               */
+    HUB_ENOTCONV = 4,  /* Lanczos hit max_iters before the residual test passed    */
+    HUB_ETIMEOUT = 5,  /* a bounded device wait gave up                            */
+    HUB_EDEVICE = 6    /* a kernel reported an error through its status word       */
+} hub_status;
+
+typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
+
+/* ---------------------------------------------------------------------------
+ * Sector handle (Sec. 2.1 basis and ranking; Sec. 4.2 Kronecker split).
+ *
+ * hubbard_sector_create builds, on the host, the ascending basis of each spin
+ * (Eq. J-formula) and the per-spin hopping tables of H_up and H_dn
+ * (Eq. H-Kroneckersum): for every rank r and every bond with exactly one end
+ * occupied, the target rank r' and the Jordan-Wigner sign of Sec. 2.1.  It
+ * copies them to the current device and returns an opaque handle that owns
+ * them.
+ *   Ns      number of sites, 1..32
+ *   bonds   host array of 2*n_bonds int32: (i0, j0, i1, j1, ...), 0 <= i,j < Ns,
+ *           i != j, no unordered pair repeated.  n_bonds may be 0.
+ *   Nup,Ndn 0..Ns electrons of each spin
+ *   t, U    finite hopping amplitude and on-site interaction of Eq. (1)
+ *   out     receives the handle (NULL on failure)
+ * Errors: HUB_EINVAL for any violated rule above or D_sigma > 2^30;
+ *         HUB_ENOMEM / HUB_ECUDA on allocation or copy failure.
+ * The handle is tied to the device that was current at creation; every later
+ * call must run with that device current.  Not thread-safe per handle.
+ * ------------------------------------------------------------------------- */
+int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn,
+                          double t, double U, hubbard_t* out);
+
+/* Frees the device tables (synchronising the device first).  NULL is a no-op. */
+void hubbard_sector_destroy(hubbard_t H);
+
+/* Dimensions D_up, D_dn and maximum hops per state W_up, W_dn (any may be NULL). */
+int hubbard_sector_info(hubbard_t H, int64_t* D_up, int64_t* D_dn, int32_t* W_up, int32_t* W_dn);
+
+/* Number of stored (target, sign) entries of H_sigma (spin 0 = up, 1 = down). */
+int64_t hubbard_table_nnz(hubbard_t H, int spin);
+
+/* Canonical host copy of one spin's basis and hopping table, for bit-exact
+ * comparison (Sec. 2.1 matrix elements).  Host buffers, caller-owned:
+ *   states[D_sigma]      ascending basis words
+ *   rowptr[D_sigma + 1]  CSR row pointers
+ *   tgt[nnz], sign[nnz]  for row r, every r' with <r'|H_sigma|r> = -t*sign != 0,
+ *                        sorted by r'
+ * Any pointer may be NULL to skip that array. */
+int hubbard_export_tables(hubbard_t H, int spin, uint32_t* states, int32_t* rowptr,
+                          int32_t* tgt, int8_t* sign);
+
+/* Host-only variant of the per-spin table build (no device needed), for
+ * testing the basis and sign tables on machines without a GPU.  Call once
+ * with states/rowptr/tgt/sign all NULL to get *D and *nnz, then again with
+ * host buffers of those sizes.  Same argument rules as hubbard_sector_create
+ * for Ns, bonds and N. */
+int hubbard_host_spin_tables(int Ns, const int32_t* bonds, int n_bonds, int N, int64_t* D, int64_t* nnz,
+                             uint32_t* states, int32_t* rowptr, int32_t* tgt, int8_t* sign);
+
+/* ---------------------------------------------------------------------------
+ * w = H v  (Sec. 4.3: the fused up-hop, down-hop and interaction kernel,
+ * Algorithms 2-4, restated for sm_103a).
+ *   v, w   device vectors of D = D_up*D_dn elements of `dtype`, row-major
+ *          D_up x D_dn (Fig. 2), 16-byte aligned, w must not overlap v.
+ * HUB_F64: the hop sums are exact integer sums of the elements of v rounded
+ * to a common fixed-point grid of 2^-48 * 2^ceil(log2 max|v|); the result is
+ * within 1e-12 * |t| * max|v| of the exact product (max-abs).  This path uses
+ * a device workspace owned by the handle, allocated on first use (the first
+ * call may therefore allocate; later calls do not).
+ * HUB_F32: binary32 arithmetic throughout.
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream);
+
+/* Same as hubbard_apply, reference kernel: one thread per element, native
+ * arithmetic of `dtype` (binary64 DADD/DFMA for HUB_F64), no workspace.
+ * Kept as the parity anchor for the fast path. */
+int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Lanczos vector operations (Algorithm 1, lines 5-7), n elements of dtype,
+ * results accumulated in binary64 in a fixed reduction order (deterministic
+ * for a given n and dtype).  Device vectors; host scalar results; these
+ * synchronise `stream`.
+ * ------------------------------------------------------------------------- */
+int hubbard_vec_dot(const void* x, const void* y, int64_t n, int dtype, void* stream, double* out);
+int hubbard_vec_nrm2(const void* x, int64_t n, int dtype, void* stream, double* out);
+/* y <- y + a*x  (asynchronous) */
+int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * One step of Algorithm 1 in the two-vector form of Eqs. (split1):
+ *   g <- H f - beta_j g;  alpha_j = g.f;  g <- g - alpha_j f;
+ *   beta_{j+1} = |g|;  g <- g / beta_{j+1}  (skipped when beta_{j+1} == 0)
+ * f must have norm 1.  f, g device vectors of D elements.  Writes alpha_j
+ * and beta_{j+1} to *alpha, *beta_next (host).  Synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int dtype,
+                         void* stream, double* alpha, double* beta_next);
+
+/* ---------------------------------------------------------------------------
+ * Lanczos ground state (Sec. 2.2, Algorithm 1, two-vector form).
+ *   v0         device start vector of D elements (dtype); normalised inside,
+ *              not modified
+ *   max_iters  >= 1; the iteration count is also capped at D
+ *   tol        stop when rho = beta_{m+1} * |s_m| < tol (s = lowest
+ *              eigenvector of the tridiagonal T_m); tol <= 0 runs exactly
+ *              max_iters steps (or to breakdown)
+ *   workspace  device buffer of at least lanczos_workspace_bytes(H, dtype)
+ *              bytes, caller-owned, 256-byte aligned
+ *   alpha_out, beta_out  optional host arrays of max_iters doubles receiving
+ *              a_1..a_m and b_2..b_{m+1}
+ *   out        host result: energy (lowest Ritz value), residual rho, iters,
+ *              status, breakdown flag
+ * Breakdown (beta_{m+1} <= 1e-13 * max(1, max|a|, max b)) counts as
+ * converged.  Returns HUB_ENOTCONV (with the best energy in *out) when
+ * max_iters is reached with tol > 0 and rho >= tol.  Synchronises `stream`.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double energy;
+    double residual;
+    int32_t iters;
+    int32_t status;
+    int32_t breakdown;
+    int32_t reserved;
+} lanczos_result;
+
+size_t lanczos_workspace_bytes(hubbard_t H, int dtype);
+
+int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype,
+                         void* workspace, size_t ws_bytes, void* stream,
+                         double* alpha_out, double* beta_out, lanczos_result* out);
+
+/* Number of kernels this library has launched in this process (all threads,
+ * all devices) - instrumentation for benchmarks and tests. */
+uint64_t hubbard_kernel_launches(void);
+
+/* Message for the last failing call on this thread ("" if none). */
+const char* hubbard_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUBBARD_H */

@@ -1,0 +1,234 @@
+"""Python binding of libhubbard.so (include/hubbard.h): argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts torch
+tensors to device pointers and the current torch stream to a cudaStream_t,
+and raises HubError on a non-zero status.  There is no CPU fallback: if the
+compiled library is missing, importing the binding's functions fails.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libhubbard.so")
+
+HUB_OK, HUB_EINVAL, HUB_ENOMEM, HUB_ECUDA, HUB_ENOTCONV, HUB_ETIMEOUT, HUB_EDEVICE = range(7)
+HUB_F64, HUB_F32 = 0, 1
+STATUS_NAMES = {0: "HUB_OK", 1: "HUB_EINVAL", 2: "HUB_ENOMEM", 3: "HUB_ECUDA", 4: "HUB_ENOTCONV",
+                5: "HUB_ETIMEOUT", 6: "HUB_EDEVICE"}
+
+
+class HubError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class LanczosResult(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("iters", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("breakdown", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+P, I32, I64, D, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+
+# name -> (restype, argtypes); must match include/hubbard.h
+SIGNATURES = {
+    "hubbard_sector_create": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D, P]),
+    "hubbard_sector_destroy": (None, [P]),
+    "hubbard_sector_info": (ctypes.c_int, [P, P, P, P, P]),
+    "hubbard_table_nnz": (I64, [P, ctypes.c_int]),
+    "hubbard_export_tables": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P]),
+    "hubbard_apply": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "hubbard_apply_reference": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "hubbard_vec_dot": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, P]),
+    "hubbard_vec_nrm2": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
+    "hubbard_vec_axpy": (ctypes.c_int, [D, P, P, I64, ctypes.c_int, P]),
+    "hubbard_lanczos_step": (ctypes.c_int, [P, P, P, D, ctypes.c_int, P, P, P]),
+    "lanczos_workspace_bytes": (SZ, [P, ctypes.c_int]),
+    "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P]),
+    "hubbard_host_spin_tables": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]),
+    "hubbard_kernel_launches": (ctypes.c_uint64, []),
+    "hubbard_last_error": (ctypes.c_char_p, []),
+}
+
+
+def load_library(path=LIB_PATH):
+    """Load libhubbard.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1204_3425_gb300.build`")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != HUB_OK:
+        raise HubError(rc, _lib.hubbard_last_error().decode())
+
+
+def _dtype_code(t):
+    import torch
+    if t.dtype == torch.float64:
+        return HUB_F64
+    if t.dtype == torch.float32:
+        return HUB_F32
+    raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _ptr(t):
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Sector:
+    """Owns one hubbard_t handle (device hopping tables of one sector)."""
+
+    def __init__(self, handle, ns, bonds, nup, ndn, t, U):
+        self.handle = handle
+        self.ns, self.bonds, self.nup, self.ndn, self.t, self.U = ns, bonds, nup, ndn, t, U
+        self.Dup, self.Ddn, self.Wup, self.Wdn = hubbard_sector_info(self)
+        self.D = self.Dup * self.Ddn
+
+    def close(self):
+        if self.handle:
+            _lib.hubbard_sector_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def hubbard_sector_create(ns, bonds, nup, ndn, t=1.0, U=0.0):
+    lib = load_library()
+    arr = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+    h = ctypes.c_void_p()
+    _check(lib.hubbard_sector_create(int(ns), arr.ctypes.data if arr.size else None, arr.size // 2,
+                                     int(nup), int(ndn), float(t), float(U), ctypes.byref(h)))
+    return Sector(h, ns, bonds, nup, ndn, t, U)
+
+
+def hubbard_sector_info(H):
+    a, b, c, d = I64(), I64(), I32(), I32()
+    _check(load_library().hubbard_sector_info(H.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c),
+                                              ctypes.byref(d)))
+    return a.value, b.value, c.value, d.value
+
+
+def hubbard_export_tables(H, spin):
+    lib = load_library()
+    D = H.Dup if spin == 0 else H.Ddn
+    nnz = lib.hubbard_table_nnz(H.handle, spin)
+    states = np.zeros(D, dtype=np.uint32)
+    rowptr = np.zeros(D + 1, dtype=np.int32)
+    tgt = np.zeros(max(nnz, 1), dtype=np.int32)
+    sign = np.zeros(max(nnz, 1), dtype=np.int8)
+    _check(lib.hubbard_export_tables(H.handle, spin, states.ctypes.data, rowptr.ctypes.data, tgt.ctypes.data,
+                                     sign.ctypes.data))
+    return states, rowptr, tgt[:nnz], sign[:nnz]
+
+
+def hubbard_host_spin_tables(ns, bonds, n):
+    """Host-only per-spin basis and hopping table (no GPU needed)."""
+    lib = load_library()
+    arr = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+    bp = arr.ctypes.data if arr.size else None
+    D, nnz = I64(), I64()
+    _check(lib.hubbard_host_spin_tables(int(ns), bp, arr.size // 2, int(n), ctypes.byref(D), ctypes.byref(nnz),
+                                        None, None, None, None))
+    states = np.zeros(D.value, dtype=np.uint32)
+    rowptr = np.zeros(D.value + 1, dtype=np.int32)
+    tgt = np.zeros(max(nnz.value, 1), dtype=np.int32)
+    sign = np.zeros(max(nnz.value, 1), dtype=np.int8)
+    _check(lib.hubbard_host_spin_tables(int(ns), bp, arr.size // 2, int(n), None, None, states.ctypes.data,
+                                        rowptr.ctypes.data, tgt.ctypes.data, sign.ctypes.data))
+    return states, rowptr, tgt[:nnz.value], sign[:nnz.value]
+
+
+def hubbard_apply(H, v, w, stream=None):
+    _check(load_library().hubbard_apply(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
+    return w
+
+
+def hubbard_apply_reference(H, v, w, stream=None):
+    _check(load_library().hubbard_apply_reference(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
+    return w
+
+
+def hubbard_vec_dot(x, y, stream=None):
+    out = D()
+    _check(load_library().hubbard_vec_dot(_ptr(x), _ptr(y), x.numel(), _dtype_code(x), _stream(stream),
+                                          ctypes.byref(out)))
+    return out.value
+
+
+def hubbard_vec_nrm2(x, stream=None):
+    out = D()
+    _check(load_library().hubbard_vec_nrm2(_ptr(x), x.numel(), _dtype_code(x), _stream(stream), ctypes.byref(out)))
+    return out.value
+
+
+def hubbard_vec_axpy(a, x, y, stream=None):
+    _check(load_library().hubbard_vec_axpy(float(a), _ptr(x), _ptr(y), x.numel(), _dtype_code(x), _stream(stream)))
+    return y
+
+
+def hubbard_lanczos_step(H, f, g, beta_j, stream=None):
+    a, b = D(), D()
+    _check(load_library().hubbard_lanczos_step(H.handle, _ptr(f), _ptr(g), float(beta_j), _dtype_code(f),
+                                               _stream(stream), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def lanczos_workspace_bytes(H, dtype=HUB_F64):
+    return int(load_library().lanczos_workspace_bytes(H.handle, dtype))
+
+
+def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None, raise_on_notconv=False):
+    """Returns dict(energy, residual, iters, status, breakdown, alpha, beta)."""
+    import torch
+    lib = load_library()
+    dt = _dtype_code(v0)
+    need = lanczos_workspace_bytes(H, dt)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=v0.device)
+    a = np.zeros(max_iters)
+    b = np.zeros(max_iters)
+    res = LanczosResult()
+    rc = lib.lanczos_ground_state(H.handle, _ptr(v0), int(max_iters), float(tol), dt, _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream),
+                                  a.ctypes.data, b.ctypes.data, ctypes.byref(res))
+    if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
+        _check(rc)
+    m = res.iters
+    return dict(energy=res.energy, residual=res.residual, iters=m, status=res.status,
+                breakdown=bool(res.breakdown), alpha=a[:m], beta=b[:m])
+
+
+def hubbard_kernel_launches():
+    return int(load_library().hubbard_kernel_launches())
+
+
+def hubbard_last_error():
+    return load_library().hubbard_last_error().decode()

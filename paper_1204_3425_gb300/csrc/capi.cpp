@@ -1,0 +1,487 @@
+// C ABI entry points (include/hubbard.h): argument checks, device tables,
+// dispatch to the kernels, and the Lanczos driver (Sec. 2.2, Algorithm 1).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace hub {
+
+namespace {
+thread_local std::string g_last_error;
+std::atomic<uint64_t> g_launches{0};
+}
+
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+void clear_error() { g_last_error.clear(); }
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return HUB_ECUDA;
+}
+
+namespace {
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+size_t elem_size(int dtype) { return dtype == HUB_F64 ? 8 : 4; }
+
+int check_handle(hubbard_t H) {
+    if (H == nullptr) return fail(HUB_EINVAL, "null handle");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != H->device)
+        return fail(HUB_EINVAL, "handle was created on another device");
+    return HUB_OK;
+}
+
+int check_dtype(int dtype) {
+    if (dtype != HUB_F64 && dtype != HUB_F32) return fail(HUB_EINVAL, "dtype must be HUB_F64 or HUB_F32");
+    return HUB_OK;
+}
+
+template <typename T>
+int upload(T** dst, const T* src, size_t n) {
+    *dst = nullptr;
+    size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tables)");
+    if (n > 0) HUB_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+    return HUB_OK;
+}
+
+void free_dev(hubbard_sector* H) {
+    for (auto& d : H->dev) {
+        cudaFree(d.states);
+        cudaFree(d.rowptr);
+        cudaFree(d.ent);
+        cudaFree(d.ell);
+        cudaFree(d.cnt);
+        d = DevSpin{};
+    }
+    cudaFree(H->fx_scratch);
+    H->fx_scratch = nullptr;
+    H->fx_bytes = 0;
+    cudaFree(H->red);
+    cudaFree(H->status);
+    H->red = nullptr;
+    H->status = nullptr;
+}
+
+int upload_spin(const SpinTables& T, DevSpin& d) {
+    std::vector<uint32_t> ent(T.tgt.size());
+    for (size_t k = 0; k < T.tgt.size(); ++k)
+        ent[k] = ((uint32_t)T.tgt[k] << 1) | (T.sign[k] < 0 ? 1u : 0u);
+    std::vector<int32_t> cnt((size_t)T.D);
+    std::vector<uint32_t> ell((size_t)T.D * (size_t)std::max(T.W, 1), 0xFFFFFFFFu);
+    for (int64_t r = 0; r < T.D; ++r) {
+        cnt[(size_t)r] = T.rowptr[(size_t)r + 1] - T.rowptr[(size_t)r];
+        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
+            ell[(size_t)c * (size_t)T.D + (size_t)r] = ent[(size_t)k];
+    }
+    int rc;
+    if ((rc = upload(&d.states, T.states.data(), T.states.size()))) return rc;
+    if ((rc = upload(&d.rowptr, T.rowptr.data(), T.rowptr.size()))) return rc;
+    if ((rc = upload(&d.ent, ent.data(), ent.size()))) return rc;
+    if ((rc = upload(&d.ell, ell.data(), ell.size()))) return rc;
+    if ((rc = upload(&d.cnt, cnt.data(), cnt.size()))) return rc;
+    return HUB_OK;
+}
+
+int ensure_fx_scratch(hubbard_sector* H) {
+    const size_t need = (size_t)H->D * 8;
+    if (H->fx_bytes >= need) return HUB_OK;
+    cudaFree(H->fx_scratch);
+    H->fx_scratch = nullptr;
+    H->fx_bytes = 0;
+    cudaError_t e = cudaMalloc(&H->fx_scratch, std::max<size_t>(need, 256));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fixed-point scratch)");
+    H->fx_bytes = need;
+    return HUB_OK;
+}
+
+// hop sums of up to 127 terms fit the two int32 fixed-point accumulators
+bool fixed_point_ok(const hubbard_sector* H) { return H->host[0].W + H->host[1].W <= 127; }
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+}  // namespace hub
+
+using namespace hub;
+
+extern "C" {
+
+const char* hubbard_last_error(void) { return g_last_error.c_str(); }
+
+uint64_t hubbard_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+static long double comb_ld(int n, int k) {
+    long double c = 1;
+    for (int i = 1; i <= k; ++i) c = c * (n - k + i) / i;
+    return c;
+}
+
+// Validates Ns, the bond list and one filling; fills `bl`.
+static int check_lattice(int Ns, const int32_t* bonds, int n_bonds, int N, std::vector<std::pair<int, int>>& bl) {
+    if (Ns < 1 || Ns > 32) return fail(HUB_EINVAL, "Ns must be in 1..32");
+    if (N < 0 || N > Ns) return fail(HUB_EINVAL, "N_up, N_dn must be in 0..Ns");
+    if (n_bonds < 0 || (n_bonds > 0 && bonds == nullptr)) return fail(HUB_EINVAL, "bad bond list");
+    bl.clear();
+    std::set<std::pair<int, int>> seen;
+    for (int b = 0; b < n_bonds; ++b) {
+        int i = bonds[2 * b], j = bonds[2 * b + 1];
+        if (i < 0 || i >= Ns || j < 0 || j >= Ns) return fail(HUB_EINVAL, "bond endpoint out of range");
+        if (i == j) return fail(HUB_EINVAL, "self bond");
+        auto key = std::make_pair(std::min(i, j), std::max(i, j));
+        if (!seen.insert(key).second) return fail(HUB_EINVAL, "duplicate bond");
+        bl.emplace_back(i, j);
+    }
+    // D_sigma = C(Ns, N_sigma) must stay below 2^30 (packed table entries)
+    if (comb_ld(Ns, N) > (long double)(1 << 30)) return fail(HUB_EINVAL, "D_sigma exceeds 2^30");
+    return HUB_OK;
+}
+
+int hubbard_host_spin_tables(int Ns, const int32_t* bonds, int n_bonds, int N, int64_t* D, int64_t* nnz,
+                             uint32_t* states, int32_t* rowptr, int32_t* tgt, int8_t* sign) {
+    clear_error();
+    std::vector<std::pair<int, int>> bl;
+    int rc = check_lattice(Ns, bonds, n_bonds, N, bl);
+    if (rc) return rc;
+    SpinTables T;
+    try {
+        build_spin_tables(Ns, N, bl, T);
+    } catch (const std::bad_alloc&) {
+        return fail(HUB_ENOMEM, "host allocation (tables)");
+    }
+    if (D) *D = T.D;
+    if (nnz) *nnz = (int64_t)T.tgt.size();
+    if (states) std::memcpy(states, T.states.data(), T.states.size() * sizeof(uint32_t));
+    if (rowptr) std::memcpy(rowptr, T.rowptr.data(), T.rowptr.size() * sizeof(int32_t));
+    if (tgt) std::memcpy(tgt, T.tgt.data(), T.tgt.size() * sizeof(int32_t));
+    if (sign) std::memcpy(sign, T.sign.data(), T.sign.size() * sizeof(int8_t));
+    return HUB_OK;
+}
+
+int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn, double t, double U,
+                          hubbard_t* out) {
+    clear_error();
+    if (out == nullptr) return fail(HUB_EINVAL, "out is null");
+    *out = nullptr;
+    std::vector<std::pair<int, int>> bl;
+    int rc0 = check_lattice(Ns, bonds, n_bonds, Nup, bl);
+    if (rc0 == HUB_OK) rc0 = check_lattice(Ns, bonds, n_bonds, Ndn, bl);
+    if (rc0) return rc0;
+    if (!std::isfinite(t) || !std::isfinite(U)) return fail(HUB_EINVAL, "t and U must be finite");
+    hubbard_sector* H = new (std::nothrow) hubbard_sector();
+    if (H == nullptr) return fail(HUB_ENOMEM, "host allocation");
+    if (cudaGetDevice(&H->device) != cudaSuccess) {
+        delete H;
+        return fail(HUB_ECUDA, "no CUDA device");
+    }
+    H->ns = Ns;
+    H->nup = Nup;
+    H->ndn = Ndn;
+    H->t = t;
+    H->U = U;
+    H->bonds = bl;
+    try {
+        build_spin_tables(Ns, Nup, bl, H->host[0]);
+        build_spin_tables(Ns, Ndn, bl, H->host[1]);
+    } catch (const std::bad_alloc&) {
+        delete H;
+        return fail(HUB_ENOMEM, "host allocation (tables)");
+    }
+    H->Dup = H->host[0].D;
+    H->Ddn = H->host[1].D;
+    H->D = H->Dup * H->Ddn;
+    int rc = upload_spin(H->host[0], H->dev[0]);
+    if (rc == HUB_OK) rc = upload_spin(H->host[1], H->dev[1]);
+    if (rc == HUB_OK) {
+        cudaError_t e = cudaMalloc((void**)&H->red, kRedSlots * sizeof(double));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&H->status, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(H->status, 0, 4 * sizeof(int));
+        if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
+    }
+    if (rc != HUB_OK) {
+        std::string msg = g_last_error;
+        free_dev(H);
+        delete H;
+        return fail(rc, msg);
+    }
+    *out = H;
+    return HUB_OK;
+}
+
+void hubbard_sector_destroy(hubbard_t H) {
+    if (H == nullptr) return;
+    cudaDeviceSynchronize();
+    free_dev(H);
+    delete H;
+}
+
+int hubbard_sector_info(hubbard_t H, int64_t* D_up, int64_t* D_dn, int32_t* W_up, int32_t* W_dn) {
+    clear_error();
+    if (H == nullptr) return fail(HUB_EINVAL, "null handle");
+    if (D_up) *D_up = H->Dup;
+    if (D_dn) *D_dn = H->Ddn;
+    if (W_up) *W_up = H->host[0].W;
+    if (W_dn) *W_dn = H->host[1].W;
+    return HUB_OK;
+}
+
+int64_t hubbard_table_nnz(hubbard_t H, int spin) {
+    if (H == nullptr || (spin != 0 && spin != 1)) return -1;
+    return (int64_t)H->host[spin].tgt.size();
+}
+
+int hubbard_export_tables(hubbard_t H, int spin, uint32_t* states, int32_t* rowptr, int32_t* tgt, int8_t* sign) {
+    clear_error();
+    if (H == nullptr) return fail(HUB_EINVAL, "null handle");
+    if (spin != 0 && spin != 1) return fail(HUB_EINVAL, "spin must be 0 (up) or 1 (down)");
+    const SpinTables& T = H->host[spin];
+    if (states) std::memcpy(states, T.states.data(), T.states.size() * sizeof(uint32_t));
+    if (rowptr) std::memcpy(rowptr, T.rowptr.data(), T.rowptr.size() * sizeof(int32_t));
+    if (tgt) std::memcpy(tgt, T.tgt.data(), T.tgt.size() * sizeof(int32_t));
+    if (sign) std::memcpy(sign, T.sign.data(), T.sign.size() * sizeof(int8_t));
+    return HUB_OK;
+}
+
+static int check_apply(hubbard_t H, const void* v, void* w, int dtype) {
+    int rc;
+    if ((rc = check_handle(H))) return rc;
+    if ((rc = check_dtype(dtype))) return rc;
+    if (v == nullptr || w == nullptr) return fail(HUB_EINVAL, "null vector");
+    if (!aligned16(v) || !aligned16(w)) return fail(HUB_EINVAL, "vectors must be 16-byte aligned");
+    const size_t bytes = (size_t)H->D * elem_size(dtype);
+    const char* a = (const char*)v;
+    const char* b = (const char*)w;
+    if (a < b + bytes && b < a + bytes) return fail(HUB_EINVAL, "v and w overlap");
+    return HUB_OK;
+}
+
+int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream) {
+    clear_error();
+    int rc = check_apply(H, v, w, dtype);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == HUB_F64 && !fixed_point_ok(H)) return launch_hv_reference(H, v, w, dtype, s);
+    if (dtype == HUB_F64 && (rc = ensure_fx_scratch(H))) return rc;
+    return launch_hv_fast(H, v, w, dtype, 0.0, nullptr, s);
+}
+
+int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream) {
+    clear_error();
+    int rc = check_apply(H, v, w, dtype);
+    if (rc) return rc;
+    return launch_hv_reference(H, v, w, dtype, (cudaStream_t)stream);
+}
+
+static int check_vec(const void* x, int64_t n, int dtype) {
+    int rc;
+    if ((rc = check_dtype(dtype))) return rc;
+    if (n < 0) return fail(HUB_EINVAL, "negative length");
+    if (n > 0 && x == nullptr) return fail(HUB_EINVAL, "null vector");
+    if (!aligned16(x)) return fail(HUB_EINVAL, "vectors must be 16-byte aligned");
+    return HUB_OK;
+}
+
+// Reductions use a small per-thread scratch allocated once per device thread.
+static double* reduction_scratch() {
+    static thread_local double* p = nullptr;
+    static thread_local int dev = -1;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (p == nullptr || dev != cur) {
+        p = nullptr;
+        if (cudaMalloc((void**)&p, kRedSlots * sizeof(double)) != cudaSuccess) p = nullptr;
+        dev = cur;
+    }
+    return p;
+}
+
+int hubbard_vec_dot(const void* x, const void* y, int64_t n, int dtype, void* stream, double* out) {
+    clear_error();
+    int rc;
+    if ((rc = check_vec(x, n, dtype)) || (rc = check_vec(y, n, dtype))) return rc;
+    if (out == nullptr) return fail(HUB_EINVAL, "out is null");
+    double* red = reduction_scratch();
+    if (red == nullptr) return fail(HUB_ENOMEM, "reduction scratch");
+    cudaStream_t s = (cudaStream_t)stream;
+    if ((rc = launch_dot(nullptr, x, y, n, dtype, red, s))) return rc;
+    return reduce_partials_host(red, s, out);
+}
+
+int hubbard_vec_nrm2(const void* x, int64_t n, int dtype, void* stream, double* out) {
+    double s2 = 0.0;
+    int rc = hubbard_vec_dot(x, x, n, dtype, stream, &s2);
+    if (rc) return rc;
+    *out = std::sqrt(s2);
+    return HUB_OK;
+}
+
+int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_vec(x, n, dtype)) || (rc = check_vec(y, n, dtype))) return rc;
+    return launch_axpy(a, x, y, n, dtype, (cudaStream_t)stream);
+}
+
+// One Lanczos step (Eqs. split1 + Algorithm 1 lines 5-11) on caller vectors.
+static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
+                             double* alpha, double* beta_next, bool normalise) {
+    int rc;
+    if (dtype == HUB_F64 && fixed_point_ok(H)) {
+        // g <- H f - beta_j g, fused
+        if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, s))) return rc;
+    } else {
+        // g <- -beta_j g ; g <- g + H f  (reference kernel needs a separate output)
+        return fail(HUB_EINVAL, "lanczos step: only the binary64 fixed-point path is available");
+    }
+    if ((rc = launch_dot(H, g, f, H->D, dtype, H->red, s))) return rc;
+    double a = 0.0;
+    if ((rc = reduce_partials_host(H->red, s, &a))) return rc;
+    if ((rc = launch_axpy_nrm2(-a, f, g, H->D, dtype, H->red, s))) return rc;
+    double b2 = 0.0;
+    if ((rc = reduce_partials_host(H->red, s, &b2))) return rc;
+    const double b = std::sqrt(std::max(b2, 0.0));
+    if (normalise && b > 0.0)
+        if ((rc = launch_scale(1.0 / b, g, H->D, dtype, s))) return rc;
+    *alpha = a;
+    *beta_next = b;
+    return HUB_OK;
+}
+
+int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int dtype, void* stream,
+                         double* alpha, double* beta_next) {
+    clear_error();
+    int rc = check_apply(H, f, g, dtype);
+    if (rc) return rc;
+    if (alpha == nullptr || beta_next == nullptr) return fail(HUB_EINVAL, "null output");
+    if (dtype == HUB_F64 && (rc = ensure_fx_scratch(H))) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = lanczos_step_impl(H, f, g, beta_j, dtype, s, alpha, beta_next, true);
+    if (rc == HUB_OK) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "lanczos step");
+    }
+    return rc;
+}
+
+size_t lanczos_workspace_bytes(hubbard_t H, int dtype) {
+    if (H == nullptr || (dtype != HUB_F64 && dtype != HUB_F32)) return 0;
+    const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
+    size_t total = 2 * vec;
+    if (dtype == HUB_F64) total += align_up((size_t)H->D * 8, 256);   // fixed-point copy
+    return total;
+}
+
+int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype, void* workspace,
+                         size_t ws_bytes, void* stream, double* alpha_out, double* beta_out,
+                         lanczos_result* out) {
+    clear_error();
+    int rc;
+    if ((rc = check_handle(H))) return rc;
+    if ((rc = check_dtype(dtype))) return rc;
+    if (out == nullptr) return fail(HUB_EINVAL, "out is null");
+    std::memset(out, 0, sizeof(*out));
+    if (v0 == nullptr || !aligned16(v0)) return fail(HUB_EINVAL, "v0 null or not 16-byte aligned");
+    if (max_iters < 1) return fail(HUB_EINVAL, "max_iters must be >= 1");
+    if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return fail(HUB_EINVAL, "workspace null or not 256-byte aligned");
+    if (ws_bytes < lanczos_workspace_bytes(H, dtype)) return fail(HUB_ENOMEM, "workspace too small");
+    if (dtype != HUB_F64 || !fixed_point_ok(H))
+        return fail(HUB_EINVAL, "lanczos: only the binary64 fixed-point path is available");
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
+    char* ws = (char*)workspace;
+    void* f = ws;
+    void* g = ws + vec;
+    // the fixed-point copy lives in the caller's workspace for the solve
+    void* saved_fx = H->fx_scratch;
+    size_t saved_bytes = H->fx_bytes;
+    H->fx_scratch = ws + 2 * vec;
+    H->fx_bytes = (size_t)H->D * 8;
+    auto restore = [&]() {
+        H->fx_scratch = saved_fx;
+        H->fx_bytes = saved_bytes;
+    };
+    // f_1 = v0 / |v0|, f_0 = 0 (Algorithm 1)
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) {
+        restore();
+        return rc;
+    }
+    n0 = std::sqrt(n0);
+    if (!(n0 > 0.0) || !std::isfinite(n0)) {
+        restore();
+        return fail(HUB_EINVAL, "start vector has zero or non-finite norm");
+    }
+    if ((rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / n0, s))) {
+        restore();
+        return rc;
+    }
+    if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) {
+        restore();
+        return fail(HUB_ECUDA, "memset");
+    }
+    const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
+    std::vector<double> a, b;
+    double bj = 0.0, theta = 0.0, rho = 0.0;
+    bool broke = false, converged = false;
+    for (int j = 0; j < m_cap; ++j) {
+        double aj = 0.0, bn = 0.0;
+        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false))) {
+            restore();
+            return rc;
+        }
+        a.push_back(aj);
+        double s_last = 1.0;
+        tridiag_lowest(a.data(), b.data(), (int)a.size(), &theta, &s_last);
+        rho = bn * std::fabs(s_last);
+        double scale = 1.0;
+        for (double x : a) scale = std::max(scale, std::fabs(x));
+        for (double x : b) scale = std::max(scale, x);
+        b.push_back(bn);
+        if (bn <= 1e-13 * scale) {
+            broke = true;
+            converged = true;
+            break;
+        }
+        if (tol > 0.0 && rho < tol) {
+            converged = true;
+            break;
+        }
+        if ((rc = launch_scale(1.0 / bn, g, H->D, dtype, s))) {
+            restore();
+            return rc;
+        }
+        std::swap(f, g);
+        bj = bn;
+    }
+    restore();
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+    const int m = (int)a.size();
+    if (alpha_out) std::memcpy(alpha_out, a.data(), m * sizeof(double));
+    if (beta_out) std::memcpy(beta_out, b.data(), m * sizeof(double));
+    out->energy = theta;
+    out->residual = rho;
+    out->iters = m;
+    out->breakdown = broke ? 1 : 0;
+    if (tol <= 0.0) converged = true;
+    out->status = converged ? HUB_OK : HUB_ENOTCONV;
+    if (!converged) return fail(HUB_ENOTCONV, "max_iters reached before the residual test passed");
+    return HUB_OK;
+}
+
+}  // extern "C"

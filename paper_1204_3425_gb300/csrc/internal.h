@@ -1,0 +1,90 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+#include <cuda_runtime.h>
+#include "../../include/hubbard.h"
+
+namespace hub {
+
+// thread-local last-error message (hubbard_last_error)
+void set_error(const std::string& msg);
+void clear_error();
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define HUB_CUDA(call)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return ::hub::cuda_fail(e_, #call); \
+    } while (0)
+
+// Per-spin host tables (Sec. 2.1 basis; Eq. H-Kroneckersum factors).
+struct SpinTables {
+    int ns = 0, n = 0;
+    int64_t D = 0;
+    int W = 0;                       // max hops per state
+    std::vector<uint32_t> states;    // ascending basis words
+    std::vector<int32_t> rowptr;     // CSR by source row r (= output row, H symmetric)
+    std::vector<int32_t> tgt;        // target rank r'
+    std::vector<int8_t> sign;        // +1 / -1: <r'|H|r> = -t * sign
+};
+
+// Builds the basis and hopping table of one spin species.
+void build_spin_tables(int ns, int n, const std::vector<std::pair<int, int>>& bonds, SpinTables& out);
+
+// Device copy of one spin's tables.
+struct DevSpin {
+    uint32_t* states = nullptr;      // [D]
+    int32_t* rowptr = nullptr;       // [D+1]
+    uint32_t* ent = nullptr;         // [nnz] packed (target << 1) | (sign < 0)
+    uint32_t* ell = nullptr;         // [W * D] column-major ELL, packed as ent; pad = 0xFFFFFFFF
+    int32_t* cnt = nullptr;          // [D] hops per state
+};
+
+}  // namespace hub
+
+struct hubbard_sector {
+    int device = 0;
+    int ns = 0, nup = 0, ndn = 0;
+    double t = 0.0, U = 0.0;
+    std::vector<std::pair<int, int>> bonds;
+    hub::SpinTables host[2];
+    hub::DevSpin dev[2];
+    int64_t Dup = 0, Ddn = 0, D = 0;
+    // fixed-point scratch for the F64 fast path, allocated on first use
+    void* fx_scratch = nullptr;
+    size_t fx_bytes = 0;
+    // small device scratch for reductions: partial sums, status words
+    double* red = nullptr;           // [kRedSlots]
+    int* status = nullptr;           // [4]
+};
+
+namespace hub {
+constexpr int kRedSlots = 4096;      // partial-sum slots for block reductions
+constexpr int kRedBlocks = 1024;     // grid size of reduction kernels (<= kRedSlots/2)
+
+// process-wide count of kernel launches (hubbard_kernel_launches)
+void count_launches(int n);
+
+// kernels.cu launchers -------------------------------------------------------
+int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dtype, cudaStream_t s);
+int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta,
+                   const void* w_old, cudaStream_t s);
+int launch_dot(const hubbard_sector* H, const void* x, const void* y, int64_t n, int dtype,
+               double* partials, cudaStream_t s);
+int reduce_partials_host(double* partials, cudaStream_t s, double* out);
+int launch_axpy(double a, const void* x, void* y, int64_t n, int dtype, cudaStream_t s);
+int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, double* partials,
+                     cudaStream_t s);
+int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s);
+int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double inv_norm, cudaStream_t s);
+
+// tridiag.cpp -----------------------------------------------------------------
+// Lowest eigenvalue of the symmetric tridiagonal T (diag a[0..m-1], off-diag
+// b[0..m-2]) and the last component of its normalised eigenvector.
+void tridiag_lowest(const double* a, const double* b, int m, double* theta, double* s_last);
+
+}  // namespace hub

@@ -1,0 +1,321 @@
+// H*v and Lanczos vector kernels for sm_103a.
+//
+// Vector layout (Fig. 2): element J = u * D_dn + d, i.e. a row-major
+// D_up x D_dn matrix V.  Up-hops combine whole rows of V (Algorithm 2),
+// down-hops gather inside a row (Algorithm 3), the interaction is diagonal
+// (Algorithm 4).
+//
+// Packed hop entry: (target << 1) | (sign < 0); <target|H_sigma|src> = -t*sign.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hub {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(int64_t work, int per_block, int cap) {
+    int64_t g = (work + per_block - 1) / per_block;
+    if (g < 1) g = 1;
+    if (g > cap) g = cap;
+    return (int)g;
+}
+
+int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// ---------------------------------------------------------------------------
+// Reference H*v: one thread per output element, native arithmetic of T.
+// Rows u are taken block-stride, columns d thread-stride.
+template <typename T>
+__global__ void k_hv_reference(const T* __restrict__ v, T* __restrict__ w, int64_t Dup, int64_t Ddn,
+                               const int32_t* __restrict__ up_ptr, const uint32_t* __restrict__ up_ent,
+                               const int32_t* __restrict__ dn_ptr, const uint32_t* __restrict__ dn_ent,
+                               const uint32_t* __restrict__ su, const uint32_t* __restrict__ sd,
+                               T mt, T U) {
+    for (int64_t u = blockIdx.x; u < Dup; u += gridDim.x) {
+        const int32_t ub = up_ptr[u], ue = up_ptr[u + 1];
+        const uint32_t su_u = su[u];
+        const T* vrow = v + u * Ddn;
+        for (int64_t d = threadIdx.x; d < Ddn; d += blockDim.x) {
+            T hop = T(0);
+            for (int32_t k = ub; k < ue; ++k) {          // H_up (x) I  (Algorithm 2)
+                const uint32_t e = up_ent[k];
+                const T x = v[(int64_t)(e >> 1) * Ddn + d];
+                hop += (e & 1u) ? -x : x;
+            }
+            const int32_t db = dn_ptr[d], de = dn_ptr[d + 1];
+            for (int32_t k = db; k < de; ++k) {          // I (x) H_dn  (Algorithm 3)
+                const uint32_t e = dn_ent[k];
+                const T x = vrow[e >> 1];
+                hop += (e & 1u) ? -x : x;
+            }
+            const int nd = __popc(su_u & sd[d]);         // H_int  (Algorithm 4)
+            w[u * Ddn + d] = mt * hop + U * T(nd) * vrow[d];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Binary64 path in exact fixed point.
+//
+// Every element of v is rounded once to the grid 2^-k, with k chosen so that
+// max|v| * 2^k < 2^48, and stored as X = hi * 2^24 + lo (lo in [0, 2^24),
+// |hi| <= 2^24).  A hop sum of up to 2^6 signed terms then fits two int32
+// accumulators without carries, and is exact.
+
+// max biased exponent of |v| -> *emax (atomicMax; *emax must start at 0)
+__global__ void k_max_exponent(const double* __restrict__ v, int64_t n, int* emax) {
+    int m = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v[i]);
+        m = max(m, (int)((b >> 52) & 0x7FF));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(emax, m);
+}
+
+// rounding of one binary64 to the fixed-point grid given the exponent bound
+__device__ __forceinline__ int2 to_fixed(double x, int emax) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    if (e != 0) mant |= (1ull << 52);
+    const int ee = e > 0 ? e : 1;
+    // value = mant * 2^(ee-1075); X = value * 2^k, k = 1070 - emax  => right shift
+    const int rs = emax - ee + 5;                     // >= 5 because ee <= emax
+    long long X;
+    if (rs >= 60) X = 0;
+    else X = (long long)((mant + (1ull << (rs - 1))) >> rs);
+    if (b >> 63) X = -X;
+    int2 r;
+    r.x = (int)(X & 0xFFFFFF);                        // lo, [0, 2^24)
+    r.y = (int)(X >> 24);                             // hi, arithmetic shift
+    return r;
+}
+
+__global__ void k_to_fixed(const double* __restrict__ v, int2* __restrict__ X, int64_t n,
+                           const int* __restrict__ emax_p) {
+    const int emax = max(*emax_p, 1);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        X[i] = to_fixed(v[i], emax);
+}
+
+// w = -t * S * 2^-k + U * n_d * v  [ - beta * w_old ]
+__global__ void k_hv_fixed(const int2* __restrict__ X, const double* __restrict__ v, double* w,
+                           const double* w_old, double beta, int64_t Dup, int64_t Ddn,
+                           const int32_t* __restrict__ up_ptr, const uint32_t* __restrict__ up_ent,
+                           const int32_t* __restrict__ dn_ptr, const uint32_t* __restrict__ dn_ent,
+                           const uint32_t* __restrict__ su, const uint32_t* __restrict__ sd,
+                           double mt, double U, const int* __restrict__ emax_p) {
+    const int emax = max(*emax_p, 1);
+    const double scale = ldexp(mt, -(1070 - emax));   // -t * 2^-k
+    for (int64_t u = blockIdx.x; u < Dup; u += gridDim.x) {
+        const int32_t ub = up_ptr[u], ue = up_ptr[u + 1];
+        const uint32_t su_u = su[u];
+        const int2* xrow = X + u * Ddn;
+        for (int64_t d = threadIdx.x; d < Ddn; d += blockDim.x) {
+            int lo = 0, hi = 0;
+            for (int32_t k = ub; k < ue; ++k) {
+                const uint32_t e = up_ent[k];
+                const int2 x = X[(int64_t)(e >> 1) * Ddn + d];
+                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+            }
+            const int32_t db = dn_ptr[d], de = dn_ptr[d + 1];
+            for (int32_t k = db; k < de; ++k) {
+                const uint32_t e = dn_ent[k];
+                const int2 x = xrow[e >> 1];
+                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+            }
+            const long long S = ((long long)hi << 24) + (long long)lo;
+            const int64_t J = u * Ddn + d;
+            const int nd = __popc(su_u & sd[d]);
+            double r = fma(U * (double)nd, v[J], scale * (double)S);
+            if (w_old != nullptr) r = fma(-beta, w_old[J], r);
+            w[J] = r;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Reductions: per-thread binary64 sums, warp shuffles, block tree, then one
+// block sums the per-block partials in a fixed order (deterministic).
+__device__ __forceinline__ double block_sum(double s) {
+    __shared__ double red[32];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) red[wid] = s;
+    __syncthreads();
+    s = 0.0;
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        s = lane < nw ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __syncthreads();
+    return s;
+}
+
+template <typename T>
+__global__ void k_dot(const T* __restrict__ x, const T* __restrict__ y, int64_t n, double* partials) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s = fma((double)x[i], (double)y[i], s);
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// y <- y + a x ; partial sums of y^2
+template <typename T>
+__global__ void k_axpy_nrm2(T a, const T* __restrict__ x, T* __restrict__ y, int64_t n, double* partials) {
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = y[i] + a * x[i];
+        y[i] = r;
+        s = fma((double)r, (double)r, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = s;
+}
+
+template <typename T>
+__global__ void k_axpy(T a, const T* __restrict__ x, T* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a * x[i];
+}
+
+template <typename T>
+__global__ void k_scale(T a, T* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] *= a;
+}
+
+template <typename T>
+__global__ void k_copy_scale(const T* __restrict__ x, T* __restrict__ y, int64_t n, T a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = a * x[i];
+}
+
+// sums partials[0..nb) in index order into partials[kRedSlots-1]
+__global__ void k_finish_sum(double* partials, int nb) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[kRedSlots - 1] = s;
+}
+
+int red_grid(int64_t n) { return grid_for(n, kThreads * 4, kRedBlocks); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dtype, cudaStream_t s) {
+    const int grid = grid_for(H->Dup, 1, sm_count() * 16);
+    const DevSpin& up = H->dev[0];
+    const DevSpin& dn = H->dev[1];
+    if (dtype == HUB_F64) {
+        k_hv_reference<double><<<grid, kThreads, 0, s>>>((const double*)v, (double*)w, H->Dup, H->Ddn,
+            up.rowptr, up.ent, dn.rowptr, dn.ent, up.states, dn.states, -H->t, H->U);
+    } else {
+        k_hv_reference<float><<<grid, kThreads, 0, s>>>((const float*)v, (float*)w, H->Dup, H->Ddn,
+            up.rowptr, up.ent, dn.rowptr, dn.ent, up.states, dn.states, (float)-H->t, (float)H->U);
+    }
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
+                   cudaStream_t s) {
+    const DevSpin& up = H->dev[0];
+    const DevSpin& dn = H->dev[1];
+    const int grid = grid_for(H->Dup, 1, sm_count() * 16);
+    if (dtype == HUB_F32) {
+        if (w_old != nullptr || beta != 0.0) return fail(HUB_EINVAL, "f32 fused step not available");
+        k_hv_reference<float><<<grid, kThreads, 0, s>>>((const float*)v, (float*)w, H->Dup, H->Ddn,
+            up.rowptr, up.ent, dn.rowptr, dn.ent, up.states, dn.states, (float)-H->t, (float)H->U);
+        HUB_CUDA(cudaGetLastError());
+        count_launches(1);
+        return HUB_OK;
+    }
+    const size_t need = (size_t)H->D * sizeof(int2);
+    if (H->fx_bytes < need) return fail(HUB_ENOMEM, "fixed-point scratch not allocated");
+    int* emax = H->status;
+    HUB_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
+    const int g2 = grid_for(H->D, kThreads * 8, sm_count() * 8);
+    k_max_exponent<<<g2, kThreads, 0, s>>>((const double*)v, H->D, emax);
+    k_to_fixed<<<g2, kThreads, 0, s>>>((const double*)v, (int2*)H->fx_scratch, H->D, emax);
+    k_hv_fixed<<<grid, kThreads, 0, s>>>((const int2*)H->fx_scratch, (const double*)v, (double*)w,
+        (const double*)w_old, beta, H->Dup, H->Ddn, up.rowptr, up.ent, dn.rowptr, dn.ent,
+        up.states, dn.states, -H->t, H->U, emax);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(3);
+    return HUB_OK;
+}
+
+int launch_dot(const hubbard_sector*, const void* x, const void* y, int64_t n, int dtype, double* partials,
+               cudaStream_t s) {
+    const int g = red_grid(n);
+    if (dtype == HUB_F64) k_dot<double><<<g, kThreads, 0, s>>>((const double*)x, (const double*)y, n, partials);
+    else k_dot<float><<<g, kThreads, 0, s>>>((const float*)x, (const float*)y, n, partials);
+    k_finish_sum<<<1, 1024, 0, s>>>(partials, g);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(2);
+    return HUB_OK;
+}
+
+int reduce_partials_host(double* partials, cudaStream_t s, double* out) {
+    HUB_CUDA(cudaMemcpyAsync(out, partials + (kRedSlots - 1), sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+}
+
+int launch_axpy(double a, const void* x, void* y, int64_t n, int dtype, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    if (dtype == HUB_F64) k_axpy<double><<<g, kThreads, 0, s>>>(a, (const double*)x, (double*)y, n);
+    else k_axpy<float><<<g, kThreads, 0, s>>>((float)a, (const float*)x, (float*)y, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, double* partials, cudaStream_t s) {
+    const int g = red_grid(n);
+    if (dtype == HUB_F64) k_axpy_nrm2<double><<<g, kThreads, 0, s>>>(a, (const double*)x, (double*)y, n, partials);
+    else k_axpy_nrm2<float><<<g, kThreads, 0, s>>>((float)a, (const float*)x, (float*)y, n, partials);
+    k_finish_sum<<<1, 1024, 0, s>>>(partials, g);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(2);
+    return HUB_OK;
+}
+
+int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    if (dtype == HUB_F64) k_scale<double><<<g, kThreads, 0, s>>>(a, (double*)y, n);
+    else k_scale<float><<<g, kThreads, 0, s>>>((float)a, (float*)y, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double inv_norm, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    if (dtype == HUB_F64) k_copy_scale<double><<<g, kThreads, 0, s>>>((const double*)x, (double*)y, n, inv_norm);
+    else k_copy_scale<float><<<g, kThreads, 0, s>>>((const float*)x, (float*)y, n, (float)inv_norm);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+}  // namespace hub

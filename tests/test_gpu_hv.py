@@ -1,0 +1,220 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (written here, derived in the design doc):
+  * tables: bit-exact;
+  * binary64 H*v: max-abs error <= 1e-12 * |v|_2 * max(1, |t|);
+  * binary32 H*v: max-abs error <= 4e-7 * (W_up + W_dn + 1) * max(|t|, |U| Ns, 1) * max|v|;
+  * ground-state energy: relative error <= 1e-9.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import paper_1204_3425_gb300 as hub
+from oracle.basis import Sector
+from oracle.lanczos import ground_energy_dense, lanczos_plain
+from workload import lattice_by_name, start_vector
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_3425_gb300 import build
+    build.build()
+    hub.load_library()
+    return torch.device("cuda:0")
+
+
+# (lattice, N_up, N_dn, t, U): paper sizes, edge fillings, degenerate cases, ragged rows
+SMALL = [
+    ("ring8", 4, 4, 1.0, 4.0), ("ring4", 2, 3, 1.7, 0.0), ("sq3x2", 2, 4, 1.0, 3.0), ("sq3x3", 4, 5, 0.9, 7.0),
+    ("sq4x2", 3, 5, 1.0, 2.0), ("ring6", 0, 3, 1.0, 2.0), ("ring6", 6, 2, 1.0, 2.0), ("ring5", 5, 5, 1.0, 2.0),
+    ("ring6", 3, 3, 0.0, 4.0), ("ring7", 3, 2, 1.0, 0.0), ("dimer", 1, 1, 1.0, 4.0), ("ring10", 5, 4, 1.0, 5.0),
+    ("sq4x3", 3, 2, 1.0, 6.0), ("ring9", 1, 8, 2.5, 1.5), ("sq4x4", 2, 1, 1.0, 8.0),
+]
+
+
+def _sector(name, nup, ndn, t, U):
+    ns, bonds = lattice_by_name(name)
+    return hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U), Sector(ns, bonds, nup, ndn, t, U)
+
+
+@pytest.mark.parametrize("case", SMALL[:6] + [("sq4x4", 8, 5, 1.0, 1.0)])
+def test_device_tables_bit_exact(dev, case):
+    H, S = _sector(*case)
+    for spin in (0, 1):
+        got = hub.hubbard_export_tables(H, spin)
+        ref = S.spin_table(spin)
+        for g, r in zip(got, ref):
+            assert np.array_equal(g, r)
+
+
+@pytest.mark.parametrize("case", SMALL)
+@pytest.mark.parametrize("path", ["fast", "reference"])
+def test_hv_f64(dev, case, path):
+    H, S = _sector(*case)
+    t = case[3]
+    v = start_vector(S.D, seed=77)
+    ref = S.explicit() @ v
+    vd = torch.from_numpy(v).to(dev)
+    w = torch.full_like(vd, np.nan)
+    (hub.hubbard_apply if path == "fast" else hub.hubbard_apply_reference)(H, vd, w)
+    got = w.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-12 * np.linalg.norm(v) * max(1.0, abs(t))
+
+
+@pytest.mark.parametrize("case", SMALL)
+def test_hv_f32(dev, case):
+    H, S = _sector(*case)
+    name, nup, ndn, t, U = case
+    v = start_vector(S.D, seed=78).astype(np.float32)
+    ref = S.explicit() @ v.astype(np.float64)
+    vd = torch.from_numpy(v).to(dev)
+    w = torch.full_like(vd, np.nan)
+    hub.hubbard_apply(H, vd, w)
+    tol = 4e-7 * (H.Wup + H.Wdn + 1) * max(abs(t), abs(U) * S.ns, 1.0) * np.abs(v).max()
+    assert np.abs(w.cpu().numpy() - ref).max() <= tol
+
+
+@pytest.mark.parametrize("case", [("ring4", 2, 3, 1.7, 2.0), ("sq3x2", 2, 2, 1.0, 3.0), ("ring6", 2, 3, 0.8, 5.5)])
+def test_hv_basis_vectors_exact(dev, case):
+    # H e_J is column J of H; every entry is exactly -t*sign or U*n
+    H, S = _sector(*case)
+    Hd = S.dense()
+    for J in range(S.D):
+        e = torch.zeros(S.D, dtype=torch.float64, device=dev)     # fresh, 16-byte aligned
+        e[J] = 1.0
+        w = torch.empty(S.D, dtype=torch.float64, device=dev)
+        hub.hubbard_apply(H, e, w)
+        assert np.array_equal(w.cpu().numpy(), Hd[:, J]), J
+
+
+def test_config1_hv_lanczos_and_alpha_beta(dev):
+    """Ring 8, (4,4), t=1, U=4, binary64, 100 Lanczos steps from the seeded start."""
+    H, S = _sector("ring8", 4, 4, 1.0, 4.0)
+    Hx = S.explicit()
+    v0 = start_vector(S.D, seed=1234)
+    f = v0 / np.linalg.norm(v0)
+    fd = torch.from_numpy(f).to(dev)
+    w = torch.empty_like(fd)
+    hub.hubbard_apply(H, fd, w)
+    assert np.abs(w.cpu().numpy() - Hx @ f).max() <= 1e-12
+    r = hub.lanczos_ground_state(H, torch.from_numpy(v0).to(dev), 100, 0.0)
+    g = json.load(open(os.path.join(GOLD, "ring8_n4_4_U4.json")))
+    assert r["iters"] == 100
+    assert abs(r["energy"] - g["e0_dense"]) <= 1e-9 * abs(g["e0_dense"])
+    ro = lanczos_plain(lambda x: Hx @ x, v0, 20)
+    np.testing.assert_allclose(r["alpha"][:20], ro["a"], rtol=1e-10)
+    np.testing.assert_allclose(r["beta"][:20], ro["b"], rtol=1e-10)
+
+
+def test_lanczos_step_matches_oracle(dev):
+    H, S = _sector("sq3x3", 3, 4, 1.0, 5.0)
+    Hx = S.explicit()
+    rng = np.random.default_rng(3)
+    f = rng.uniform(-1, 1, S.D)
+    f /= np.linalg.norm(f)
+    g = rng.uniform(-1, 1, S.D)
+    beta = 1.37
+    q = Hx @ f - beta * g
+    a = q @ f
+    q -= a * f
+    b = np.linalg.norm(q)
+    fd, gd = torch.from_numpy(f).to(dev), torch.from_numpy(g).to(dev)
+    ag, bg = hub.hubbard_lanczos_step(H, fd, gd, beta)
+    assert ag == pytest.approx(a, rel=1e-12) and bg == pytest.approx(b, rel=1e-12)
+    assert np.abs(gd.cpu().numpy() - q / b).max() <= 1e-12
+
+
+def test_lanczos_breakdown_tiny_sector(dev):
+    H, S = _sector("ring4", 1, 1, 1.0, 2.0)
+    r = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(S.D, seed=5)).to(dev), 50, 1e-10)
+    assert r["breakdown"] and r["iters"] <= S.D
+    assert r["energy"] == pytest.approx(ground_energy_dense(S.dense()), abs=1e-12)
+
+
+@pytest.mark.parametrize("case", [("sq3x3", 4, 4, 1.0, 6.0), ("ring10", 5, 5, 1.0, 3.0), ("sq4x3", 2, 3, 1.0, 9.0)])
+def test_lanczos_energy_small(dev, case):
+    H, S = _sector(*case)
+    from scipy.sparse.linalg import eigsh
+    e_ref = float(eigsh(S.explicit(), k=1, which="SA", tol=1e-14, v0=start_vector(S.D, seed=9))[0][0])
+    r = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(S.D, seed=1234)).to(dev), 1000, 1e-10)
+    assert r["status"] == hub.HUB_OK
+    assert abs(r["energy"] - e_ref) <= 1e-9 * max(abs(e_ref), 1.0)
+
+
+# ---- the 4x4 (8,8) sector: D = 1.66e8 ----------------------------------------
+@pytest.fixture(scope="module")
+def sq4x4(dev):
+    H, S = _sector("sq4x4", 8, 8, 1.0, 8.0)
+    v0 = start_vector(S.D, seed=1234)
+    return H, S, v0
+
+
+def test_config2_sampled_rows(dev, sq4x4):
+    H, S, v0 = sq4x4
+    f = v0 / np.linalg.norm(v0)
+    fd = torch.from_numpy(f).to(dev)
+    w = torch.empty_like(fd)
+    hub.hubbard_apply(H, fd, w)
+    rng = np.random.default_rng(1)
+    J = np.concatenate([rng.integers(0, S.D, 4000), np.arange(64), S.D - 1 - np.arange(64)])
+    ref = S.rows_of_hv(J, f)
+    got = w.cpu().numpy()[J]
+    assert np.abs(got - ref).max() <= 1e-12
+    # the reference kernel over the whole vector (property: both GPU paths agree)
+    w2 = torch.empty_like(fd)
+    hub.hubbard_apply_reference(H, fd, w2)
+    assert (w - w2).abs().max().item() <= 1e-12
+    del fd, w, w2
+
+
+def test_config2_ground_state(dev, sq4x4):
+    H, S, v0 = sq4x4
+    g = json.load(open(os.path.join(GOLD, "sq4x4_n8_8_U8.json")))
+    r = hub.lanczos_ground_state(H, torch.from_numpy(v0).to(dev), 600, 1e-10)
+    assert r["status"] == hub.HUB_OK and r["residual"] < 1e-10
+    assert abs(r["energy"] - g["e0"]) <= 1e-9 * abs(g["e0"])
+
+
+# ---- vector operations --------------------------------------------------------
+@pytest.mark.parametrize("n", [1, 7, 1000, 1 << 20, 3_000_017])
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_vec_ops(dev, n, dtype):
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    x = start_vector(n, seed=1).astype(np.float64)
+    y = start_vector(n, seed=2).astype(np.float64)
+    if dtype == "f32":
+        x, y = x.astype(np.float32).astype(np.float64), y.astype(np.float32).astype(np.float64)
+    xd = torch.from_numpy(x).to(dev, tdt)
+    yd = torch.from_numpy(y).to(dev, tdt)
+    assert hub.hubbard_vec_dot(xd, yd) == pytest.approx(float(x @ y), rel=1e-12, abs=1e-12)
+    assert hub.hubbard_vec_nrm2(xd) == pytest.approx(float(np.linalg.norm(x)), rel=1e-12)
+    hub.hubbard_vec_axpy(-0.75, xd, yd)
+    tol = 1e-15 if dtype == "f64" else 2e-7
+    assert np.abs(yd.cpu().double().numpy() - (y - 0.75 * x)).max() <= tol * 2
+
+
+def test_argument_errors(dev):
+    H, S = _sector("ring6", 3, 3, 1.0, 2.0)
+    buf = torch.zeros(S.D + 2, dtype=torch.float64, device=dev)
+    w = torch.zeros(S.D, dtype=torch.float64, device=dev)
+    with pytest.raises(hub.HubError) as e:
+        hub.hubbard_apply(H, buf[1:S.D + 1], w)                     # 8-byte offset: misaligned
+    assert e.value.code == hub.HUB_EINVAL
+    with pytest.raises(hub.HubError) as e:
+        hub.hubbard_apply(H, buf[:S.D], buf[2:S.D + 2])              # overlap
+    assert e.value.code == hub.HUB_EINVAL
+    with pytest.raises(hub.HubError):
+        hub.hubbard_sector_create(4, [(0, 1), (1, 0)], 1, 1, 1.0, 1.0)
+    with pytest.raises(hub.HubError):
+        hub.hubbard_sector_create(4, [(0, 1)], 1, 1, float("nan"), 1.0)
