@@ -136,9 +136,16 @@ def test_lanczos_step_matches_oracle(dev):
 
 
 def test_lanczos_breakdown_tiny_sector(dev):
+    # one electron on a 4-ring: eigenvalues -2, 0, 0, 2, so the Krylov space
+    # of any start vector has dimension 3 and step 3 breaks down (b_4 ~ 0)
+    H, S = _sector("ring4", 1, 0, 1.0, 2.0)
+    r = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(S.D, seed=5)).to(dev), 50, 0.0)
+    assert r["breakdown"] and r["iters"] == 3
+    assert r["energy"] == pytest.approx(-2.0, abs=1e-12)
+    # a 16-state sector: iterations are capped at D, the energy is exact
     H, S = _sector("ring4", 1, 1, 1.0, 2.0)
-    r = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(S.D, seed=5)).to(dev), 50, 1e-10)
-    assert r["breakdown"] and r["iters"] <= S.D
+    r = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(S.D, seed=5)).to(dev), 50, 0.0)
+    assert r["iters"] <= S.D
     assert r["energy"] == pytest.approx(ground_energy_dense(S.dense()), abs=1e-12)
 
 
