@@ -128,6 +128,33 @@ int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Binary64 w = H v that allocates no device memory.
+ *
+ * The paper has no counterpart; this entry point exists for callers that
+ * cannot call cudaMalloc at the point where they need H*v: code that runs
+ * while another framework owns the device allocator, code under a hard
+ * memory budget, or hot loops that must never reach the allocator.  Such a
+ * caller creates the handle beforehand (hubbard_sector_create allocates the
+ * tables) and then calls this function with its own v and w.
+ *
+ * It runs the binary64 fixed-point kernels of hubbard_apply, but its scratch
+ * (the fixed-point copy of v and one exponent word) lives in a file-scope
+ * device array of HUBBARD_NOALLOC_MAX_ELEMS * 8 bytes (16 MiB) that every
+ * GPU loading the library holds until process exit.
+ *   - D_up * D_dn above HUBBARD_NOALLOC_MAX_ELEMS: HUB_EINVAL, nothing runs.
+ *   - The first call on a device (with that device current) looks up the
+ *     array's device address with cudaGetSymbolAddress; make that first call
+ *     before any stream capture.
+ *   - Every call, from any thread or stream, shares the one array and leaves
+ *     its contents behind; calls whose GPU work overlaps (concurrent streams
+ *     or threads) race on it and must be serialised by the caller.
+ * Same accuracy and argument rules as hubbard_apply with HUB_F64.
+ * Asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+#define HUBBARD_NOALLOC_MAX_ELEMS (1 << 21)
+int hubbard_apply_noalloc(hubbard_t H, const void* v, void* w, void* stream);
+
+/* ---------------------------------------------------------------------------
  * Lanczos vector operations (Algorithm 1, lines 5-7), n elements of dtype,
  * results accumulated in binary64 in a fixed reduction order (deterministic
  * for a given n and dtype).  Device vectors; host scalar results; these

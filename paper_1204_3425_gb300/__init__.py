@@ -42,6 +42,7 @@ SIGNATURES = {
     "hubbard_export_tables": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P]),
     "hubbard_apply": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_apply_reference": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "hubbard_apply_noalloc": (ctypes.c_int, [P, P, P, P]),
     "hubbard_vec_dot": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_nrm2": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_axpy": (ctypes.c_int, [D, P, P, I64, ctypes.c_int, P]),
@@ -173,6 +174,22 @@ def hubbard_apply(H, v, w, stream=None):
 
 def hubbard_apply_reference(H, v, w, stream=None):
     _check(load_library().hubbard_apply_reference(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
+    return w
+
+
+HUBBARD_NOALLOC_MAX_ELEMS = 1 << 21
+
+
+def hubbard_apply_noalloc(H, v, w, stream=None):
+    """Binary64 w = H v through the entry point that allocates no device memory.
+
+    For callers that cannot call cudaMalloc when they need H*v (another
+    framework owns the allocator, a hard memory budget, or a hot loop that
+    must not reach the allocator).  Its scratch is a fixed 16 MiB device array
+    shared by all calls: sectors above HUBBARD_NOALLOC_MAX_ELEMS are rejected,
+    and calls whose GPU work overlaps race on the array.
+    """
+    _check(load_library().hubbard_apply_noalloc(H.handle, _ptr(v), _ptr(w), _stream(stream)))
     return w
 
 

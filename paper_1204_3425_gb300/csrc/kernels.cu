@@ -7,6 +7,7 @@
 //
 // Packed hop entry: (target << 1) | (sign < 0); <target|H_sigma|src> = -t*sign.
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "internal.h"
@@ -319,3 +320,84 @@ int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double i
 }
 
 }  // namespace hub
+
+// ---------------------------------------------------------------------------
+// hubbard_apply_noalloc: binary64 H*v with its scratch in a file-scope device
+// array, for callers that cannot allocate device memory at call time.
+namespace hub {
+
+static __device__ __align__(256) int2 g_noalloc_fixed[HUBBARD_NOALLOC_MAX_ELEMS];
+static __device__ __align__(256) int g_noalloc_emax[64];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+struct NoAllocAddr {
+    std::once_flag once;
+    int rc = HUB_OK;
+    int2* fixed = nullptr;
+    int* emax = nullptr;
+};
+NoAllocAddr g_noalloc_addr[kMaxDevices];
+
+// Looks up, once per device with that device current, the device addresses
+// of the scratch arrays.  In host code the array names are host-side stand-
+// ins, so kernels must be given these looked-up addresses instead.
+int noalloc_addresses(int dev, int2** fixed, int** emax) {
+    if (dev < 0 || dev >= kMaxDevices) return fail(HUB_EINVAL, "device index out of range for the no-allocation path");
+    NoAllocAddr& a = g_noalloc_addr[dev];
+    std::call_once(a.once, [&a]() {
+        cudaError_t e = cudaGetSymbolAddress((void**)&a.fixed, g_noalloc_fixed);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void**)&a.emax, g_noalloc_emax);
+        if (e != cudaSuccess) {
+            a.rc = cuda_fail(e, "cudaGetSymbolAddress(no-allocation scratch)");
+            a.fixed = nullptr;
+            a.emax = nullptr;
+        }
+    });
+    if (a.rc != HUB_OK) return fail(a.rc, "no-allocation scratch address lookup failed on this device");
+    *fixed = a.fixed;
+    *emax = a.emax;
+    return HUB_OK;
+}
+
+}  // namespace
+}  // namespace hub
+
+extern "C" int hubbard_apply_noalloc(hubbard_t H, const void* v, void* w, void* stream) {
+    using namespace hub;
+    clear_error();
+    if (H == nullptr) return fail(HUB_EINVAL, "null handle");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != H->device)
+        return fail(HUB_EINVAL, "handle was created on another device");
+    if (v == nullptr || w == nullptr) return fail(HUB_EINVAL, "null vector");
+    if ((reinterpret_cast<uintptr_t>(v) & 15u) || (reinterpret_cast<uintptr_t>(w) & 15u))
+        return fail(HUB_EINVAL, "vectors must be 16-byte aligned");
+    const size_t bytes = (size_t)H->D * sizeof(double);
+    const char* a = (const char*)v;
+    const char* b = (const char*)w;
+    if (a < b + bytes && b < a + bytes) return fail(HUB_EINVAL, "v and w overlap");
+    if (H->D > (int64_t)HUBBARD_NOALLOC_MAX_ELEMS)
+        return fail(HUB_EINVAL, "sector dimension exceeds HUBBARD_NOALLOC_MAX_ELEMS (2^21) of the no-allocation path");
+    if (H->host[0].W + H->host[1].W > 127)
+        return fail(HUB_EINVAL, "more than 127 hops per state: not supported by the no-allocation path");
+    int2* fixed = nullptr;
+    int* emax = nullptr;
+    int rc = noalloc_addresses(dev, &fixed, &emax);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const DevSpin& up = H->dev[0];
+    const DevSpin& dn = H->dev[1];
+    // the exponent word keeps the previous call's value: it must restart at 0
+    HUB_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
+    const int g2 = grid_for(H->D, kThreads * 8, sm_count() * 8);
+    const int grid = grid_for(H->Dup, 1, sm_count() * 16);
+    k_max_exponent<<<g2, kThreads, 0, s>>>((const double*)v, H->D, emax);
+    k_to_fixed<<<g2, kThreads, 0, s>>>((const double*)v, fixed, H->D, emax);
+    k_hv_fixed<<<grid, kThreads, 0, s>>>(fixed, (const double*)v, (double*)w, nullptr, 0.0, H->Dup, H->Ddn,
+        up.rowptr, up.ent, dn.rowptr, dn.ent, up.states, dn.states, -H->t, H->U, emax);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(3);
+    return HUB_OK;
+}
