@@ -34,10 +34,33 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 METRIC = "H·v GB/s vs HBM peak; ground-state solves/s, p50/p99 at ≤1e-9 rel"
-WORKLOAD = dict(workload="sq4x4_n8_8_U8_f64", lattice="4x4 periodic square (32 bonds)", nup=8, ndn=8,
-                t=1.0, U=8.0, dim=12870 * 12870, vector_bytes=12870 * 12870 * 8, seed=1234,
-                l2_policy="inputs larger than L2 (1.3 GB vectors vs 129 MB L2); no flush")
+# name -> (lattice, N_up, N_dn, U, dtype); the first is the benchmarked workload,
+# the others are smaller cases of the same kernels for profiling
+WORKLOADS = {
+    "sq4x4_n8_8_U8_f64": ("sq4x4", 8, 8, 8.0, "f64"),
+    "sq4x4_n8_8_U8_f32": ("sq4x4", 8, 8, 8.0, "f32"),
+    "sq4x4_n6_6_U8_f64": ("sq4x4", 6, 6, 8.0, "f64"),
+    "sq4x4_n6_6_U8_f32": ("sq4x4", 6, 6, 8.0, "f32"),
+}
 GOLDEN = os.path.join(ROOT, "tests", "golden", "sq4x4_n8_8_U8.json")
+
+
+def workload_config(name):
+    from workload import lattice_by_name
+    lat, nup, ndn, U, dt = WORKLOADS[name]
+    ns, bonds = lattice_by_name(lat)
+    dup, ddn = math.comb(ns, nup), math.comb(ns, ndn)
+    s = 8 if dt == "f64" else 4
+    cfg = dict(workload=name, lattice=f"{lat} periodic ({len(bonds)} bonds)", nup=nup, ndn=ndn, t=1.0, U=U,
+               dim=dup * ddn, vector_bytes=dup * ddn * s, seed=1234,
+               l2_policy=("inputs larger than L2 (%.2f GB vectors vs 129 MB L2); no flush" % (dup * ddn * s / 1e9)))
+    return ns, bonds, nup, ndn, U, dt, cfg
+
+
+# DRAM bytes per hubbard_apply from the ncu capture summarised in
+# profiles/hv_f64_sq4x4_n6_6_phases_ncu.md (small case scaled by D to the bench
+# sector); must be set back to None whenever the H*v kernels change.
+TRAFFIC = {"sq4x4_n8_8_U8_f64": 9.17e9}
 
 
 def peaks():
@@ -70,7 +93,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "20"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
         except Exception:
@@ -131,13 +154,15 @@ def run_ours(args):
     hub.load_library()
     stream = torch.cuda.current_stream()
 
-    bonds = square(4, 4)
-    H = hub.hubbard_sector_create(16, bonds, 8, 8, 1.0, 8.0)
+    ns, bonds, nup, ndn, U, dts, cfg = workload_config(args.workload)
+    tdt = torch.float64 if dts == "f64" else torch.float32
+    esize = 8 if dts == "f64" else 4
+    H = hub.hubbard_sector_create(ns, bonds, nup, ndn, 1.0, U)
     D = H.D
     tables = sum(int(hub.load_library().hubbard_table_nnz(H.handle, s)) * 4 + (H.Dup if s == 0 else H.Ddn) * 12
                  for s in (0, 1))
-    nbytes = hv_bytes(D, tables)
-    v_host = torch.from_numpy(start_vector(D, seed=1234))
+    nbytes = hv_bytes(D, tables, esize)
+    v_host = torch.from_numpy(start_vector(D, seed=1234)).to(tdt)
     v_host /= v_host.norm()
     v_pin = v_host.pin_memory()
     v = v_pin.to(dev, non_blocking=True)
@@ -178,7 +203,7 @@ def run_ours(args):
     value = ws * nbytes * args.steps / (total_ms * 1e-3) / 1e9
 
     # ---- end to end through the C ABI with host buffers -------------------
-    w_pin = torch.empty(D, dtype=torch.float64).pin_memory()
+    w_pin = torch.empty(D, dtype=tdt).pin_memory()
     e2e_ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
     k_e2e = max(2, min(args.steps, 5))
     hub.hubbard_apply(H, v_pin.to(dev, non_blocking=True), w)
@@ -195,7 +220,7 @@ def run_ours(args):
 
     # ---- ground-state solves ----------------------------------------------
     golden = json.load(open(GOLDEN))["e0"]
-    n_solves = args.solves
+    n_solves = args.solves if args.workload == "sq4x4_n8_8_U8_f64" else 0
     lat, iters, errs = [], [], []
     ws_buf = torch.empty(hub.lanczos_workspace_bytes(H, hub.HUB_F64), dtype=torch.uint8, device=dev)
     v0 = torch.from_numpy(start_vector(D, seed=1234)).to(dev)
@@ -224,21 +249,22 @@ def run_ours(args):
     achieved = nbytes / (avg_kernel_ms * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "arith": "int32-pair fixed-point hop sums, binary64 storage and epilogue",
+        "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dts,
+        "arith": ("exact int32-pair fixed-point hop sums, binary64 storage and rounding" if dts == "f64"
+                  else "binary32"),
         "data": "synthetic (seeded SplitMix64 start vector)",
-        "config": dict(WORKLOAD, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single"),
+        "config": dict(cfg, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single"),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "peak_source": src,
+                     "traffic": TRAFFIC.get(args.workload), "peak_source": src,
                      "algorithmic_bytes_per_launch": nbytes,
-                     "kernel": "hubbard_apply (k_max_exponent + k_to_fixed + k_hv_fixed)"},
-        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * 8, "d2h_bytes_per_step": D * 8,
+                     "kernel": "hubbard_apply (row phase + up phase kernels)"},
+        "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * esize, "d2h_bytes_per_step": D * esize,
                 "ms_per_step": e2e_ms},
         "gpu_launches": int(launches),
         "clocks": clk,
         "solve": solve,
     }
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sq4x4_n8_8_U8_f64":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     H.close()
     if rank == 0:
@@ -296,7 +322,7 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded SplitMix64 start vector)",
-            "config": dict(WORKLOAD, step="one H*v (oracle Kronecker-sum, host cores)"),
+            "config": dict(workload_config("sq4x4_n8_8_U8_f64")[-1], step="one H*v (oracle Kronecker-sum, host cores)"),
             "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
                              "sample": f"{args.steps} full H*v calls on the 4x4 (8,8) sector"},
             "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -306,9 +332,10 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="sq4x4_n8_8_U8_f64")
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

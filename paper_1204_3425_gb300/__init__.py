@@ -43,6 +43,7 @@ SIGNATURES = {
     "hubbard_apply": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_apply_reference": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_apply_noalloc": (ctypes.c_int, [P, P, P, P]),
+    "hubbard_set_schedule": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "hubbard_vec_dot": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_nrm2": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_axpy": (ctypes.c_int, [D, P, P, I64, ctypes.c_int, P]),
@@ -175,6 +176,11 @@ def hubbard_apply(H, v, w, stream=None):
 def hubbard_apply_reference(H, v, w, stream=None):
     _check(load_library().hubbard_apply_reference(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
     return w
+
+
+def hubbard_set_schedule(H, vec_rows=0, vec_cols=0, ctas_rows=0, ctas_cols=0):
+    _check(load_library().hubbard_set_schedule(H.handle, int(vec_rows), int(vec_cols), int(ctas_rows),
+                                               int(ctas_cols)))
 
 
 HUBBARD_NOALLOC_MAX_ELEMS = 1 << 21

@@ -67,6 +67,16 @@ void free_dev(hubbard_sector* H) {
         cudaFree(d.ent);
         cudaFree(d.ell);
         cudaFree(d.cnt);
+        cudaFree(d.sell_off);
+        cudaFree(d.sell_cnt);
+        cudaFree(d.sell_ent);
+        cudaFree(d.blk_off);
+        cudaFree(d.blk_cnt);
+        cudaFree(d.ent16);
+        cudaFree(d.ent32);
+        cudaFree(d.pn_ptr);
+        cudaFree(d.pn_npos);
+        cudaFree(d.pn_list);
         d = DevSpin{};
     }
     cudaFree(H->fx_scratch);
@@ -89,7 +99,69 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
         for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
             ell[(size_t)c * (size_t)T.D + (size_t)r] = ent[(size_t)k];
     }
+    // warp-sliced ELL: group g = states 32g .. 32g+31, slots = max hops in the group
+    const int64_t groups = (T.D + 31) / 32;
+    std::vector<int64_t> soff((size_t)groups);
+    std::vector<int32_t> scnt((size_t)groups);
+    int64_t total = 0;
+    for (int64_t g = 0; g < groups; ++g) {
+        int32_t m = 0;
+        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) m = std::max(m, cnt[(size_t)r]);
+        soff[(size_t)g] = total;
+        scnt[(size_t)g] = m;
+        total += (int64_t)m * 32;
+    }
+    std::vector<uint32_t> sent((size_t)std::max<int64_t>(total, 1), 0u);   // padding: target 0, weight 0
+    for (int64_t r = 0; r < T.D; ++r) {
+        const int64_t g = r / 32, lane = r % 32;
+        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
+            sent[(size_t)(soff[(size_t)g] + (int64_t)c * 32 + lane)] =
+                ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
+    }
+    d.sell_entries = total;
+    // SELL-32/8: per group, blocks of 8 slots per lane, contiguous per lane
+    std::vector<int64_t> boff((size_t)groups);
+    std::vector<int32_t> bcnt((size_t)groups);
+    int64_t btotal = 0;
+    for (int64_t g = 0; g < groups; ++g) {
+        boff[(size_t)g] = btotal;
+        bcnt[(size_t)g] = (scnt[(size_t)g] + 7) / 8;
+        btotal += (int64_t)bcnt[(size_t)g] * 32 * 8;
+    }
+    std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), 0u);
+    for (int64_t r = 0; r < T.D; ++r) {
+        const int64_t g = r / 32, lane = r % 32;
+        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
+            bent[(size_t)(boff[(size_t)g] + ((int64_t)(c / 8) * 32 + lane) * 8 + c % 8)] =
+                ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
+    }
+    // sign-split list: +1 targets first, then -1 targets, each ascending
+    std::vector<int32_t> npos((size_t)T.D);
+    std::vector<uint32_t> pnl(T.tgt.size());
+    for (int64_t r = 0; r < T.D; ++r) {
+        int32_t o = T.rowptr[(size_t)r], np = 0;
+        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
+            if (T.sign[(size_t)k] > 0) { pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k]; ++np; }
+        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
+            if (T.sign[(size_t)k] < 0) pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k];
+        npos[(size_t)r] = np;
+    }
     int rc;
+    if ((rc = upload(&d.pn_ptr, T.rowptr.data(), T.rowptr.size()))) return rc;
+    if ((rc = upload(&d.pn_npos, npos.data(), npos.size()))) return rc;
+    if ((rc = upload(&d.pn_list, pnl.data(), pnl.size()))) return rc;
+    if ((rc = upload(&d.blk_off, boff.data(), boff.size()))) return rc;
+    if ((rc = upload(&d.blk_cnt, bcnt.data(), bcnt.size()))) return rc;
+    if (T.D < (1 << 14)) {
+        std::vector<uint16_t> e16(bent.size());
+        for (size_t i = 0; i < bent.size(); ++i) e16[i] = (uint16_t)bent[i];
+        if ((rc = upload(&d.ent16, e16.data(), e16.size()))) return rc;
+    } else {
+        if ((rc = upload(&d.ent32, bent.data(), bent.size()))) return rc;
+    }
+    if ((rc = upload(&d.sell_off, soff.data(), soff.size()))) return rc;
+    if ((rc = upload(&d.sell_cnt, scnt.data(), scnt.size()))) return rc;
+    if ((rc = upload(&d.sell_ent, sent.data(), sent.size()))) return rc;
     if ((rc = upload(&d.states, T.states.data(), T.states.size()))) return rc;
     if ((rc = upload(&d.rowptr, T.rowptr.data(), T.rowptr.size()))) return rc;
     if ((rc = upload(&d.ent, ent.data(), ent.size()))) return rc;
@@ -98,8 +170,9 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     return HUB_OK;
 }
 
+// binary64: row-phase sums Y (int64) + fixed-point copy X (int2); binary32 uses the first half
 int ensure_fx_scratch(hubbard_sector* H) {
-    const size_t need = (size_t)H->D * 8;
+    const size_t need = (size_t)H->D * 16;
     if (H->fx_bytes >= need) return HUB_OK;
     cudaFree(H->fx_scratch);
     H->fx_scratch = nullptr;
@@ -276,8 +349,22 @@ int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream) 
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
     if (dtype == HUB_F64 && !fixed_point_ok(H)) return launch_hv_reference(H, v, w, dtype, s);
-    if (dtype == HUB_F64 && (rc = ensure_fx_scratch(H))) return rc;
-    return launch_hv_fast(H, v, w, dtype, 0.0, nullptr, s);
+    if ((rc = ensure_fx_scratch(H))) return rc;
+    return launch_hv_fast(H, v, w, dtype, 0.0, nullptr, 0, s);
+}
+
+int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols) {
+    clear_error();
+    if (H == nullptr) return fail(HUB_EINVAL, "null handle");
+    auto ok_vec = [](int v) { return v == 0 || v == 1 || v == 2 || v == 4; };
+    auto ok_cta = [](int c) { return c >= 0 && c <= 2; };
+    if (!ok_vec(vec_rows) || !ok_vec(vec_cols) || !ok_cta(ctas_rows) || !ok_cta(ctas_cols))
+        return fail(HUB_EINVAL, "schedule: vec in {0,1,2,4}, ctas in {0,1,2}");
+    H->vec_rows = vec_rows;
+    H->vec_cols = vec_cols;
+    H->ctas_rows = ctas_rows;
+    H->ctas_cols = ctas_cols;
+    return HUB_OK;
 }
 
 int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream) {
@@ -338,16 +425,15 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
 }
 
 // One Lanczos step (Eqs. split1 + Algorithm 1 lines 5-11) on caller vectors.
+// fixed_emax: 1023 when f and g are known to have norm <= 1 (inside the
+// solver), 0 to derive the fixed-point scale from the data.
 static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
-                             double* alpha, double* beta_next, bool normalise) {
+                             double* alpha, double* beta_next, bool normalise, int fixed_emax) {
     int rc;
-    if (dtype == HUB_F64 && fixed_point_ok(H)) {
-        // g <- H f - beta_j g, fused
-        if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, s))) return rc;
-    } else {
-        // g <- -beta_j g ; g <- g + H f  (reference kernel needs a separate output)
-        return fail(HUB_EINVAL, "lanczos step: only the binary64 fixed-point path is available");
-    }
+    if (dtype == HUB_F64 && !fixed_point_ok(H))
+        return fail(HUB_EINVAL, "lanczos step: more than 127 hops per state is not supported");
+    // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels
+    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s))) return rc;
     if ((rc = launch_dot(H, g, f, H->D, dtype, H->red, s))) return rc;
     double a = 0.0;
     if ((rc = reduce_partials_host(H->red, s, &a))) return rc;
@@ -368,9 +454,9 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
     int rc = check_apply(H, f, g, dtype);
     if (rc) return rc;
     if (alpha == nullptr || beta_next == nullptr) return fail(HUB_EINVAL, "null output");
-    if (dtype == HUB_F64 && (rc = ensure_fx_scratch(H))) return rc;
+    if ((rc = ensure_fx_scratch(H))) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = lanczos_step_impl(H, f, g, beta_j, dtype, s, alpha, beta_next, true);
+    rc = lanczos_step_impl(H, f, g, beta_j, dtype, s, alpha, beta_next, true, 0);
     if (rc == HUB_OK) {
         cudaError_t e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) return cuda_fail(e, "lanczos step");
@@ -381,9 +467,8 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
 size_t lanczos_workspace_bytes(hubbard_t H, int dtype) {
     if (H == nullptr || (dtype != HUB_F64 && dtype != HUB_F32)) return 0;
     const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
-    size_t total = 2 * vec;
-    if (dtype == HUB_F64) total += align_up((size_t)H->D * 8, 256);   // fixed-point copy
-    return total;
+    // two Lanczos vectors + the H*v scratch (binary64: int64 row sums + fixed-point copy)
+    return 2 * vec + align_up((size_t)H->D * 16, 256);
 }
 
 int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype, void* workspace,
@@ -400,8 +485,8 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u))
         return fail(HUB_EINVAL, "workspace null or not 256-byte aligned");
     if (ws_bytes < lanczos_workspace_bytes(H, dtype)) return fail(HUB_ENOMEM, "workspace too small");
-    if (dtype != HUB_F64 || !fixed_point_ok(H))
-        return fail(HUB_EINVAL, "lanczos: only the binary64 fixed-point path is available");
+    if (dtype == HUB_F64 && !fixed_point_ok(H))
+        return fail(HUB_EINVAL, "lanczos: more than 127 hops per state is not supported");
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
     char* ws = (char*)workspace;
@@ -411,7 +496,7 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     void* saved_fx = H->fx_scratch;
     size_t saved_bytes = H->fx_bytes;
     H->fx_scratch = ws + 2 * vec;
-    H->fx_bytes = (size_t)H->D * 8;
+    H->fx_bytes = (size_t)H->D * 16;
     auto restore = [&]() {
         H->fx_scratch = saved_fx;
         H->fx_bytes = saved_bytes;
@@ -441,7 +526,7 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     bool broke = false, converged = false;
     for (int j = 0; j < m_cap; ++j) {
         double aj = 0.0, bn = 0.0;
-        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false))) {
+        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023))) {
             restore();
             return rc;
         }

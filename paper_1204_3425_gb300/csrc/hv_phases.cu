@@ -1,0 +1,698 @@
+// Two-phase H*v with shared-memory staging (Sec. 4.3 restated for sm_103a).
+//
+// V is the row-major D_up x D_dn matrix of Fig. 2.  The Kronecker sum of
+// Eq. (H-Kroneckersum) splits H*v into
+//   row phase    Y[u, :] = sum over down-hops inside row u        (Algorithm 3)
+//   column phase W[:, c] = sum over up-hops inside column c + Y[:, c]
+//                          + U * popcount(s_up & s_dn) * V[:, c]   (Algorithms 2, 4)
+// Each phase stages whole rows (row phase) or whole column strips (column
+// phase) of V in shared memory, so every gathered operand comes from shared
+// memory.  Rows per block / columns per strip (VEC) share one read of the
+// warp-sliced hop table: one 16-byte shared load feeds VEC outputs.
+//
+// Binary64 path: every element is rounded once to the fixed-point grid 2^-k
+// (k = 1070 - emax, emax = biased exponent bound of max|v|) and held as
+// (lo, hi) int32 words, X = hi * 2^24 + lo; hop sums are exact integer sums.
+// The column phase forms, exactly in 128-bit integers,
+//   T*A + X_own*B[n] + G*Bbeta,   A = -t 2^m, B[n] = U n 2^m, Bbeta = -beta 2^m
+// (T = hop sum, G = fixed-point w_old) and rounds it once to binary64: the
+// FP64 pipe (1.7 op/clk/SM on this part) is not used per element.
+#include <cstdint>
+#include <cmath>
+#include <type_traits>
+#include <cuda_runtime.h>
+
+#include "internal.h"
+
+namespace hub {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// binary64 <-> fixed point
+__device__ __forceinline__ void fx_split(double x, int emax, int& lo, int& hi) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    if (e != 0) mant |= (1ull << 52);
+    const int ee = e > 0 ? e : 1;
+    const int rs = max(emax - ee + 5, 1);             // >= 5 whenever |x| < 2^(emax-1022)
+    long long X = (rs >= 60) ? 0 : (long long)((mant + (1ull << (rs - 1))) >> rs);
+    if (b >> 63) X = -X;
+    lo = (int)(X & 0xFFFFFF);
+    hi = (int)(X >> 24);
+}
+
+__device__ __forceinline__ long long fx_join(int lo, int hi) { return ((long long)hi << 24) + (long long)lo; }
+
+struct I128 {
+    unsigned long long lo;
+    long long hi;
+};
+
+__device__ __forceinline__ void mac128(I128& acc, long long a, long long b) {
+    const unsigned long long plo = (unsigned long long)a * (unsigned long long)b;
+    const long long phi = __mul64hi(a, b);
+    const unsigned long long nlo = acc.lo + plo;
+    acc.hi += phi + (nlo < plo ? 1 : 0);
+    acc.lo = nlo;
+}
+
+// (hi * 2^64 + lo) * 2^e2, rounded to nearest (ties to even)
+__device__ __forceinline__ double i128_to_double(I128 v, int e2) {
+    unsigned long long lo = v.lo;
+    unsigned long long hi = (unsigned long long)v.hi;
+    const bool neg = v.hi < 0;
+    if (neg) {
+        lo = ~lo + 1ull;
+        hi = ~hi + (lo == 0 ? 1ull : 0ull);
+    }
+    if (hi == 0 && lo == 0) return 0.0;
+    const int lz = hi ? __clzll((long long)hi) : 64 + __clzll((long long)lo);
+    unsigned long long nh, nl;
+    if (lz == 0) {
+        nh = hi;
+        nl = lo;
+    } else if (lz < 64) {
+        nh = (hi << lz) | (lo >> (64 - lz));
+        nl = lo << lz;
+    } else {
+        nh = lo << (lz - 64);
+        nl = 0;
+    }
+    unsigned long long mant = nh >> 11;               // 53 bits, leading one at bit 52
+    const unsigned long long rem = nh & 0x7FFull;
+    const bool up = (rem > 0x400ull) || (rem == 0x400ull && (nl != 0 || (mant & 1ull)));
+    mant += up ? 1ull : 0ull;
+    int ex = 127 - lz + e2;
+    if (mant == (1ull << 53)) {
+        mant >>= 1;
+        ++ex;
+    }
+    const int be = ex + 1023;
+    if (be <= 0 || be >= 2047) {
+        const double m = (double)mant;                // exact
+        return ldexp(neg ? -m : m, ex - 52);
+    }
+    unsigned long long bits = ((unsigned long long)be << 52) | (mant & ((1ull << 52) - 1));
+    if (neg) bits |= (1ull << 63);
+    return __longlong_as_double((long long)bits);
+}
+
+// P * 2^e2, correctly rounded: I2F.F64 rounds once, the power of two is
+// applied exactly to the exponent field (ldexp only off the normal range)
+__device__ __forceinline__ double i64_scaled_to_double(long long P, int e2) {
+    if (P == 0) return 0.0;
+    const double d = __ll2double_rn(P);
+    const long long bits = __double_as_longlong(d);
+    const int be = (int)((bits >> 52) & 0x7FF) + e2;
+    if (be <= 0 || be >= 2047) return ldexp(d, e2);
+    return __longlong_as_double(bits + ((long long)e2 << 52));
+}
+
+__device__ __forceinline__ int hop_sign(uint32_t e) { return (int)(e & 1u) - (int)(e & 2u); }
+
+template <int VEC> struct FxVec;
+template <> struct FxVec<1> { using T = int2; };
+template <> struct FxVec<2> { using T = int4; };
+
+template <int VEC> struct F32Vec;
+template <> struct F32Vec<1> { using T = float; };
+template <> struct F32Vec<2> { using T = float2; };
+template <> struct F32Vec<4> { using T = float4; };
+
+__device__ __forceinline__ float comp(float x, int) { return x; }
+__device__ __forceinline__ float comp(float2 x, int i) { return i == 0 ? x.x : x.y; }
+__device__ __forceinline__ float comp(float4 x, int i) { return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w)); }
+
+// ---------------------------------------------------------------------------
+// Hop sums of one lane over its group's slots (warp-sliced table, blocks of 8
+// slots per lane).  All blocks of a chunk are loaded with 16-byte loads before
+// any gather, so one table-load latency is paid per chunk rather than per hop.
+// add(e) receives each packed entry (target << 2) | code; padding entries are 0
+// (target 0, weight 0).
+template <typename EntT, typename F>
+__device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int nblk, int lane, F&& add) {
+    constexpr int LOADS = (int)sizeof(EntT);          // 16-byte loads per 8-slot block: 2 (u16) -> 1, 4 (u32) -> 2
+    constexpr int NL = LOADS == 2 ? 1 : 2;
+    constexpr int CH = NL == 1 ? 4 : 2;               // blocks per chunk
+    const uint4* p = reinterpret_cast<const uint4*>(base) + (int64_t)lane * NL;
+    for (int b0 = 0; b0 < nblk; b0 += CH) {
+        uint4 buf[CH][NL];
+#pragma unroll
+        for (int i = 0; i < CH; ++i)
+#pragma unroll
+            for (int j = 0; j < NL; ++j)
+                buf[i][j] = (b0 + i < nblk) ? __ldg(p + (int64_t)(b0 + i) * 32 * NL + j) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+            if (b0 + i >= nblk) break;
+#pragma unroll
+            for (int j = 0; j < NL; ++j) {
+                const uint32_t q[4] = {buf[i][j].x, buf[i][j].y, buf[i][j].z, buf[i][j].w};
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    if constexpr (NL == 1) {
+                        add(q[r] & 0xFFFFu);
+                        add(q[r] >> 16);
+                    } else {
+                        add(q[r]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+// Row phase, binary64 fixed point: Y[u, d] = sum_{(d', s) in hops_dn(d)} s X[u, d']
+template <int VEC, typename EntT>
+__global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v, long long* __restrict__ Y,
+                                                     int2* __restrict__ Xg, int64_t Dup, int64_t Ddn,
+                                                     const int64_t* __restrict__ boff,
+                                                     const int32_t* __restrict__ bcnt,
+                                                     const EntT* __restrict__ ent,
+                                                     const int* __restrict__ emax_p, int fixed_emax) {
+    using S = typename FxVec<VEC>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* X = reinterpret_cast<S*>(smem_raw);
+    const int emax = fixed_emax > 0 ? fixed_emax : max(*emax_p, 1);
+    const int lane = threadIdx.x & 31;
+    const int64_t nblk = (Dup + VEC - 1) / VEC;
+    const int64_t step = blockDim.x;
+    for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int64_t u0 = b * VEC;
+        const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
+        // stage rows u0 .. u0+nrow-1 as fixed point, 4 loads per row in flight
+        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += 4 * step) {
+            double xv[4][VEC];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int r = 0; r < VEC; ++r) {
+                    const int64_t d = d0 + i * step;
+                    xv[i][r] = (d < Ddn && r < nrow) ? v[(u0 + r) * Ddn + d] : 0.0;
+                }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t d = d0 + i * step;
+                if (d >= Ddn) break;
+                int w[2 * VEC];
+#pragma unroll
+                for (int r = 0; r < VEC; ++r) {
+                    fx_split(xv[i][r], emax, w[2 * r], w[2 * r + 1]);
+                    if (r < nrow) __stcg(Xg + (u0 + r) * Ddn + d, make_int2(w[2 * r], w[2 * r + 1]));
+                }
+                if constexpr (VEC == 1) X[d] = make_int2(w[0], w[1]);
+                else X[d] = make_int4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        __syncthreads();
+        for (int64_t d0 = threadIdx.x & ~31; d0 < Ddn; d0 += step) {
+            const int64_t g = d0 >> 5;
+            const int64_t d = d0 + lane;
+            int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+            for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
+                const int s = hop_sign(e);
+                const S x = X[e >> 2];
+                a0 += s * x.x;
+                a1 += s * x.y;
+                if constexpr (VEC == 2) {
+                    a2 += s * x.z;
+                    a3 += s * x.w;
+                }
+            });
+            if (d < Ddn) {
+                Y[u0 * Ddn + d] = fx_join(a0, a1);
+                if (VEC == 2 && nrow > 1) Y[(u0 + 1) * Ddn + d] = fx_join(a2, a3);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+struct EpiParams {
+    long long A;          // round(-t * 2^m)
+    long long Bbeta;      // round(-beta * 2^m)
+    long long B[33];      // round(U * n * 2^m), n = 0..32
+    int m;
+    int nB;
+    // exact int64 path, valid when t = +-2^et and U * 2^ju is a small integer:
+    //   value = (sgn_t * T * 2^(et+ju) + Uint * n * X) * 2^-(k+ju)
+    int fast;
+    int tshift;           // et + ju >= 0
+    int tneg;             // t < 0
+    int ju;
+    long long Uint;       // U * 2^ju
+};
+
+// Up phase, binary64 fixed point (Algorithms 2 and 4):
+//   W[u, c] = -t (sum_{(u', s) in hops_up(u)} s X[u', c] + Y[u, c]) + U n(u, c) X[u, c]  [- beta w_old]
+// Row u of W is a signed combination of whole rows u' of X (Eq. H-Kroneckersum),
+// so a warp builds one row segment of CC = 32 * VPL columns with lanes over
+// columns: the hop list is warp-uniform and every access is coalesced.  Work
+// items are (column chunk, block of RB rows); consecutive items share a chunk,
+// which keeps that chunk of X resident in L2 while all rows are combined, and
+// consecutive rows share part of their neighbours (reuse in L1).
+constexpr int kUpRows = 16;
+
+// Signed sum over the warp-uniform hop list of row u: targets t in
+// list[kb .. kb+n), the first np with sign +1.  load(t) returns this lane's
+// operand from row t; four independent loads are issued before they are
+// added.  Loop bounds are warp-uniform, so the sign split costs no divergence.
+template <typename Val, typename Load, typename Add>
+__device__ __forceinline__ void uniform_hops(const uint32_t* __restrict__ list, int32_t kb, int n, int np, int lane,
+                                             Val& P, Val& N, Load&& load, Add&& add) {
+    for (int k0 = 0; k0 < n; k0 += 32) {
+        const int nk = min(32, n - k0);
+        const uint32_t mine = lane < nk ? __ldg(list + kb + k0 + lane) : 0u;
+        const int pend = max(0, min(nk, np - k0));
+        int q = 0;
+        for (; q + 4 <= pend; q += 4) {
+            const Val a = load(__shfl_sync(0xffffffffu, mine, q));
+            const Val b = load(__shfl_sync(0xffffffffu, mine, q + 1));
+            const Val c = load(__shfl_sync(0xffffffffu, mine, q + 2));
+            const Val d = load(__shfl_sync(0xffffffffu, mine, q + 3));
+            add(P, a, b, c, d);
+        }
+        for (; q < pend; ++q) add(P, load(__shfl_sync(0xffffffffu, mine, q)));
+        for (; q + 4 <= nk; q += 4) {
+            const Val a = load(__shfl_sync(0xffffffffu, mine, q));
+            const Val b = load(__shfl_sync(0xffffffffu, mine, q + 1));
+            const Val c = load(__shfl_sync(0xffffffffu, mine, q + 2));
+            const Val d = load(__shfl_sync(0xffffffffu, mine, q + 3));
+            add(N, a, b, c, d);
+        }
+        for (; q < nk; ++q) add(N, load(__shfl_sync(0xffffffffu, mine, q)));
+    }
+}
+
+__device__ __forceinline__ void add4(int4& A, int4 a, int4 b, int4 c, int4 d) {
+    A.x += a.x + b.x + c.x + d.x;
+    A.y += a.y + b.y + c.y + d.y;
+    A.z += a.z + b.z + c.z + d.z;
+    A.w += a.w + b.w + c.w + d.w;
+}
+__device__ __forceinline__ void add4(int4& A, int4 a) {
+    A.x += a.x; A.y += a.y; A.z += a.z; A.w += a.w;
+}
+__device__ __forceinline__ void add4(int2& A, int2 a, int2 b, int2 c, int2 d) {
+    A.x += a.x + b.x + c.x + d.x;
+    A.y += a.y + b.y + c.y + d.y;
+}
+__device__ __forceinline__ void add4(int2& A, int2 a) { A.x += a.x; A.y += a.y; }
+
+// Up phase, binary64 fixed point (Algorithms 2 and 4):
+//   W[u, c] = -t (sum_{(u', s) in hops_up(u)} s X[u', c] + Y[u, c]) + U n(u, c) X[u, c]  [- beta w_old]
+// Row u of W is a signed combination of whole rows u' of X (Eq. H-Kroneckersum),
+// so a warp builds one row segment of CC = 32 * VPL columns with lanes over
+// columns: the hop list is warp-uniform and every access is coalesced.  Work
+// items are (column chunk, block of kUpRows rows); consecutive items share a
+// chunk, which keeps that chunk of X resident in L2 while all rows are
+// combined, and consecutive rows share part of their neighbours (L1 reuse).
+template <int VPL, bool FAST>
+__global__ void __launch_bounds__(256, 3) k_up_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
+                                                     double* w, const double* w_old, int64_t Dup, int64_t Ddn,
+                                                     const int32_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ npos,
+                                                     const uint32_t* __restrict__ list,
+                                                     const uint32_t* __restrict__ su,
+                                                     const uint32_t* __restrict__ sd, EpiParams ep,
+                                                     const int* __restrict__ emax_p, int fixed_emax) {
+    using IV = typename FxVec<VPL>::T;
+    __shared__ long long Bs[33];
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) Bs[i] = i < ep.nB ? ep.B[i] : 0;
+    __syncthreads();
+    const int emax = fixed_emax > 0 ? fixed_emax : max(*emax_p, 1);
+    const int k = 1070 - emax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int CC = 32 * VPL;
+    const int64_t nchunk = (Ddn + CC - 1) / CC;
+    const int64_t nrb = (Dup + kUpRows - 1) / kUpRows;
+    // item = chunk * nrb + rb, advanced by gridDim.x without division
+    int64_t chunk = blockIdx.x / nrb, rb = blockIdx.x % nrb;
+    const int64_t dch = gridDim.x / nrb, drb = gridDim.x % nrb;
+    for (; chunk < nchunk; chunk += dch, rb += drb) {
+        if (rb >= nrb) {
+            rb -= nrb;
+            ++chunk;
+            if (chunk >= nchunk) break;
+        }
+        const int64_t c_raw = chunk * CC + (int64_t)lane * VPL;
+        const bool act = c_raw < Ddn;
+        const int64_t c = act ? c_raw : Ddn - VPL;     // tail lanes read a valid column, store nothing
+        uint32_t sdc[VPL];
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) sdc[j] = sd[c + j];
+        const IV* base = reinterpret_cast<const IV*>(X + c);
+        const int64_t uend = min(rb * kUpRows + kUpRows, Dup);
+        for (int64_t u = rb * kUpRows + warp; u < uend; u += nw) {
+            const int32_t kb = ptr[u];
+            IV P{}, N{};
+            uniform_hops<IV>(list, kb, ptr[u + 1] - kb, npos[u], lane, P, N,
+                [&](uint32_t t) { return __ldg(reinterpret_cast<const IV*>(reinterpret_cast<const int2*>(base) + (int64_t)t * Ddn)); },
+                [](IV& A, auto... xs) { add4(A, xs...); });
+            if (act) {
+                const uint32_t su_u = su[u];
+                const int64_t J = u * Ddn + c;
+                int lo[VPL], hi[VPL];
+                int2 xo[VPL];
+                long long yv[VPL];
+                if constexpr (VPL == 2) {
+                    lo[0] = P.x - N.x; hi[0] = P.y - N.y; lo[1] = P.z - N.z; hi[1] = P.w - N.w;
+                    const int4 t4 = __ldg(reinterpret_cast<const int4*>(X + J));
+                    xo[0] = make_int2(t4.x, t4.y);
+                    xo[1] = make_int2(t4.z, t4.w);
+                    const longlong2 y2 = __ldcs(reinterpret_cast<const longlong2*>(Y + J));
+                    yv[0] = y2.x;
+                    yv[1] = y2.y;
+                } else {
+                    lo[0] = P.x - N.x; hi[0] = P.y - N.y;
+                    xo[0] = __ldg(X + J);
+                    yv[0] = __ldcs(Y + J);
+                }
+                double r[VPL];
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) {
+                    if constexpr (FAST) {
+                        // exact: |T| < 2^55, |X| <= 2^48, |Uint * n| < 2^14 and tshift <= 6
+                        long long Pv = (fx_join(lo[j], hi[j]) + yv[j]) << ep.tshift;
+                        if (ep.tneg == 0) Pv = -Pv;
+                        Pv += ep.Uint * (long long)__popc(su_u & sdc[j]) * fx_join(xo[j].x, xo[j].y);
+                        r[j] = i64_scaled_to_double(Pv, -(k + ep.ju));
+                    } else {
+                        I128 acc{0ull, 0ll};
+                        mac128(acc, fx_join(lo[j], hi[j]) + yv[j], ep.A);
+                        mac128(acc, fx_join(xo[j].x, xo[j].y), Bs[__popc(su_u & sdc[j])]);
+                        if (w_old != nullptr) {
+                            int glo, ghi;
+                            fx_split(w_old[J + j], emax, glo, ghi);
+                            mac128(acc, fx_join(glo, ghi), ep.Bbeta);
+                        }
+                        r[j] = i128_to_double(acc, -(k + ep.m));
+                    }
+                }
+                if constexpr (VPL == 2) __stcs(reinterpret_cast<double2*>(w + J), make_double2(r[0], r[1]));
+                else __stcs(w + J, r[0]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void addf(float& A, float a, float b, float c, float d) { A += (a + b) + (c + d); }
+__device__ __forceinline__ void addf(float& A, float a) { A += a; }
+__device__ __forceinline__ void addf(float2& A, float2 a, float2 b, float2 c, float2 d) {
+    A.x += (a.x + b.x) + (c.x + d.x);
+    A.y += (a.y + b.y) + (c.y + d.y);
+}
+__device__ __forceinline__ void addf(float2& A, float2 a) { A.x += a.x; A.y += a.y; }
+__device__ __forceinline__ void addf(float4& A, float4 a, float4 b, float4 c, float4 d) {
+    A.x += (a.x + b.x) + (c.x + d.x);
+    A.y += (a.y + b.y) + (c.y + d.y);
+    A.z += (a.z + b.z) + (c.z + d.z);
+    A.w += (a.w + b.w) + (c.w + d.w);
+}
+__device__ __forceinline__ void addf(float4& A, float4 a) { A.x += a.x; A.y += a.y; A.z += a.z; A.w += a.w; }
+
+// Up phase, binary32: same decomposition, float arithmetic
+template <int VPL>
+__global__ void __launch_bounds__(256, 3) k_up_f32(const float* __restrict__ v, const float* __restrict__ Y, float* w,
+                                                    const float* w_old, int64_t Dup, int64_t Ddn,
+                                                    const int32_t* __restrict__ ptr,
+                                                    const int32_t* __restrict__ npos,
+                                                    const uint32_t* __restrict__ list,
+                                                    const uint32_t* __restrict__ su,
+                                                    const uint32_t* __restrict__ sd, float mt, float U, float mbeta) {
+    using V = typename F32Vec<VPL>::T;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int CC = 32 * VPL;
+    const int64_t nchunk = (Ddn + CC - 1) / CC;
+    const int64_t nrb = (Dup + kUpRows - 1) / kUpRows;
+    int64_t chunk = blockIdx.x / nrb, rb = blockIdx.x % nrb;
+    const int64_t dch = gridDim.x / nrb, drb = gridDim.x % nrb;
+    for (; chunk < nchunk; chunk += dch, rb += drb) {
+        if (rb >= nrb) {
+            rb -= nrb;
+            ++chunk;
+            if (chunk >= nchunk) break;
+        }
+        const int64_t c_raw = chunk * CC + (int64_t)lane * VPL;
+        const bool act = c_raw < Ddn;
+        const int64_t c = act ? c_raw : Ddn - VPL;
+        uint32_t sdc[VPL];
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) sdc[j] = sd[c + j];
+        const float* base = v + c;
+        const int64_t uend = min(rb * kUpRows + kUpRows, Dup);
+        for (int64_t u = rb * kUpRows + warp; u < uend; u += nw) {
+            const int32_t kb = ptr[u];
+            V P{}, N{};
+            uniform_hops<V>(list, kb, ptr[u + 1] - kb, npos[u], lane, P, N,
+                [&](uint32_t t) { return __ldg(reinterpret_cast<const V*>(base + (int64_t)t * Ddn)); },
+                [](V& A, auto... xs) { addf(A, xs...); });
+            if (act) {
+                const uint32_t su_u = su[u];
+                const int64_t J = u * Ddn + c;
+                const V xo = __ldg(reinterpret_cast<const V*>(v + J));
+                const V yv = __ldcs(reinterpret_cast<const V*>(Y + J));
+                float r[VPL];
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) {
+                    const float nd = (float)__popc(su_u & sdc[j]);
+                    r[j] = fmaf(mt, (comp(P, j) - comp(N, j)) + comp(yv, j), U * nd * comp(xo, j));
+                    if (w_old != nullptr) r[j] = fmaf(mbeta, w_old[J + j], r[j]);
+                }
+                if constexpr (VPL == 4) __stcs(reinterpret_cast<float4*>(w + J), make_float4(r[0], r[1], r[2], r[3]));
+                else if constexpr (VPL == 2) __stcs(reinterpret_cast<float2*>(w + J), make_float2(r[0], r[1]));
+                else __stcs(w + J, r[0]);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// binary32 variants: same structure, float arithmetic
+template <int VEC, typename EntT>
+__global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, float* __restrict__ Y, int64_t Dup,
+                                                    int64_t Ddn, const int64_t* __restrict__ boff,
+                                                    const int32_t* __restrict__ bcnt,
+                                                    const EntT* __restrict__ ent) {
+    using S = typename F32Vec<VEC>::T;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S* X = reinterpret_cast<S*>(smem_raw);
+    float* Xf = reinterpret_cast<float*>(smem_raw);
+    const int lane = threadIdx.x & 31;
+    const int64_t nblk = (Dup + VEC - 1) / VEC;
+    const int64_t step = blockDim.x;
+    for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
+        const int64_t u0 = b * VEC;
+        const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
+        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += 4 * step) {
+            float xv[4][VEC];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int r = 0; r < VEC; ++r) {
+                    const int64_t d = d0 + i * step;
+                    xv[i][r] = (d < Ddn && r < nrow) ? v[(u0 + r) * Ddn + d] : 0.0f;
+                }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int64_t d = d0 + i * step;
+                if (d >= Ddn) break;
+#pragma unroll
+                for (int r = 0; r < VEC; ++r) Xf[d * VEC + r] = xv[i][r];
+            }
+        }
+        __syncthreads();
+        for (int64_t d0 = threadIdx.x & ~31; d0 < Ddn; d0 += step) {
+            const int64_t g = d0 >> 5;
+            const int64_t d = d0 + lane;
+            float acc[VEC];
+#pragma unroll
+            for (int r = 0; r < VEC; ++r) acc[r] = 0.0f;
+            for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
+                const float s = (float)hop_sign(e);
+                const S x = X[e >> 2];
+#pragma unroll
+                for (int r = 0; r < VEC; ++r) acc[r] = fmaf(s, comp(x, r), acc[r]);
+            });
+            if (d < Ddn) {
+#pragma unroll
+                for (int r = 0; r < VEC; ++r)
+                    if (r < nrow) Y[(u0 + r) * Ddn + d] = acc[r];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+int smem_optin() {
+    static int v = 0;
+    if (v == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (v <= 0) v = 48 * 1024;
+    }
+    return v;
+}
+
+int sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+// largest VEC in {4,2,1} (capped by vmax) whose staging buffer fits
+int pick_vec(int64_t len, int elem_bytes, int vmax, int reserve) {
+    for (int v = vmax; v >= 1; v >>= 1)
+        if ((int64_t)len * elem_bytes * v + reserve <= smem_optin()) return v;
+    return 0;
+}
+
+struct Launch {
+    int blocks, threads;
+    size_t smem;
+};
+
+// ctas = 0: two CTAs per SM when both fit, else one
+Launch shape(size_t smem, int ctas) {
+    const size_t per_sm = 228 * 1024;
+    const int fit = (int)std::max<size_t>(1, std::min<size_t>(2, per_sm / (smem + 2048)));
+    if (ctas <= 0 || ctas > fit) ctas = fit;
+    Launch L;
+    L.smem = smem;
+    L.threads = ctas == 1 ? 1024 : 512;
+    L.blocks = sms() * ctas;
+    return L;
+}
+
+template <typename K>
+void allow_smem(K kern, size_t bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// m such that max(|t|, |U| Ns, |beta|) * 2^m <= 2^61
+EpiParams make_epilogue(double t, double U, int ns, double beta) {
+    EpiParams p{};
+    double M = std::max(std::fabs(t), std::max(std::fabs(U) * ns, std::fabs(beta)));
+    int m = 0;
+    if (M > 0) {
+        int ex = 0;
+        std::frexp(M, &ex);                           // M < 2^ex
+        m = 61 - ex;
+    }
+    p.m = m;
+    p.A = (long long)std::llround(std::ldexp(-t, m));
+    p.Bbeta = (long long)std::llround(std::ldexp(-beta, m));
+    p.nB = std::min(ns, 32) + 1;
+    for (int n = 0; n < 33; ++n) p.B[n] = n < p.nB ? (long long)std::llround(std::ldexp(U * n, m)) : 0;
+    // exact int64 path: t = +-2^et (et in [-8, 6]), U * 2^ju integer for some ju in [0, 8] with
+    // |U 2^ju| * Ns < 2^14, no beta term; the shifted hop sum stays below 2^(55+6+8) ... bounded below
+    p.fast = 0;
+    if (beta == 0.0 && t != 0.0) {
+        int et = 0;
+        const double mt = std::frexp(std::fabs(t), &et);   // |t| = mt * 2^et, mt in [0.5, 1)
+        if (mt == 0.5) {
+            et -= 1;                                        // |t| = 2^et
+            for (int ju = 0; ju <= 8; ++ju) {
+                const double us = std::ldexp(U, ju);
+                if (us == std::floor(us) && std::fabs(us) * ns < 16384.0 && et + ju >= 0 && et + ju <= 6) {
+                    p.fast = 1;
+                    p.tshift = et + ju;
+                    p.tneg = t < 0 ? 1 : 0;
+                    p.ju = ju;
+                    p.Uint = (long long)us;
+                    break;
+                }
+            }
+        }
+    }
+    return p;
+}
+
+// requested vec (0 = largest that fits), capped to what fits
+int choose_vec(int req, int64_t len, int elem_bytes, int vmax, int reserve) {
+    const int fit = pick_vec(len, elem_bytes, vmax, reserve);
+    if (req <= 0 || req > fit) return fit;
+    return req;
+}
+
+}  // namespace
+
+// Returns HUB_OK and launches, or returns -1 when the staging buffers do not fit
+// (the caller then uses the single-pass gather kernel).
+int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
+                     void* ybuf, int fixed_emax, cudaStream_t s) {
+    const DevSpin& up = H->dev[0];
+    const DevSpin& dn = H->dev[1];
+    const int64_t Dup = H->Dup, Ddn = H->Ddn;
+    const bool dn16 = dn.ent16 != nullptr;
+    const int up_blocks = sms() * 3;
+    if (dtype == HUB_F64) {
+        const int va = choose_vec(H->vec_rows, Ddn, 8, 2, 0);
+        if (va == 0) return -1;
+        int* emax = H->status;
+        if (fixed_emax <= 0) {
+            HUB_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
+            launch_max_exponent((const double*)v, H->D, emax, s);
+            if (w_old != nullptr) launch_max_exponent((const double*)w_old, H->D, emax, s);
+        }
+        const Launch LA = shape((size_t)Ddn * 8 * va, H->ctas_rows);
+        long long* Y = (long long*)ybuf;
+        int2* Xg = (int2*)((char*)ybuf + (size_t)H->D * 8);
+#define ROWS64(V, E, P)                                                                                     \
+    allow_smem(k_rows_f64x<V, E>, LA.smem);                                                                  \
+    k_rows_f64x<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const double*)v, Y, Xg, Dup, Ddn, dn.blk_off,  \
+                                                            dn.blk_cnt, P, emax, fixed_emax)
+        if (va == 2) {
+            if (dn16) { ROWS64(2, uint16_t, dn.ent16); } else { ROWS64(2, uint32_t, dn.ent32); }
+        } else {
+            if (dn16) { ROWS64(1, uint16_t, dn.ent16); } else { ROWS64(1, uint32_t, dn.ent32); }
+        }
+#undef ROWS64
+        const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
+#define UP64(V, F)                                                                                          \
+    k_up_f64x<V, F><<<up_blocks, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,  \
+                                              up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax)
+        if ((Ddn & 1) == 0) {
+            if (ep.fast) { UP64(2, true); } else { UP64(2, false); }
+        } else {
+            if (ep.fast) { UP64(1, true); } else { UP64(1, false); }
+        }
+#undef UP64
+        HUB_CUDA(cudaGetLastError());
+        count_launches(2 + (fixed_emax <= 0 ? (w_old ? 2 : 1) : 0));
+        return HUB_OK;
+    }
+    // binary32
+    const int va = choose_vec(H->vec_rows, Ddn, 4, 4, 0);
+    if (va == 0) return -1;
+    const Launch LA = shape((size_t)Ddn * 4 * va, H->ctas_rows);
+    float* Y = (float*)ybuf;
+#define ROWS32(V, E, P)                                                                                    \
+    allow_smem(k_rows_f32<V, E>, LA.smem);                                                                  \
+    k_rows_f32<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const float*)v, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, P)
+#define BOTH32(M, V, F, P16, P32) if (F) { M(V, uint16_t, P16); } else { M(V, uint32_t, P32); }
+    if (va == 4) { BOTH32(ROWS32, 4, dn16, dn.ent16, dn.ent32) }
+    else if (va == 2) { BOTH32(ROWS32, 2, dn16, dn.ent16, dn.ent32) }
+    else { BOTH32(ROWS32, 1, dn16, dn.ent16, dn.ent32) }
+#undef BOTH32
+#undef ROWS32
+#define UP32(V)                                                                                            \
+    k_up_f32<V><<<up_blocks, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old, Dup, Ddn,   \
+        up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t, (float)H->U, (float)-beta)
+    if ((Ddn & 3) == 0) { UP32(4); } else if ((Ddn & 1) == 0) { UP32(2); } else { UP32(1); }
+#undef UP32
+    HUB_CUDA(cudaGetLastError());
+    count_launches(2);
+    return HUB_OK;
+}
+
+}  // namespace hub

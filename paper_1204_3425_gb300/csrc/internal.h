@@ -42,6 +42,27 @@ struct DevSpin {
     uint32_t* ent = nullptr;         // [nnz] packed (target << 1) | (sign < 0)
     uint32_t* ell = nullptr;         // [W * D] column-major ELL, packed as ent; pad = 0xFFFFFFFF
     int32_t* cnt = nullptr;          // [D] hops per state
+    // warp-sliced ELL ("SELL-32"): states in groups of 32 (one per lane);
+    // group g holds sell_cnt[g] slots of 32 entries at sell_off[g]; entry =
+    // (target << 2) | code, code 1 = +1, 3 = -1, 0 = padding (weight 0).
+    int64_t* sell_off = nullptr;     // [groups]
+    int32_t* sell_cnt = nullptr;     // [groups]
+    uint32_t* sell_ent = nullptr;    // [sum cnt * 32]
+    int64_t sell_entries = 0;
+    // the same table in blocks of 8 slots per lane ("SELL-32/8"): group g has
+    // blk_cnt[g] blocks at blk_off[g] (in entries); block b of lane l holds
+    // slots 8b .. 8b+7 at blk_off[g] + (b*32 + l)*8.  Entries are 16-bit when
+    // D < 2^14 (ent16), else 32-bit (ent32); same (target << 2) | code packing.
+    int64_t* blk_off = nullptr;      // [groups]
+    int32_t* blk_cnt = nullptr;      // [groups]
+    uint16_t* ent16 = nullptr;
+    uint32_t* ent32 = nullptr;
+    // per-state hop list with the +1 targets first, then the -1 targets:
+    // targets of state r at pn_list[pn_ptr[r] .. pn_ptr[r+1]), the first
+    // pn_npos[r] of them with sign +1 (used where the list is warp-uniform)
+    int32_t* pn_ptr = nullptr;       // [D+1]
+    int32_t* pn_npos = nullptr;      // [D]
+    uint32_t* pn_list = nullptr;     // [nnz]
 };
 
 }  // namespace hub
@@ -57,6 +78,9 @@ struct hubbard_sector {
     // fixed-point scratch for the F64 fast path, allocated on first use
     void* fx_scratch = nullptr;
     size_t fx_bytes = 0;
+    // two-phase H*v schedule (0 = automatic): rows / columns per staged block
+    // and CTAs per SM for the row and column phases (hubbard_set_schedule)
+    int vec_rows = 0, vec_cols = 0, ctas_rows = 0, ctas_cols = 0;
     // small device scratch for reductions: partial sums, status words
     double* red = nullptr;           // [kRedSlots]
     int* status = nullptr;           // [4]
@@ -72,7 +96,14 @@ void count_launches(int n);
 // kernels.cu launchers -------------------------------------------------------
 int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dtype, cudaStream_t s);
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta,
-                   const void* w_old, cudaStream_t s);
+                   const void* w_old, int fixed_emax, cudaStream_t s);
+// hv_phases.cu: two-phase shared-memory H*v; -1 when the staging buffers do not fit.
+// fixed_emax > 0 fixes the fixed-point exponent bound (vectors of norm <= 1:
+// 1023); otherwise it is computed from v and w_old.
+int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
+                     void* ybuf, int fixed_emax, cudaStream_t s);
+// max biased binary64 exponent of |v| folded into *emax (atomicMax; caller zeroes it)
+void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s);
 int launch_dot(const hubbard_sector* H, const void* x, const void* y, int64_t n, int dtype,
                double* partials, cudaStream_t s);
 int reduce_partials_host(double* partials, cudaStream_t s, double* out);

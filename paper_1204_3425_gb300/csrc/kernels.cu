@@ -237,11 +237,20 @@ int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dty
     return HUB_OK;
 }
 
+void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s) {
+    const int g2 = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_max_exponent<<<g2, kThreads, 0, s>>>(v, n, emax);
+}
+
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                   cudaStream_t s) {
+                   int fixed_emax, cudaStream_t s) {
     const DevSpin& up = H->dev[0];
     const DevSpin& dn = H->dev[1];
     const int grid = grid_for(H->Dup, 1, sm_count() * 16);
+    if (H->fx_bytes >= (size_t)H->D * 16) {
+        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s);
+        if (rc != -1) return rc;
+    }
     if (dtype == HUB_F32) {
         if (w_old != nullptr || beta != 0.0) return fail(HUB_EINVAL, "f32 fused step not available");
         k_hv_reference<float><<<grid, kThreads, 0, s>>>((const float*)v, (float*)w, H->Dup, H->Ddn,
