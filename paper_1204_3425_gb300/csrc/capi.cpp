@@ -88,6 +88,96 @@ void free_dev(hubbard_sector* H) {
     H->status = nullptr;
 }
 
+// Slot assignment for the row-phase gathers of one group of 32 states.
+// Lanes are split into phases of `pl` lanes (one shared-memory wavefront each
+// for an element of `eb` bytes: 128/eb bank groups).  Within a phase, a hop
+// of lane l to target t is an edge (l, t mod groups) of a bipartite multigraph;
+// a proper edge colouring with Delta = max degree colours (Koenig) gives slots
+// in which no two lanes of a phase hit the same bank group.  Colouring by
+// alternating paths.  Returns, per lane, the slot of each of its hops.
+struct SlotColouring {
+    int slots = 0;
+    std::vector<std::vector<int>> slot_of;   // [lane][hop index] -> slot
+};
+
+static SlotColouring colour_group(const std::vector<std::vector<int32_t>>& lane_tgts, int eb) {
+    const int ngroups = std::max(1, 128 / eb);
+    const int pl = std::max(1, std::min(32, 128 / eb));   // lanes per wavefront phase
+    SlotColouring R;
+    R.slot_of.resize(lane_tgts.size());
+    for (size_t l = 0; l < lane_tgts.size(); ++l) R.slot_of[l].assign(lane_tgts[l].size(), -1);
+    for (size_t p0 = 0; p0 < lane_tgts.size(); p0 += pl) {
+        const size_t p1 = std::min(lane_tgts.size(), p0 + pl);
+        struct E { int l, g; size_t lane, k; };
+        std::vector<E> edges;
+        std::vector<int> degl(pl, 0), degg(ngroups, 0);
+        for (size_t l = p0; l < p1; ++l)
+            for (size_t k = 0; k < lane_tgts[l].size(); ++k) {
+                const int g = (int)(lane_tgts[l][k] % ngroups);
+                edges.push_back({(int)(l - p0), g, l, k});
+                degl[l - p0]++;
+                degg[g]++;
+            }
+        int D = 0;
+        for (int x : degl) D = std::max(D, x);
+        for (int x : degg) D = std::max(D, x);
+        std::vector<std::vector<int>> atl(pl, std::vector<int>(D, -1)), atg(ngroups, std::vector<int>(D, -1));
+        std::vector<int> col(edges.size(), -1);
+        for (size_t ei = 0; ei < edges.size(); ++ei) {
+            const int l = edges[ei].l, g = edges[ei].g;
+            int a = 0, b = 0;
+            while (atl[l][a] >= 0) ++a;
+            while (atg[g][b] >= 0) ++b;
+            if (atg[g][a] >= 0) {
+                // flip the a/b alternating path that starts at g along colour a
+                std::vector<int> path;
+                bool at_g = true;
+                int node = g, cur = a;
+                while (true) {
+                    const int e = at_g ? atg[node][cur] : atl[node][cur];
+                    if (e < 0) break;
+                    path.push_back(e);
+                    node = at_g ? edges[e].l : edges[e].g;
+                    at_g = !at_g;
+                    cur = (cur == a) ? b : a;
+                }
+                for (int e : path) {
+                    atl[edges[e].l][col[e]] = -1;
+                    atg[edges[e].g][col[e]] = -1;
+                }
+                for (int e : path) {
+                    col[e] = (col[e] == a) ? b : a;
+                    atl[edges[e].l][col[e]] = e;
+                    atg[edges[e].g][col[e]] = e;
+                }
+            }
+            col[ei] = a;
+            atl[l][a] = (int)ei;
+            atg[g][a] = (int)ei;
+        }
+        for (size_t ei = 0; ei < edges.size(); ++ei) R.slot_of[edges[ei].lane][edges[ei].k] = col[ei];
+        R.slots = std::max(R.slots, D);
+    }
+    // validate: every hop has a slot in [0, slots) and no lane uses a slot twice;
+    // otherwise fall back to consecutive slots (correct, only slower)
+    bool ok = true;
+    for (size_t l = 0; l < R.slot_of.size() && ok; ++l) {
+        std::vector<char> used((size_t)std::max(R.slots, 1), 0);
+        for (int s : R.slot_of[l]) {
+            if (s < 0 || s >= R.slots || used[(size_t)s]) { ok = false; break; }
+            used[(size_t)s] = 1;
+        }
+    }
+    if (!ok) {
+        R.slots = 0;
+        for (size_t l = 0; l < R.slot_of.size(); ++l) {
+            for (size_t k = 0; k < R.slot_of[l].size(); ++k) R.slot_of[l][k] = (int)k;
+            R.slots = std::max(R.slots, (int)R.slot_of[l].size());
+        }
+    }
+    return R;
+}
+
 int upload_spin(const SpinTables& T, DevSpin& d) {
     std::vector<uint32_t> ent(T.tgt.size());
     for (size_t k = 0; k < T.tgt.size(); ++k)
@@ -119,21 +209,34 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
                 ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
     }
     d.sell_entries = total;
-    // SELL-32/8: per group, blocks of 8 slots per lane, contiguous per lane
+    // SELL-32/8 for the row phase: per group, slots assigned by bank-conflict-free
+    // colouring for the element size the row phase will stage (16 bytes when a
+    // 16-byte-per-state row fits in shared memory, else 8, else 4), in blocks of
+    // 8 slots per lane, contiguous per lane; empty slots are padding (code 0).
+    const int64_t smem_budget = 220 * 1024;
+    const int eb = (T.D * 16 <= smem_budget) ? 16 : ((T.D * 8 <= smem_budget) ? 8 : 4);
     std::vector<int64_t> boff((size_t)groups);
     std::vector<int32_t> bcnt((size_t)groups);
+    std::vector<SlotColouring> colours((size_t)groups);
     int64_t btotal = 0;
     for (int64_t g = 0; g < groups; ++g) {
+        std::vector<std::vector<int32_t>> lt;
+        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r)
+            lt.emplace_back(T.tgt.begin() + T.rowptr[(size_t)r], T.tgt.begin() + T.rowptr[(size_t)r + 1]);
+        colours[(size_t)g] = colour_group(lt, eb);
         boff[(size_t)g] = btotal;
-        bcnt[(size_t)g] = (scnt[(size_t)g] + 7) / 8;
+        bcnt[(size_t)g] = (colours[(size_t)g].slots + 7) / 8;
         btotal += (int64_t)bcnt[(size_t)g] * 32 * 8;
     }
     std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), 0u);
     for (int64_t r = 0; r < T.D; ++r) {
         const int64_t g = r / 32, lane = r % 32;
-        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
-            bent[(size_t)(boff[(size_t)g] + ((int64_t)(c / 8) * 32 + lane) * 8 + c % 8)] =
+        const std::vector<int>& so = colours[(size_t)g].slot_of[(size_t)lane];
+        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c) {
+            const int slot = so[(size_t)c];
+            bent[(size_t)(boff[(size_t)g] + ((int64_t)(slot / 8) * 32 + lane) * 8 + slot % 8)] =
                 ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
+        }
     }
     // sign-split list: +1 targets first, then -1 targets, each ascending
     std::vector<int32_t> npos((size_t)T.D);

@@ -212,13 +212,15 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
             const int64_t d = d0 + lane;
             int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
             for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
-                const int s = hop_sign(e);
-                const S x = X[e >> 2];
-                a0 += s * x.x;
-                a1 += s * x.y;
-                if constexpr (VEC == 2) {
-                    a2 += s * x.z;
-                    a3 += s * x.w;
+                if (e & 3u) {                                 // padding slots read nothing
+                    const int s = hop_sign(e);
+                    const S x = X[e >> 2];
+                    a0 += s * x.x;
+                    a1 += s * x.y;
+                    if constexpr (VEC == 2) {
+                        a2 += s * x.z;
+                        a3 += s * x.w;
+                    }
                 }
             });
             if (d < Ddn) {
@@ -511,10 +513,12 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
 #pragma unroll
             for (int r = 0; r < VEC; ++r) acc[r] = 0.0f;
             for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
-                const float s = (float)hop_sign(e);
-                const S x = X[e >> 2];
+                if (e & 3u) {                                 // padding slots read nothing
+                    const float s = (float)hop_sign(e);
+                    const S x = X[e >> 2];
 #pragma unroll
-                for (int r = 0; r < VEC; ++r) acc[r] = fmaf(s, comp(x, r), acc[r]);
+                    for (int r = 0; r < VEC; ++r) acc[r] = fmaf(s, comp(x, r), acc[r]);
+                }
             });
             if (d < Ddn) {
 #pragma unroll
