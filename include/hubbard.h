@@ -222,6 +222,45 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
  * all devices) - instrumentation for benchmarks and tests. */
 uint64_t hubbard_kernel_launches(void);
 
+/* ---------------------------------------------------------------------------
+ * Ground state in binary32 with binary64 refinement (Sec. 2.2, Algorithm 1,
+ * run in binary32; the paper benchmarks both precisions, Sec. 5).
+ *   1. binary32 Lanczos (H*v and vectors binary32; a_j, b_j reductions
+ *      accumulated in float-float, ~48 bits) until rho < 2e-6 max(1,|theta|);
+ *   2. Ritz vector psi = sum_j s_j f_j: the same binary32 recurrence is
+ *      replayed with the stored a_j, b_j (bit-identical f_j) and psi is
+ *      accumulated in binary64;
+ *   3. binary64 Rayleigh quotient theta = <psi|H|psi> and residual
+ *      |H psi - theta psi| with the binary64 H*v;
+ *   4. if residual^2 / gap > tol max(1,|theta|): a short binary64 Lanczos
+ *      run started from psi (at most 60 steps).
+ *   v0          binary64 device start vector (normalised inside)
+ *   workspace   >= lanczos_refined_workspace_bytes(H) bytes (40 D), 256-aligned
+ *   psi_out     optional binary64 device vector receiving the normalised psi
+ *               of step 2
+ *   out         energy (binary64 Rayleigh quotient or polished Ritz value),
+ *               residual, error_bound = residual^2 / gap (a-posteriori bound on
+ *               |energy - E0| when the gap estimate holds), binary32 energy,
+ *               gap estimate, iteration counts, status
+ * Returns HUB_ENOTCONV when the bound stays above tol.  Synchronises stream.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    double energy;
+    double residual;
+    double error_bound;
+    double energy_f32;
+    double gap;
+    int32_t iters_f32;
+    int32_t iters_f64;
+    int32_t status;
+    int32_t reserved;
+} lanczos_refined_result;
+
+size_t lanczos_refined_workspace_bytes(hubbard_t H);
+
+int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, double tol, void* workspace,
+                                 size_t ws_bytes, void* psi_out, void* stream, lanczos_refined_result* out);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* hubbard_last_error(void);
 

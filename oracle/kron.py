@@ -89,13 +89,15 @@ class KronHamiltonian:
         self._lib.kron_scale(y.size, float(a), _p(y))
 
 
-def lanczos_matrix_free(Hk, v0, max_iter, tol=None, on_step=None):
+def lanczos_matrix_free(Hk, v0, max_iter, tol=None, on_step=None, inplace=False):
     """Algorithm 1, two-vector form (Eqs. split1), with the C helpers.
 
     Same steps as lanczos.lanczos_plain, written against KronHamiltonian so
-    that two vectors of a 2.4e9-element sector fit in host memory.
+    that two vectors of a 2.4e9-element sector fit in host memory (with
+    inplace=True the start vector's own buffer becomes the first Lanczos
+    vector).
     """
-    f = np.array(v0, dtype=np.float64)
+    f = v0 if (inplace and v0.dtype == np.float64) else np.array(v0, dtype=np.float64)
     Hk.scale(1.0 / np.sqrt(Hk.dot(f, f)), f)
     g = np.zeros_like(f)
     a, b = [], []

@@ -52,6 +52,8 @@ SIGNATURES = {
     "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P]),
     "hubbard_host_spin_tables": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]),
     "hubbard_kernel_launches": (ctypes.c_uint64, []),
+    "lanczos_refined_workspace_bytes": (SZ, [P]),
+    "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
     "hubbard_last_error": (ctypes.c_char_p, []),
 }
 
@@ -247,6 +249,34 @@ def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None,
     m = res.iters
     return dict(energy=res.energy, residual=res.residual, iters=m, status=res.status,
                 breakdown=bool(res.breakdown), alpha=a[:m], beta=b[:m])
+
+
+class RefinedResult(ctypes.Structure):
+    _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("error_bound", ctypes.c_double),
+                ("energy_f32", ctypes.c_double), ("gap", ctypes.c_double), ("iters_f32", ctypes.c_int32),
+                ("iters_f64", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def lanczos_refined_workspace_bytes(H):
+    return int(load_library().lanczos_refined_workspace_bytes(H.handle))
+
+
+def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=None, psi_out=None, stream=None,
+                                 raise_on_notconv=False):
+    """binary32 Lanczos + binary64 refinement; v0 binary64.  Returns a dict of the result fields."""
+    import torch
+    lib = load_library()
+    need = lanczos_refined_workspace_bytes(H)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=v0.device)
+    res = RefinedResult()
+    rc = lib.lanczos_ground_state_refined(H.handle, _ptr(v0), int(max_iters), float(tol), _ptr(workspace),
+                                          workspace.numel() * workspace.element_size(),
+                                          _ptr(psi_out) if psi_out is not None else None, _stream(stream),
+                                          ctypes.byref(res))
+    if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
+        _check(rc)
+    return {f: getattr(res, f) for f, _ in RefinedResult._fields_ if f != "reserved"}
 
 
 def hubbard_kernel_launches():

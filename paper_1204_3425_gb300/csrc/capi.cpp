@@ -574,6 +574,73 @@ size_t lanczos_workspace_bytes(hubbard_t H, int dtype) {
     return 2 * vec + align_up((size_t)H->D * 16, 256);
 }
 
+// Algorithm 1 in the two-vector form on caller buffers f, g (D elements of
+// dtype each; the handle's H*v scratch must already point at 16 D bytes).
+// f receives v0 / |v0| (v0 of dtype v0_dtype; binary64 -> binary32 allowed).
+// Returns the a_j, b_{j+1} sequences and the lowest Ritz value.
+struct LanczosRun {
+    std::vector<double> a, b;
+    double theta = 0.0, rho = 0.0;
+    bool broke = false, converged = false;
+};
+
+static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype, void* f,
+                        void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0) {
+    int rc;
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+    n0 = std::sqrt(n0);
+    if (!(n0 > 0.0) || !std::isfinite(n0)) return fail(HUB_EINVAL, "start vector has zero or non-finite norm");
+    if (v0_dtype == dtype) rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / n0, s);
+    else rc = launch_f64_to_f32_scaled((const double*)v0, (float*)f, H->D, 1.0 / n0, s);
+    if (rc) return rc;
+    if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
+    double bj = 0.0;
+    for (int j = 0; j < m_cap; ++j) {
+        double aj = 0.0, bn = 0.0;
+        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023))) return rc;
+        R.a.push_back(aj);
+        double s_last = 1.0;
+        tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
+        R.rho = bn * std::fabs(s_last);
+        double scale = 1.0;
+        for (double x : R.a) scale = std::max(scale, std::fabs(x));
+        for (double x : R.b) scale = std::max(scale, x);
+        R.b.push_back(bn);
+        if (bn <= 1e-13 * scale) {
+            R.broke = true;
+            R.converged = true;
+            break;
+        }
+        if ((tol > 0.0 && R.rho < tol) || (rel_tol > 0.0 && R.rho < rel_tol * std::max(1.0, std::fabs(R.theta)))) {
+            R.converged = true;
+            break;
+        }
+        if ((rc = launch_scale(1.0 / bn, g, H->D, dtype, s))) return rc;
+        std::swap(f, g);
+        bj = bn;
+    }
+    if (tol <= 0.0 && rel_tol <= 0.0) R.converged = true;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+    return HUB_OK;
+}
+
+// points the handle's H*v scratch at a caller region for the duration of a call
+struct ScratchGuard {
+    hubbard_sector* H;
+    void* p;
+    size_t n;
+    ScratchGuard(hubbard_sector* h, void* region, size_t bytes) : H(h), p(h->fx_scratch), n(h->fx_bytes) {
+        H->fx_scratch = region;
+        H->fx_bytes = bytes;
+    }
+    ~ScratchGuard() {
+        H->fx_scratch = p;
+        H->fx_bytes = n;
+    }
+};
+
 int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype, void* workspace,
                          size_t ws_bytes, void* stream, double* alpha_out, double* beta_out,
                          lanczos_result* out) {
@@ -593,82 +660,130 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
     char* ws = (char*)workspace;
-    void* f = ws;
-    void* g = ws + vec;
-    // the fixed-point copy lives in the caller's workspace for the solve
-    void* saved_fx = H->fx_scratch;
-    size_t saved_bytes = H->fx_bytes;
-    H->fx_scratch = ws + 2 * vec;
-    H->fx_bytes = (size_t)H->D * 16;
-    auto restore = [&]() {
-        H->fx_scratch = saved_fx;
-        H->fx_bytes = saved_bytes;
-    };
-    // f_1 = v0 / |v0|, f_0 = 0 (Algorithm 1)
-    double n0 = 0.0;
-    if ((rc = launch_dot(H, v0, v0, H->D, dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) {
-        restore();
-        return rc;
-    }
-    n0 = std::sqrt(n0);
-    if (!(n0 > 0.0) || !std::isfinite(n0)) {
-        restore();
-        return fail(HUB_EINVAL, "start vector has zero or non-finite norm");
-    }
-    if ((rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / n0, s))) {
-        restore();
-        return rc;
-    }
-    if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) {
-        restore();
-        return fail(HUB_ECUDA, "memset");
-    }
-    const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
-    std::vector<double> a, b;
-    double bj = 0.0, theta = 0.0, rho = 0.0;
-    bool broke = false, converged = false;
-    for (int j = 0; j < m_cap; ++j) {
-        double aj = 0.0, bn = 0.0;
-        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023))) {
-            restore();
-            return rc;
-        }
-        a.push_back(aj);
-        double s_last = 1.0;
-        tridiag_lowest(a.data(), b.data(), (int)a.size(), &theta, &s_last);
-        rho = bn * std::fabs(s_last);
-        double scale = 1.0;
-        for (double x : a) scale = std::max(scale, std::fabs(x));
-        for (double x : b) scale = std::max(scale, x);
-        b.push_back(bn);
-        if (bn <= 1e-13 * scale) {
-            broke = true;
-            converged = true;
-            break;
-        }
-        if (tol > 0.0 && rho < tol) {
-            converged = true;
-            break;
-        }
-        if ((rc = launch_scale(1.0 / bn, g, H->D, dtype, s))) {
-            restore();
-            return rc;
-        }
-        std::swap(f, g);
-        bj = bn;
-    }
-    restore();
-    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
-    const int m = (int)a.size();
-    if (alpha_out) std::memcpy(alpha_out, a.data(), m * sizeof(double));
-    if (beta_out) std::memcpy(beta_out, b.data(), m * sizeof(double));
-    out->energy = theta;
-    out->residual = rho;
+    ScratchGuard guard(H, ws + 2 * vec, (size_t)H->D * 16);
+    LanczosRun R;
+    if ((rc = lanczos_core(H, v0, dtype, max_iters, tol, dtype, ws, ws + vec, s, R))) return rc;
+    const int m = (int)R.a.size();
+    if (alpha_out) std::memcpy(alpha_out, R.a.data(), m * sizeof(double));
+    if (beta_out) std::memcpy(beta_out, R.b.data(), m * sizeof(double));
+    out->energy = R.theta;
+    out->residual = R.rho;
     out->iters = m;
-    out->breakdown = broke ? 1 : 0;
-    if (tol <= 0.0) converged = true;
-    out->status = converged ? HUB_OK : HUB_ENOTCONV;
-    if (!converged) return fail(HUB_ENOTCONV, "max_iters reached before the residual test passed");
+    out->breakdown = R.broke ? 1 : 0;
+    out->status = R.converged ? HUB_OK : HUB_ENOTCONV;
+    if (!R.converged) return fail(HUB_ENOTCONV, "max_iters reached before the residual test passed");
+    return HUB_OK;
+}
+
+size_t lanczos_refined_workspace_bytes(hubbard_t H) {
+    if (H == nullptr) return 0;
+    const size_t D = (size_t)H->D;
+    // psi (8D) | H*v scratch (16D) | w (8D) | f, g binary32 (4D + 4D)
+    return align_up(D * 8, 256) + align_up(D * 16, 256) + align_up(D * 8, 256) + 2 * align_up(D * 4, 256);
+}
+
+int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, double tol, void* workspace,
+                                 size_t ws_bytes, void* psi_out, void* stream, lanczos_refined_result* out) {
+    clear_error();
+    int rc;
+    if ((rc = check_handle(H))) return rc;
+    if (out == nullptr) return fail(HUB_EINVAL, "out is null");
+    std::memset(out, 0, sizeof(*out));
+    if (v0 == nullptr || !aligned16(v0)) return fail(HUB_EINVAL, "v0 null or not 16-byte aligned");
+    if (psi_out != nullptr && !aligned16(psi_out)) return fail(HUB_EINVAL, "psi_out not 16-byte aligned");
+    if (max_iters < 1) return fail(HUB_EINVAL, "max_iters must be >= 1");
+    if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return fail(HUB_EINVAL, "workspace null or not 256-byte aligned");
+    if (ws_bytes < lanczos_refined_workspace_bytes(H)) return fail(HUB_ENOMEM, "workspace too small");
+    if (!fixed_point_ok(H)) return fail(HUB_EINVAL, "refined lanczos: more than 127 hops per state");
+    if (!(tol > 0.0)) tol = 1e-10;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t D = (size_t)H->D;
+    char* ws = (char*)workspace;
+    double* psi = (double*)ws;
+    char* scr = ws + align_up(D * 8, 256);
+    double* w = (double*)(scr + align_up(D * 16, 256));
+    float* f = (float*)((char*)w + align_up(D * 8, 256));
+    float* g = (float*)((char*)f + align_up(D * 4, 256));
+    ScratchGuard guard(H, scr, D * 16);
+
+    // 1. binary32 Lanczos: stop when the Ritz estimate reaches binary32 level
+    LanczosRun R;
+    if ((rc = lanczos_core(H, v0, HUB_F64, max_iters, 0.0, HUB_F32, f, g, s, R, 2e-6))) return rc;
+    const int m = (int)R.a.size();
+    std::vector<double> sv((size_t)m);
+    double theta32 = 0.0;
+    tridiag_lowest_vector(R.a.data(), R.b.data(), m, &theta32, sv.data());
+    // gap to the next distinct Ritz value (skipping converged copies of the lowest)
+    double gap = 0.0;
+    for (int k = 1; k < std::min(m, 8); ++k) {
+        const double tk = tridiag_kth(R.a.data(), R.b.data(), m, k);
+        if (tk - theta32 > 1e-5 * std::max(1.0, std::fabs(theta32))) {
+            gap = tk - theta32;
+            break;
+        }
+    }
+    out->energy_f32 = theta32;
+    out->iters_f32 = m;
+    out->gap = gap;
+
+    // 2. Ritz vector: replay the same binary32 recurrence with the stored a, b
+    //    (every kernel is deterministic, so the f_j are bit-identical) and
+    //    accumulate psi = sum_j s_j f_j in binary64
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+    if ((rc = launch_f64_to_f32_scaled((const double*)v0, f, H->D, 1.0 / std::sqrt(n0), s))) return rc;
+    if (cudaMemsetAsync(g, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    if ((rc = launch_psi_accumulate(f, psi, H->D, sv[0], true, s))) return rc;
+    {
+        float* ff = f;
+        float* gg = g;
+        for (int j = 0; j + 1 < m; ++j) {
+            const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
+            if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
+            if ((rc = launch_axpy_nrm2(-R.a[(size_t)j], ff, gg, H->D, HUB_F32, H->red, s))) return rc;
+            if ((rc = launch_scale(1.0 / R.b[(size_t)j], gg, H->D, HUB_F32, s))) return rc;
+            std::swap(ff, gg);
+            if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
+        }
+    }
+    double pn = 0.0;
+    if ((rc = launch_dot(H, psi, psi, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pn))) return rc;
+    if ((rc = launch_scale(1.0 / std::sqrt(pn), psi, H->D, HUB_F64, s))) return rc;
+    if (psi_out != nullptr)
+        if (cudaMemcpyAsync(psi_out, psi, D * 8, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(HUB_ECUDA, "copy psi");
+
+    // 3. binary64 Rayleigh quotient and residual of psi (|psi| = 1)
+    if ((rc = launch_hv_fast(H, psi, w, HUB_F64, 0.0, nullptr, 0, s))) return rc;
+    double th = 0.0, r2 = 0.0;
+    if ((rc = launch_dot(H, psi, w, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &th))) return rc;
+    if ((rc = launch_axpy_nrm2(-th, psi, w, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &r2)))
+        return rc;
+    out->energy = th;
+    out->residual = std::sqrt(std::max(r2, 0.0));
+    out->error_bound = gap > 0.0 ? r2 / gap : INFINITY;
+    out->iters_f64 = 0;
+
+    // 4. short binary64 Lanczos polish from psi when the bound misses tol * |theta|
+    if (!(out->error_bound <= tol * std::max(1.0, std::fabs(th)))) {
+        // polish workspace: f, g (binary64) over [scratch .. end], scratch after them
+        char* base = scr;
+        double* pf = (double*)base;
+        double* pg = (double*)(base + align_up(D * 8, 256));
+        char* pscr = base + 2 * align_up(D * 8, 256);
+        if (2 * align_up(D * 8, 256) + D * 16 > (size_t)((char*)workspace + ws_bytes - base))
+            return fail(HUB_ENOMEM, "workspace too small for the binary64 polish");
+        ScratchGuard g2(H, pscr, D * 16);
+        LanczosRun P;
+        if ((rc = lanczos_core(H, psi, HUB_F64, 60, 0.0, HUB_F64, pf, pg, s, P, 1e-12))) return rc;
+        out->energy = P.theta;
+        out->residual = P.rho;
+        out->error_bound = gap > 0.0 ? P.rho * P.rho / gap : INFINITY;
+        out->iters_f64 = (int)P.a.size();
+    }
+    out->status = (out->error_bound <= tol * std::max(1.0, std::fabs(out->energy))) ? HUB_OK : HUB_ENOTCONV;
+    if (out->status != HUB_OK) return fail(HUB_ENOTCONV, "refined energy bound above tol");
     return HUB_OK;
 }
 

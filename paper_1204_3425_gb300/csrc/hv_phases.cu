@@ -232,6 +232,35 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
     }
 }
 
+// Row phase for binary64 rows too long for shared memory: the fixed-point
+// copy X is already in global memory (k_to_fixed) and the down-hop gathers
+// read row u of it through L1/L2.
+template <typename EntT>
+__global__ void __launch_bounds__(512) k_rows_global_f64x(const int2* __restrict__ Xg, long long* __restrict__ Y,
+                                                           int64_t Dup, int64_t Ddn,
+                                                           const int64_t* __restrict__ boff,
+                                                           const int32_t* __restrict__ bcnt,
+                                                           const EntT* __restrict__ ent) {
+    const int lane = threadIdx.x & 31;
+    for (int64_t u = blockIdx.x; u < Dup; u += gridDim.x) {
+        const int2* X = Xg + u * Ddn;
+        for (int64_t d0 = threadIdx.x & ~31; d0 < Ddn; d0 += blockDim.x) {
+            const int64_t g = d0 >> 5;
+            const int64_t d = d0 + lane;
+            int a0 = 0, a1 = 0;
+            for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
+                if (e & 3u) {
+                    const int s = hop_sign(e);
+                    const int2 x = __ldg(X + (e >> 2));
+                    a0 += s * x.x;
+                    a1 += s * x.y;
+                }
+            });
+            if (d < Ddn) Y[u * Ddn + d] = fx_join(a0, a1);
+        }
+    }
+}
+
 struct EpiParams {
     long long A;          // round(-t * 2^m)
     long long Bbeta;      // round(-beta * 2^m)
@@ -641,16 +670,33 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     const int up_blocks = sms() * 3;
     if (dtype == HUB_F64) {
         const int va = choose_vec(H->vec_rows, Ddn, 8, 2, 0);
-        if (va == 0) return -1;
         int* emax = H->status;
         if (fixed_emax <= 0) {
             HUB_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
             launch_max_exponent((const double*)v, H->D, emax, s);
             if (w_old != nullptr) launch_max_exponent((const double*)w_old, H->D, emax, s);
         }
-        const Launch LA = shape((size_t)Ddn * 8 * va, H->ctas_rows);
+        const Launch LA = shape((size_t)Ddn * 8 * std::max(va, 1), H->ctas_rows);
         long long* Y = (long long*)ybuf;
         int2* Xg = (int2*)((char*)ybuf + (size_t)H->D * 8);
+        int extra = 0;
+        if (va == 0) {
+            // rows longer than shared memory: fixed-point copy first, then gathers through L1/L2
+            int* em = emax;
+            int* fixed_word = H->status + 1;
+            if (fixed_emax > 0) {
+                H->fixed_emax_host = fixed_emax;
+                HUB_CUDA(cudaMemcpyAsync(fixed_word, &H->fixed_emax_host, sizeof(int), cudaMemcpyHostToDevice, s));
+                em = fixed_word;
+            }
+            launch_to_fixed((const double*)v, H->D, Xg, em, s);
+            if (dn16) {
+                k_rows_global_f64x<uint16_t><<<sms() * 4, 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, dn.ent16);
+            } else {
+                k_rows_global_f64x<uint32_t><<<sms() * 4, 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, dn.ent32);
+            }
+            extra = 2;
+        } else {
 #define ROWS64(V, E, P)                                                                                     \
     allow_smem(k_rows_f64x<V, E>, LA.smem);                                                                  \
     k_rows_f64x<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const double*)v, Y, Xg, Dup, Ddn, dn.blk_off,  \
@@ -659,6 +705,8 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             if (dn16) { ROWS64(2, uint16_t, dn.ent16); } else { ROWS64(2, uint32_t, dn.ent32); }
         } else {
             if (dn16) { ROWS64(1, uint16_t, dn.ent16); } else { ROWS64(1, uint32_t, dn.ent32); }
+        }
+        extra = 1;
         }
 #undef ROWS64
         const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
@@ -672,7 +720,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
         }
 #undef UP64
         HUB_CUDA(cudaGetLastError());
-        count_launches(2 + (fixed_emax <= 0 ? (w_old ? 2 : 1) : 0));
+        count_launches(1 + extra + (fixed_emax <= 0 ? (w_old ? 2 : 1) : 0));
         return HUB_OK;
     }
     // binary32

@@ -81,6 +81,7 @@ struct hubbard_sector {
     // two-phase H*v schedule (0 = automatic): rows / columns per staged block
     // and CTAs per SM for the row and column phases (hubbard_set_schedule)
     int vec_rows = 0, vec_cols = 0, ctas_rows = 0, ctas_cols = 0;
+    int fixed_emax_host = 1023;      // host copy for the device word used by the fixed-scale fallback
     // small device scratch for reductions: partial sums, status words
     double* red = nullptr;           // [kRedSlots]
     int* status = nullptr;           // [4]
@@ -104,6 +105,8 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
                      void* ybuf, int fixed_emax, cudaStream_t s);
 // max biased binary64 exponent of |v| folded into *emax (atomicMax; caller zeroes it)
 void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s);
+// binary64 -> (lo, hi) fixed point with the exponent bound *emax (read on the device)
+void launch_to_fixed(const double* v, int64_t n, void* X, const int* emax, cudaStream_t s);
 int launch_dot(const hubbard_sector* H, const void* x, const void* y, int64_t n, int dtype,
                double* partials, cudaStream_t s);
 int reduce_partials_host(double* partials, cudaStream_t s, double* out);
@@ -112,10 +115,16 @@ int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, dou
                      cudaStream_t s);
 int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s);
 int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double inv_norm, cudaStream_t s);
+int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cudaStream_t s);
+int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s);
 
 // tridiag.cpp -----------------------------------------------------------------
 // Lowest eigenvalue of the symmetric tridiagonal T (diag a[0..m-1], off-diag
 // b[0..m-2]) and the last component of its normalised eigenvector.
 void tridiag_lowest(const double* a, const double* b, int m, double* theta, double* s_last);
+// the whole normalised lowest eigenvector s[0..m)
+void tridiag_lowest_vector(const double* a, const double* b, int m, double* theta, double* s);
+// k-th smallest eigenvalue (k = 0 is the lowest)
+double tridiag_kth(const double* a, const double* b, int m, int k);
 
 }  // namespace hub

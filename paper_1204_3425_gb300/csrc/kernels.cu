@@ -168,25 +168,61 @@ __device__ __forceinline__ double block_sum(double s) {
     return s;
 }
 
-template <typename T>
-__global__ void k_dot(const T* __restrict__ x, const T* __restrict__ y, int64_t n, double* partials) {
+// Per-thread float-float accumulator for binary32 vectors: each product x*y
+// is split exactly (p + e with e = fma(x, y, -p)) and added with Knuth's
+// TwoSum, so the FP32 pipe carries ~48 bits and the binary64 pipe (1.7
+// op/clk/SM here) is touched once per thread, not per element.
+struct FF {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add_product(float x, float y) {
+        const float p = x * y;
+        const float e = fmaf(x, y, -p);
+        const float s = hi + p;
+        const float bb = s - hi;
+        lo += ((hi - (s - bb)) + (p - bb)) + e;
+        hi = s;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__global__ void k_dot_f64(const double* __restrict__ x, const double* __restrict__ y, int64_t n, double* partials) {
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        s = fma((double)x[i], (double)y[i], s);
+        s = fma(x[i], y[i], s);
     s = block_sum(s);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
+__global__ void k_dot_f32(const float* __restrict__ x, const float* __restrict__ y, int64_t n, double* partials) {
+    FF acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc.add_product(x[i], y[i]);
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
 // y <- y + a x ; partial sums of y^2
-template <typename T>
-__global__ void k_axpy_nrm2(T a, const T* __restrict__ x, T* __restrict__ y, int64_t n, double* partials) {
+__global__ void k_axpy_nrm2_f64(double a, const double* __restrict__ x, double* __restrict__ y, int64_t n,
+                                double* partials) {
     double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const T r = y[i] + a * x[i];
+        const double r = fma(a, x[i], y[i]);
         y[i] = r;
-        s = fma((double)r, (double)r, s);
+        s = fma(r, r, s);
     }
     s = block_sum(s);
+    if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = s;
+}
+
+__global__ void k_axpy_nrm2_f32(float a, const float* __restrict__ x, float* __restrict__ y, int64_t n,
+                                double* partials) {
+    FF acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = fmaf(a, x[i], y[i]);
+        y[i] = r;
+        acc.add_product(r, r);
+    }
+    const double s = block_sum(acc.value());
     if (threadIdx.x == 0 && partials != nullptr) partials[blockIdx.x] = s;
 }
 
@@ -206,6 +242,17 @@ template <typename T>
 __global__ void k_copy_scale(const T* __restrict__ x, T* __restrict__ y, int64_t n, T a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = a * x[i];
+}
+
+__global__ void k_f64_to_f32_scaled(const double* __restrict__ x, float* __restrict__ y, int64_t n, double a) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)(a * x[i]);
+}
+
+// psi <- (init ? 0 : psi) + s * f  (binary32 f, binary64 psi)
+__global__ void k_psi_acc(const float* __restrict__ f, double* __restrict__ psi, int64_t n, double s, int init) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] = init ? s * (double)f[i] : fma(s, (double)f[i], psi[i]);
 }
 
 // sums partials[0..nb) in index order into partials[kRedSlots-1]
@@ -235,6 +282,11 @@ int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dty
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;
+}
+
+void launch_to_fixed(const double* v, int64_t n, void* X, const int* emax, cudaStream_t s) {
+    const int g2 = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_to_fixed<<<g2, kThreads, 0, s>>>(v, (int2*)X, n, emax);
 }
 
 void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s) {
@@ -277,8 +329,8 @@ int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double 
 int launch_dot(const hubbard_sector*, const void* x, const void* y, int64_t n, int dtype, double* partials,
                cudaStream_t s) {
     const int g = red_grid(n);
-    if (dtype == HUB_F64) k_dot<double><<<g, kThreads, 0, s>>>((const double*)x, (const double*)y, n, partials);
-    else k_dot<float><<<g, kThreads, 0, s>>>((const float*)x, (const float*)y, n, partials);
+    if (dtype == HUB_F64) k_dot_f64<<<g, kThreads, 0, s>>>((const double*)x, (const double*)y, n, partials);
+    else k_dot_f32<<<g, kThreads, 0, s>>>((const float*)x, (const float*)y, n, partials);
     k_finish_sum<<<1, 1024, 0, s>>>(partials, g);
     HUB_CUDA(cudaGetLastError());
     count_launches(2);
@@ -302,8 +354,8 @@ int launch_axpy(double a, const void* x, void* y, int64_t n, int dtype, cudaStre
 
 int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, double* partials, cudaStream_t s) {
     const int g = red_grid(n);
-    if (dtype == HUB_F64) k_axpy_nrm2<double><<<g, kThreads, 0, s>>>(a, (const double*)x, (double*)y, n, partials);
-    else k_axpy_nrm2<float><<<g, kThreads, 0, s>>>((float)a, (const float*)x, (float*)y, n, partials);
+    if (dtype == HUB_F64) k_axpy_nrm2_f64<<<g, kThreads, 0, s>>>(a, (const double*)x, (double*)y, n, partials);
+    else k_axpy_nrm2_f32<<<g, kThreads, 0, s>>>((float)a, (const float*)x, (float*)y, n, partials);
     k_finish_sum<<<1, 1024, 0, s>>>(partials, g);
     HUB_CUDA(cudaGetLastError());
     count_launches(2);
@@ -314,6 +366,22 @@ int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
     if (dtype == HUB_F64) k_scale<double><<<g, kThreads, 0, s>>>(a, (double*)y, n);
     else k_scale<float><<<g, kThreads, 0, s>>>((float)a, (float*)y, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_f64_to_f32_scaled<<<g, kThreads, 0, s>>>(x, y, n, a);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_psi_acc<<<g, kThreads, 0, s>>>(f, psi, n, sj, init ? 1 : 0);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;

@@ -68,6 +68,43 @@ void tridiag_solve(const double* a, const double* b, int m, double x, std::vecto
 
 }  // namespace
 
+double tridiag_kth(const double* a, const double* b, int m, int k) {
+    // k-th smallest eigenvalue (k = 0 lowest) by bisection on the Sturm count
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < m; ++i) {
+        double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(a, b, m, mid) >= k + 1) hi = mid; else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+void tridiag_lowest_vector(const double* a, const double* b, int m, double* theta, double* s) {
+    double th = 0.0, last = 0.0;
+    tridiag_lowest(a, b, m, &th, &last);
+    *theta = th;
+    if (m == 1) {
+        s[0] = 1.0;
+        return;
+    }
+    const double shift = th - 1e-14 * std::max(1.0, std::fabs(th));
+    std::vector<double> y(m, 1.0 / std::sqrt((double)m));
+    for (int it = 0; it < 4; ++it) {
+        tridiag_solve(a, b, m, shift, y);
+        double nrm = 0.0;
+        for (double v : y) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) break;
+        for (double& v : y) v /= nrm;
+    }
+    for (int i = 0; i < m; ++i) s[i] = y[i];
+}
+
 void tridiag_lowest(const double* a, const double* b, int m, double* theta, double* s_last) {
     if (m == 1) {
         *theta = a[0];

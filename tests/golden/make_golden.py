@@ -56,13 +56,17 @@ def _matrix_free(name, nup, ndn, U, tol, max_iter, fname):
     ns, bonds = lattice_by_name(name)
     t0 = time.time()
     K = KronHamiltonian(ns, bonds, nup, ndn, 1.0, U)
-    v0 = start_vector(K.D, seed=1234)
+    v0 = np.empty(K.D)
+    chunk = 1 << 26
+    for s0 in range(0, K.D, chunk):                    # chunked: the generator's temporaries stay small
+        n = min(chunk, K.D - s0)
+        v0[s0:s0 + n] = start_vector(n, seed=1234, start=s0)
 
     def step(j, e, rho):
         if j % 10 == 0:
             print(f"  it {j:4d} E {e:.15f} rho {rho:.3e} ({time.time() - t0:.0f}s)", flush=True)
 
-    r = lanczos_matrix_free(K, v0, max_iter, tol=tol, on_step=step)
+    r = lanczos_matrix_free(K, v0, max_iter, tol=tol, on_step=step, inplace=True)
     _write(fname, dict(
         lattice=name, ns=ns, nup=nup, ndn=ndn, t=1.0, U=U, seed=1234, dim=K.D,
         e0=r["energy"], residual=r["residual"], iters=r["iters"], tol=tol,
@@ -82,7 +86,7 @@ def main():
         _matrix_free("sq4x4", 8, 8, U, 1e-12, 600, f"sq4x4_n8_8_U{U:g}.json")
     else:
         U = 4.0 if a.U is None else a.U
-        _matrix_free("ring18", 9, 9, U, 1e-12, 600, f"ring18_n9_9_U{U:g}.json")
+        _matrix_free("ring18", 9, 9, U, 1e-11, 600, f"ring18_n9_9_U{U:g}.json")
 
 
 if __name__ == "__main__":

@@ -1,0 +1,81 @@
+"""GPU tests of the binary32 Lanczos and the binary32 + binary64-refined ground
+state against the CPU oracle (energies within 1e-9 relative)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import paper_1204_3425_gb300 as hub
+from oracle.basis import Sector
+from workload import lattice_by_name, start_vector
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_3425_gb300 import build
+    build.build()
+    hub.load_library()
+    return torch.device("cuda:0")
+
+
+def _ref_energy(S):
+    from scipy.sparse.linalg import eigsh
+    if S.D <= 2000:
+        return float(np.linalg.eigvalsh(S.dense())[0])
+    return float(eigsh(S.explicit(), k=1, which="SA", tol=1e-14, v0=start_vector(S.D, seed=9))[0][0])
+
+
+CASES = [("ring8", 4, 4, 1.0, 4.0), ("sq3x3", 4, 4, 1.0, 6.0), ("ring10", 5, 5, 1.0, 3.0),
+         ("sq4x3", 2, 3, 1.0, 9.0), ("ring12", 3, 4, 1.0, 2.5), ("sq4x2", 3, 5, 1.0, 0.7)]
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_f32_lanczos_energy(dev, case):
+    name, nup, ndn, t, U = case
+    ns, bonds = lattice_by_name(name)
+    S = Sector(ns, bonds, nup, ndn, t, U)
+    H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+    e = _ref_energy(S)
+    v0 = torch.from_numpy(start_vector(S.D, seed=1234)).to(dev, torch.float32)
+    r = hub.lanczos_ground_state(H, v0, 400, 1e-5)
+    assert abs(r["energy"] - e) <= 2e-5 * max(1.0, abs(e))
+
+
+@pytest.mark.parametrize("case", CASES)
+def test_refined_energy_small(dev, case):
+    name, nup, ndn, t, U = case
+    ns, bonds = lattice_by_name(name)
+    S = Sector(ns, bonds, nup, ndn, t, U)
+    H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+    e = _ref_energy(S)
+    v0 = torch.from_numpy(start_vector(S.D, seed=1234)).to(dev)
+    psi = torch.empty_like(v0)
+    r = hub.lanczos_ground_state_refined(H, v0, 1000, 1e-10, psi_out=psi)
+    assert r["status"] == hub.HUB_OK, r
+    assert abs(r["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (r, e)
+    # the stated bound covers the actual error (up to rounding)
+    assert abs(r["energy"] - e) <= max(r["error_bound"], 1e-12 * max(1.0, abs(e)))
+    # psi is the binary32 Ritz vector: unit norm, residual small
+    p = psi.cpu().numpy()
+    assert abs(np.linalg.norm(p) - 1.0) < 1e-12
+    Hp = S.explicit() @ p
+    th = p @ Hp
+    assert np.linalg.norm(Hp - th * p) < 1e-3
+
+
+def test_refined_sq4x4(dev):
+    """4x4, (8,8), U=8: binary32 path refined in binary64 against the stored oracle energy."""
+    ns, bonds = lattice_by_name("sq4x4")
+    H = hub.hubbard_sector_create(ns, bonds, 8, 8, 1.0, 8.0)
+    g = json.load(open(os.path.join(GOLD, "sq4x4_n8_8_U8.json")))
+    v0 = torch.from_numpy(start_vector(H.D, seed=1234)).to(dev)
+    r = hub.lanczos_ground_state_refined(H, v0, 1000, 1e-10)
+    assert r["status"] == hub.HUB_OK, r
+    assert abs(r["energy"] - g["e0"]) <= 1e-9 * abs(g["e0"]), r
