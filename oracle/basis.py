@@ -137,21 +137,25 @@ class Sector:
     def rows_of_hv(self, J, v):
         """(H v)[J] for the sampled indices J only: sum over <J|H|J'> v[J'].
 
+        v is an array, or a callable returning v at an index array (so that
+        sectors too large for host memory can be sampled).
+
         <J|H|J'> is nonzero for J' = J (diagonal) and for the states J'
         with c+_a c_b |J'> ~ |J>, i.e. |J'> ~ c+_b c_a |J>; the same sign
         appears both ways (the hopping matrix is real symmetric).
         """
         J = np.asarray(J, dtype=np.int64)
+        vat = v if callable(v) else (lambda idx: v[idx])
         up, dn = self.unrank(J)
         occ = self._modes(up, dn)
-        out = self.U * np.bitwise_count(up & dn).astype(np.float64) * v[J]
+        out = self.U * np.bitwise_count(up & dn).astype(np.float64) * vat(J)
         mask_up = (np.int64(1) << self.ns) - 1
         for a, b in self._terms():
             valid, new, sign = self._hop(occ, a, b)
             if not np.any(valid):
                 continue
             Jp = self.rank(new[valid] & mask_up, new[valid] >> self.ns)
-            out[valid] += -self.t * sign[valid] * v[Jp]
+            out[valid] += -self.t * sign[valid] * vat(Jp)
         return out
 
     # ---- per-spin hopping tables (for bit-exact comparison) ------------

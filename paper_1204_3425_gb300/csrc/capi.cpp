@@ -776,7 +776,9 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
             return fail(HUB_ENOMEM, "workspace too small for the binary64 polish");
         ScratchGuard g2(H, pscr, D * 16);
         LanczosRun P;
-        if ((rc = lanczos_core(H, psi, HUB_F64, 60, 0.0, HUB_F64, pf, pg, s, P, 1e-12))) return rc;
+        // stop as soon as rho^2 / gap meets the requested bound
+        const double rho_target = std::sqrt(tol * std::max(1.0, std::fabs(th)) * std::max(gap, 1e-300));
+        if ((rc = lanczos_core(H, psi, HUB_F64, 60, gap > 0.0 ? rho_target : 1e-13, HUB_F64, pf, pg, s, P))) return rc;
         out->energy = P.theta;
         out->residual = P.rho;
         out->error_bound = gap > 0.0 ? P.rho * P.rho / gap : INFINITY;

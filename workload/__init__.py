@@ -6,8 +6,8 @@ arithmetic (no basis, ranking, signs, H*v or Lanczos), so both the CPU
 oracle and the CUDA path may draw their inputs from it.
 """
 from .lattices import ring, square, dimer, lattice_by_name
-from .vectors import splitmix64, start_vector
+from .vectors import splitmix64, start_vector, start_vector_into, start_vector_at
 from .requests import batch_sectors, serve_requests
 
-__all__ = ["ring", "square", "dimer", "lattice_by_name", "splitmix64",
-           "start_vector", "batch_sectors", "serve_requests"]
+__all__ = ["ring", "square", "dimer", "lattice_by_name", "splitmix64", "start_vector", "start_vector_into",
+           "start_vector_at", "batch_sectors", "serve_requests"]

@@ -39,3 +39,20 @@ def start_vector(n, seed=1234, start=0, dtype=np.float64):
     x = (z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
     v = 2.0 * x - 1.0
     return v.astype(dtype, copy=False)
+
+
+def start_vector_into(out, seed=1234, chunk=1 << 25):
+    """Fill a preallocated float64/float32 array with the seeded start vector, chunk by chunk."""
+    n = out.shape[0]
+    for s0 in range(0, n, chunk):
+        m = min(chunk, n - s0)
+        out[s0:s0 + m] = start_vector(m, seed=seed, start=s0, dtype=out.dtype)
+    return out
+
+
+def start_vector_at(indices, seed=1234):
+    """Entries of the seeded start vector at arbitrary indices (float64)."""
+    idx = np.asarray(indices, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = splitmix64(np.uint64(seed) * np.uint64(1 << 40) + idx)
+    return 2.0 * ((z >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)) - 1.0
