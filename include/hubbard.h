@@ -261,6 +261,59 @@ size_t lanczos_refined_workspace_bytes(hubbard_t H);
 int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, double tol, void* workspace,
                                  size_t ws_bytes, void* psi_out, void* stream, lanczos_refined_result* out);
 
+/* ---------------------------------------------------------------------------
+ * Many sectors solved in one persistent launch (Algorithm 1 for every
+ * sector, entirely on the device; the paper notes that small sectors leave
+ * the GPU idle, Sec. 5).  A batch owns the hopping tables of all its sectors
+ * (tables are shared between sectors with the same lattice and filling).
+ * Every sector's solve is run by a team of CTAs of one cooperative kernel;
+ * sectors up to ~12800 elements per CTA keep their fixed-point Lanczos vector
+ * in shared memory.  Team size = ceil(D / elems_per_cta) (the schedule knob
+ * that hubbard_batch_autotune chooses).  Results do not depend on which other
+ * sectors share the batch (fixed-order reductions).
+ * ------------------------------------------------------------------------- */
+typedef struct hubbard_batch* hubbard_batch_t;
+
+typedef struct {
+    int32_t ns, nup, ndn, n_bonds;
+    const int32_t* bonds;      /* host, 2 * n_bonds, same rules as hubbard_sector_create */
+    double t, U;
+} hubbard_sector_desc;
+
+/* Builds and uploads the tables of n_sectors sectors (host descriptors). */
+int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubbard_batch_t* out);
+void hubbard_batch_destroy(hubbard_batch_t B);
+
+/* offsets[n_sectors + 1]: sector i's start vector occupies elements
+ * offsets[i] .. offsets[i] + D_i of the concatenated binary64 v0 buffer
+ * (offsets are even, so every sector is 16-byte aligned). */
+int hubbard_batch_vector_offsets(hubbard_batch_t B, int64_t* offsets);
+
+/* Device workspace bytes for hubbard_batch_solve_async with this max_iters. */
+size_t hubbard_batch_workspace_bytes(hubbard_batch_t B, int max_iters);
+
+/* Elements per CTA of a sector's team (>= 1). */
+int hubbard_batch_set_schedule(hubbard_batch_t B, int64_t elems_per_cta);
+
+/* One launch solving every sector to rho < tol * max(1, |theta|) (or
+ * breakdown, or max_iters capped at D).  v0_all: device, 16-byte aligned.
+ * Asynchronous on `stream`; results stay in the workspace until
+ * hubbard_batch_results.  The first call for a given max_iters / schedule
+ * uploads descriptors synchronously; later calls only enqueue two memsets and
+ * one cooperative launch, so they can be captured in a CUDA graph. */
+int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
+                              size_t ws_bytes, void* stream);
+
+/* Copies the per-sector results (host array of n_sectors); synchronises
+ * `stream`.  HUB_ETIMEOUT if a team barrier gave up. */
+int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
+                          lanczos_result* results);
+
+/* Times full solves for elems_per_cta in {2^12 .. 2^17} and keeps the fastest
+ * (written to *chosen).  Synchronises `stream`. */
+int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
+                           size_t ws_bytes, void* stream, int64_t* chosen);
+
 /* Message for the last failing call on this thread ("" if none). */
 const char* hubbard_last_error(void);
 

@@ -53,6 +53,14 @@ SIGNATURES = {
     "hubbard_host_spin_tables": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]),
     "hubbard_kernel_launches": (ctypes.c_uint64, []),
     "lanczos_refined_workspace_bytes": (SZ, [P]),
+    "hubbard_batch_create": (ctypes.c_int, [P, ctypes.c_int, P]),
+    "hubbard_batch_destroy": (None, [P]),
+    "hubbard_batch_vector_offsets": (ctypes.c_int, [P, P]),
+    "hubbard_batch_workspace_bytes": (SZ, [P, ctypes.c_int]),
+    "hubbard_batch_set_schedule": (ctypes.c_int, [P, I64]),
+    "hubbard_batch_solve_async": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P]),
+    "hubbard_batch_results": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
+    "hubbard_batch_autotune": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
     "hubbard_last_error": (ctypes.c_char_p, []),
 }
@@ -277,6 +285,67 @@ def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=Non
     if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
         _check(rc)
     return {f: getattr(res, f) for f, _ in RefinedResult._fields_ if f != "reserved"}
+
+
+class SectorDesc(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int32), ("nup", ctypes.c_int32), ("ndn", ctypes.c_int32),
+                ("n_bonds", ctypes.c_int32), ("bonds", ctypes.c_void_p), ("t", ctypes.c_double),
+                ("U", ctypes.c_double)]
+
+
+class Batch:
+    """Owns a hubbard_batch_t: many sectors solved in one persistent launch."""
+
+    def __init__(self, specs):
+        """specs: list of (ns, bonds, nup, ndn, t, U)."""
+        lib = load_library()
+        self._bond_arrays = [np.ascontiguousarray(np.asarray(b, dtype=np.int32).reshape(-1)) for _, b, *_ in specs]
+        descs = (SectorDesc * len(specs))()
+        for i, ((ns, bonds, nup, ndn, t, U), arr) in enumerate(zip(specs, self._bond_arrays)):
+            descs[i] = SectorDesc(int(ns), int(nup), int(ndn), arr.size // 2,
+                                  arr.ctypes.data if arr.size else None, float(t), float(U))
+        h = ctypes.c_void_p()
+        _check(lib.hubbard_batch_create(descs, len(specs), ctypes.byref(h)))
+        self.handle = h
+        self.n = len(specs)
+        off = np.zeros(self.n + 1, dtype=np.int64)
+        _check(lib.hubbard_batch_vector_offsets(h, off.ctypes.data))
+        self.offsets = off
+
+    def workspace_bytes(self, max_iters):
+        return int(load_library().hubbard_batch_workspace_bytes(self.handle, int(max_iters)))
+
+    def set_schedule(self, elems_per_cta):
+        _check(load_library().hubbard_batch_set_schedule(self.handle, int(elems_per_cta)))
+
+    def solve_async(self, v0_all, max_iters, tol, workspace, stream=None):
+        _check(load_library().hubbard_batch_solve_async(self.handle, _ptr(v0_all), int(max_iters), float(tol),
+                                                        _ptr(workspace), workspace.numel(), _stream(stream)))
+
+    def results(self, workspace, max_iters, stream=None):
+        res = (LanczosResult * self.n)()
+        _check(load_library().hubbard_batch_results(self.handle, _ptr(workspace), int(max_iters), _stream(stream),
+                                                    res))
+        return [dict(energy=r.energy, residual=r.residual, iters=r.iters, status=r.status,
+                     breakdown=bool(r.breakdown)) for r in res]
+
+    def autotune(self, v0_all, max_iters, tol, workspace, stream=None):
+        chosen = I64()
+        _check(load_library().hubbard_batch_autotune(self.handle, _ptr(v0_all), int(max_iters), float(tol),
+                                                     _ptr(workspace), workspace.numel(), _stream(stream),
+                                                     ctypes.byref(chosen)))
+        return chosen.value
+
+    def close(self):
+        if self.handle:
+            load_library().hubbard_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hubbard_kernel_launches():

@@ -1,0 +1,889 @@
+// Many small sectors solved in one persistent launch (Sec. 2.2, Algorithm 1,
+// run entirely on the device for each sector).
+//
+// The paper measured that sectors below ~10 sites leave a GPU idle (Sec. 5:
+// 16 % occupancy at 8 sites).  Here every CTA of one cooperative launch walks
+// a static list of tasks; a task is one sector's whole ground-state solve, run
+// by a team of 1..kMaxTeam CTAs that split the sector's elements.  A solo
+// team keeps the fixed-point copy of its Lanczos vector in shared memory; a
+// larger team keeps it in global memory (L2-resident) and meets at team
+// barriers (bounded waits; a timeout sets an error word and ends the task).
+// Tasks are ordered globally and every CTA takes its own tasks in that order,
+// so team waits cannot form a cycle.  Reductions are summed in a fixed order
+// (block tree, then the team's partials in rank order): the result of a
+// sector does not depend on which other sectors share the launch.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <new>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace hub {
+namespace {
+
+constexpr int kBatchThreads = 512;
+constexpr int kMaxTeam = 32;
+constexpr int kCheckEvery = 4;        // Ritz-value test every few steps
+
+struct SectorDesc {
+    int64_t Dup, Ddn, D;
+    int64_t voff;          // element offset of the sector's vectors in the pools
+    int64_t up_rp, dn_rp;  // offsets of the row pointers in the rowptr pool
+    int64_t up_ent, dn_ent;
+    int64_t up_st, dn_st;
+    int64_t ab;            // offset of its a/b history (2 * max_iters doubles)
+    double t, U;
+    int team;
+    int pad;
+};
+
+struct Task {
+    int sector;
+    int rank;
+};
+
+struct BatchParams {
+    const SectorDesc* sec;
+    const int* cta_ptr;    // [gridDim.x + 1]
+    const Task* tasks;
+    const int32_t* rp;     // pooled row pointers
+    const uint32_t* ent;   // pooled packed hop entries (target << 1) | neg
+    const uint32_t* st;    // pooled basis words
+    const double* v0;      // caller start vectors (concatenated)
+    double* f;             // Lanczos vector pools (workspace)
+    double* g;
+    int2* xg;              // global fixed-point copies (team tasks)
+    double* ab;            // a/b histories
+    double* tri;           // tridiagonal scratch, 4 * max_iters per CTA
+    double* partial;       // [sector][2][kMaxTeam]
+    unsigned int* bar;     // team barrier counters [sector]
+    lanczos_result* res;   // [sector]
+    int* err;              // batch error word
+    int max_iters;
+    double tol;
+    int smem_elems;        // capacity of the shared fixed-point buffer
+    long long spin_limit;  // bounded waits
+};
+
+__device__ __forceinline__ int2 fixed47(double x) {
+    // |x| <= 1: X = round(x 2^47), split as (lo 24 bits, hi)
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7FF);
+    unsigned long long mant = b & ((1ull << 52) - 1);
+    if (e != 0) mant |= (1ull << 52);
+    const int ee = e > 0 ? e : 1;
+    const int rs = max(1023 - ee + 5, 1);
+    long long X = (rs >= 60) ? 0 : (long long)((mant + (1ull << (rs - 1))) >> rs);
+    if (b >> 63) X = -X;
+    return make_int2((int)(X & 0xFFFFFF), (int)(X >> 24));
+}
+
+__device__ __forceinline__ double block_reduce(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    const int nw = blockDim.x >> 5;
+    for (int i = 0; i < nw; ++i) s += red[i];      // same order in every thread
+    return s;
+}
+
+// team barrier number `gen` (1, 2, ...): returns false on timeout
+__device__ bool team_barrier(unsigned int* ctr, int team, unsigned gen, long long limit, int* err, int* flag) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(ctr, 1u);
+        const unsigned target = (unsigned)team * gen;
+        long long it = 0;
+        int ok = 1;
+        while (true) {
+            unsigned v;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+            if (v >= target) break;
+            if (*(volatile int*)err != 0 || ++it > limit) {     // fail fast after any timeout
+                ok = 0;
+                atomicExch(err, (int)HUB_ETIMEOUT);
+                break;
+            }
+            __nanosleep(128);
+        }
+        __threadfence();
+        *flag = ok;
+    }
+    __syncthreads();
+    return *flag != 0;
+}
+
+// ---- device tridiagonal helpers (thread-serial; m <= max_iters) -------------
+// Number of eigenvalues of T_m below x: sign changes of the characteristic
+// polynomials p_0 = 1, p_1 = a_0 - x, p_k = (a_{k-1} - x) p_{k-1} - b_{k-2}^2 p_{k-2}
+// (Sturm sequence).  No division (the binary64 divide is slow on this part);
+// both terms are rescaled by 2^-600 / 2^600 when they leave a safe range.
+// A zero p_k takes the sign of p_{k-1}.
+__device__ __noinline__ int d_sturm(const double* a, const double* b, int m, double x) {
+    double p0 = 1.0, p1 = a[0] - x;
+    int c = (p1 < 0.0) ? 1 : 0;
+    bool s1 = (p1 != 0.0) ? (p1 < 0.0) : false;       // sign used for counting
+    for (int i = 1; i < m; ++i) {
+        const double p2 = (a[i] - x) * p1 - (b[i - 1] * b[i - 1]) * p0;
+        const bool s2 = (p2 != 0.0) ? (p2 < 0.0) : s1;
+        if (s2 != s1) ++c;
+        s1 = s2;
+        p0 = p1;
+        p1 = p2;
+        const double mag = fmax(fabs(p0), fabs(p1));
+        if (mag > 0x1p600) {
+            p0 *= 0x1p-600;
+            p1 *= 0x1p-600;
+        } else if (mag < 0x1p-600 && mag > 0.0) {
+            p0 *= 0x1p600;
+            p1 *= 0x1p600;
+        }
+    }
+    return c;
+}
+
+// lowest eigenvalue of T_m and |last component| of its unit eigenvector.
+// prev: the lowest Ritz value of an earlier T_{m'} (m' < m) or NaN; the lowest
+// Ritz value never increases with m (interlacing), so prev bounds it above.
+__device__ __noinline__ void d_tridiag(const double* a, const double* b, int m, double* w, double prev,
+                                       double* theta, double* slast) {
+    double glo = a[0], ghi = a[0];
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+        glo = fmin(glo, a[i] - r);
+        ghi = fmax(ghi, a[i] + r);
+    }
+    double lo = glo, hi = ghi;
+    if (prev == prev) {                                  // warm start from the previous value
+        const double h = prev + 1e-12 * fmax(1.0, fabs(prev));
+        if (h < ghi && d_sturm(a, b, m, h) >= 1) {
+            hi = h;
+            double step = 1e-6 * fmax(1.0, fabs(prev));
+            while (true) {
+                const double l = prev - step;
+                if (l <= glo) break;
+                if (d_sturm(a, b, m, l) == 0) {
+                    lo = l;
+                    break;
+                }
+                hi = l;
+                step *= 16.0;
+            }
+        }
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (d_sturm(a, b, m, mid) >= 1) hi = mid; else lo = mid;
+        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
+    }
+    const double th = 0.5 * (lo + hi);
+    *theta = th;
+    if (m == 1) {
+        *slast = 1.0;
+        return;
+    }
+    // inverse iteration, banded LU with partial pivoting on T - x I
+    double* d = w;
+    double* u1 = w + m;
+    double* u2 = w + 2 * m;
+    double* y = w + 3 * m;
+    const double x = th - 1e-14 * fmax(1.0, fabs(th));
+    for (int i = 0; i < m; ++i) y[i] = 1.0;
+    for (int rep = 0; rep < 3; ++rep) {
+        for (int i = 0; i < m; ++i) {
+            d[i] = a[i] - x;
+            u1[i] = i + 1 < m ? b[i] : 0.0;
+            u2[i] = 0.0;
+        }
+        for (int i = 0; i + 1 < m; ++i) {
+            double sub = b[i];
+            if (fabs(sub) > fabs(d[i])) {
+                double t0 = d[i]; d[i] = sub; sub = t0;
+                double t1 = u1[i]; u1[i] = d[i + 1]; d[i + 1] = t1;
+                double t2 = u2[i]; u2[i] = u1[i + 1]; u1[i + 1] = t2;
+                double t3 = y[i]; y[i] = y[i + 1]; y[i + 1] = t3;
+            }
+            if (d[i] == 0.0) d[i] = 1e-300;
+            const double f = sub / d[i];
+            d[i + 1] -= f * u1[i];
+            u1[i + 1] -= f * u2[i];
+            y[i + 1] -= f * y[i];
+        }
+        if (d[m - 1] == 0.0) d[m - 1] = 1e-300;
+        for (int i = m - 1; i >= 0; --i) {
+            double s = y[i];
+            if (i + 1 < m) s -= u1[i] * y[i + 1];
+            if (i + 2 < m) s -= u2[i] * y[i + 2];
+            y[i] = s / d[i];
+        }
+        double n2 = 0.0;
+        for (int i = 0; i < m; ++i) n2 += y[i] * y[i];
+        const double inv = 1.0 / sqrt(n2);
+        for (int i = 0; i < m; ++i) y[i] *= inv;
+    }
+    *slast = fabs(y[m - 1]);
+}
+
+// Lowest eigenvalue of T_m by multisection over the whole CTA: every thread
+// evaluates the Sturm count at its own point of the bracket, which shrinks by
+// blockDim + 1 per round.  prev (or NaN) is an upper bound from an earlier
+// step (interlacing).  Returns the same value in every thread.
+__device__ double cta_lowest_eig(const double* a, const double* b, int m, double prev, int* flags, double* sh2) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+    double glo = a[0], ghi = a[0];
+    for (int i = 0; i < m; ++i) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
+        glo = fmin(glo, a[i] - r);
+        ghi = fmax(ghi, a[i] + r);
+    }
+    double lo = glo, hi = ghi;
+    if (prev == prev) {
+        // warm bracket [prev - 1e-6, prev + 1e-12] (relative), checked by two threads
+        const double wl = prev - 1e-6 * fmax(1.0, fabs(prev)), wh = prev + 1e-12 * fmax(1.0, fabs(prev));
+        if (tid == 0) flags[0] = (wl > glo) ? (d_sturm(a, b, m, wl) == 0) : 0;
+        if (tid == 1 % nt) flags[1] = (wh < ghi) ? (d_sturm(a, b, m, wh) >= 1) : 0;
+        __syncthreads();
+        const bool okl = flags[0] != 0, okh = flags[1] != 0;
+        __syncthreads();
+        if (okh) hi = wh;
+        if (okl && okh) lo = wl;
+    }
+    for (int round = 0; round < 12; ++round) {
+        if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
+        const double x = lo + (hi - lo) * (double)(tid + 1) / (double)(nt + 1);
+        flags[tid] = d_sturm(a, b, m, x) >= 1;
+        __syncthreads();
+        // counts are monotone in x: the first thread with a positive count bounds the eigenvalue
+        if (flags[tid] && (tid == 0 || !flags[tid - 1])) sh2[0] = (double)tid;
+        if (tid == nt - 1 && !flags[tid]) sh2[0] = (double)nt;
+        __syncthreads();
+        const int k = (int)sh2[0];
+        const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(nt + 1);
+        const double nhi = k == nt ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(nt + 1);
+        lo = nlo;
+        hi = nhi;
+        __syncthreads();
+    }
+    return 0.5 * (lo + hi);
+}
+
+// |last component| of the unit eigenvector of T_m for eigenvalue th: solve the
+// eigen-equations backwards from y_m = 1 (the lowest eigenvector grows in that
+// direction), rescaling by powers of two; returns 1 / |y|.
+__device__ __noinline__ double d_last_component(const double* a, const double* b, int m, double th) {
+    if (m == 1) return 1.0;
+    double y1 = 1.0;                                   // y_m
+    double y0 = -(a[m - 1] - th) / b[m - 2];           // y_{m-1}
+    double n2 = 1.0 + y0 * y0;
+    double scale_log = 0.0;                            // n2 and the y's carry 2^scale_log
+    for (int i = m - 2; i >= 1; --i) {
+        // row i: b_{i-1} y_{i-1} + (a_i - th) y_i + b_i y_{i+1} = 0
+        const double ym = -((a[i] - th) * y0 + b[i] * y1) / b[i - 1];
+        y1 = y0;
+        y0 = ym;
+        n2 += ym * ym;
+        const double mag = fmax(fabs(y0), fabs(y1));
+        if (mag > 0x1p300) {
+            y0 *= 0x1p-300;
+            y1 *= 0x1p-300;
+            n2 *= 0x1p-600;
+            scale_log += 600.0;
+        }
+    }
+    // |y|^2 = n2 * 2^scale_log; y_m was 1 in the unscaled frame
+    return exp2(-0.5 * scale_log) / sqrt(n2);
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams P) {
+    extern __shared__ __align__(16) int2 xs[];
+    __shared__ double red[kBatchThreads / 32];
+    __shared__ int flag, stop;
+    __shared__ double sh_theta, sh_rho;
+    __shared__ double sh_prev;
+    __shared__ int sh_flags[kBatchThreads];
+    __shared__ double sh_k[1];
+    for (int ti = P.cta_ptr[blockIdx.x]; ti < P.cta_ptr[blockIdx.x + 1]; ++ti) {
+        const Task task = P.tasks[ti];
+        const SectorDesc S = P.sec[task.sector];
+        const int team = S.team, rank = task.rank;
+        const int64_t D = S.D, Ddn = S.Ddn, Dup = S.Dup;
+        // the team splits the rows of V (row-major D_up x D_dn)
+        const int64_t rchunk = (Dup + team - 1) / team;
+        const int64_t r0 = ((int64_t)rank * rchunk < Dup) ? (int64_t)rank * rchunk : Dup;
+        const int64_t r1 = (r0 + rchunk < Dup) ? r0 + rchunk : Dup;
+        const int64_t j0 = r0 * Ddn, j1 = r1 * Ddn;
+        const bool in_smem = (team == 1) && (D <= P.smem_elems);
+        // per-warp row buffer for the global-memory path (rows of the fixed-point copy)
+        const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const bool rowbuf = !in_smem && Ddn * nwarps <= P.smem_elems;
+        int2* X = in_smem ? xs : (P.xg + S.voff);
+        double* f = P.f + S.voff;
+        double* g = P.g + S.voff;
+        const double* v0 = P.v0 + S.voff;
+        const int32_t* urp = P.rp + S.up_rp;
+        const int32_t* drp = P.rp + S.dn_rp;
+        const uint32_t* uent = P.ent + S.up_ent;
+        const uint32_t* dent = P.ent + S.dn_ent;
+        const uint32_t* ust = P.st + S.up_st;
+        const uint32_t* dst = P.st + S.dn_st;
+        double* A = P.ab + S.ab;
+        double* B = A + P.max_iters;
+        double* part = P.partial + (int64_t)task.sector * 2 * kMaxTeam;
+        unsigned* ctr = P.bar + task.sector;
+        unsigned gen = 0;
+        bool alive = true;
+        // deterministic team sum: block tree, then the team's partials in rank order
+        auto team_sum = [&](double v) -> double {
+            const double s = block_reduce(v, red);
+            if (team == 1) return s;
+            ++gen;
+            if (threadIdx.x == 0) part[(gen & 1) * kMaxTeam + rank] = s;
+            if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) {
+                alive = false;
+                return 0.0;
+            }
+            double t = 0.0;
+            for (int r = 0; r < team; ++r) t += __ldcg(part + (gen & 1) * kMaxTeam + r);
+            return t;
+        };
+        // f_1 = v0 / |v0|, f_0 = 0
+        double nn = 0.0;
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) nn = fma(v0[j], v0[j], nn);
+        nn = team_sum(nn);
+        if (!alive) return;
+        const double inv0 = 1.0 / sqrt(nn);
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            f[j] = v0[j] * inv0;
+            g[j] = 0.0;
+        }
+        const double scale = -S.t * 0x1p-47;           // -t times the fixed-point unit
+        const int mcap = (int)((int64_t)P.max_iters < D ? (int64_t)P.max_iters : D);
+        double beta = 0.0, theta = 0.0, rho = 0.0;
+        int m = 0, broke = 0, conv = 0;
+        if (threadIdx.x == 0) sh_prev = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no previous value
+        double amax = 1.0;
+        for (int it = 0; it < mcap; ++it) {
+            // fixed-point copy of f (|f| <= 1) for the exact hop sums
+            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) X[j] = fixed47(f[j]);
+            if (team > 1) {
+                ++gen;
+                if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) return;
+            } else {
+                __syncthreads();
+            }
+            // q = H f - beta g  (Eqs. split1), alpha = q . f
+            double ap = 0.0;
+            auto element = [&](int64_t u, int64_t d, int lo, int hi) {
+                const int64_t j = u * Ddn + d;
+                const long long Sx = ((long long)hi << 24) + (long long)lo;
+                const double fj = f[j];
+                const double q = fma(-beta, g[j], fma(S.U * (double)__popc(ust[u] & dst[d]), fj, scale * (double)Sx));
+                g[j] = q;
+                ap = fma(q, fj, ap);
+            };
+            if (in_smem) {
+                // whole fixed-point vector in shared memory: flat loop over elements
+                for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+                    const int64_t u = j / Ddn, d = j - u * Ddn;
+                    int lo = 0, hi = 0;
+                    for (int32_t k = urp[u]; k < urp[u + 1]; ++k) {
+                        const uint32_t e = uent[k];
+                        const int2 x = X[(int64_t)(e >> 1) * Ddn + d];
+                        if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                    }
+                    const int64_t rowb = u * Ddn;
+                    for (int32_t k = drp[d]; k < drp[d + 1]; ++k) {
+                        const uint32_t e = dent[k];
+                        const int2 x = X[rowb + (e >> 1)];
+                        if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                    }
+                    element(u, d, lo, hi);
+                }
+            } else {
+                // global copy (L2): a warp per row; the row is staged in shared
+                // memory for the down-hops, up-hops read whole neighbour rows
+                // with lanes over columns (coalesced, warp-uniform hop list)
+                int2* buf = xs + (int64_t)warp * Ddn;
+                for (int64_t u = r0 + warp; u < r1; u += nwarps) {
+                    const int2* xr = X + u * Ddn;
+                    if (rowbuf) {
+                        for (int64_t d = lane; d < Ddn; d += 32) buf[d] = __ldcg(xr + d);
+                        __syncwarp();
+                        xr = buf;
+                    }
+                    const int32_t kb = urp[u], ke = urp[u + 1];
+                    for (int64_t d = lane; d < Ddn; d += 32) {
+                        int lo = 0, hi = 0;
+#pragma unroll 4
+                        for (int32_t k = kb; k < ke; ++k) {
+                            const uint32_t e = uent[k];
+                            const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + d);
+                            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                        }
+                        for (int32_t k = drp[d]; k < drp[d + 1]; ++k) {
+                            const uint32_t e = dent[k];
+                            const int2 x = rowbuf ? xr[e >> 1] : __ldcg(xr + (e >> 1));
+                            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                        }
+                        element(u, d, lo, hi);
+                    }
+                    __syncwarp();
+                }
+            }
+            const double alpha = team_sum(ap);
+            if (!alive) return;
+            // r = q - alpha f, beta_next = |r|
+            double bp = 0.0;
+            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+                const double r = fma(-alpha, f[j], g[j]);
+                g[j] = r;
+                bp = fma(r, r, bp);
+            }
+            const double b2 = team_sum(bp);
+            if (!alive) return;
+            const double bn = sqrt(fmax(b2, 0.0));
+            if (threadIdx.x == 0) {
+                A[it] = alpha;
+                B[it] = bn;
+            }
+            m = it + 1;
+            amax = fmax(amax, fmax(fabs(alpha), bn));
+            if (bn <= 1e-13 * amax) broke = 1;
+            // Ritz test (thread 0; every CTA of the team reaches the same decision)
+            if (broke || (m >= 8 && (m % (m >= 32 ? 2 * kCheckEvery : kCheckEvery)) == 0) || m == mcap) {
+                __syncthreads();                             // A, B written by thread 0
+                const double th = cta_lowest_eig(A, B, m, sh_prev, sh_flags, sh_k);
+                if (threadIdx.x == 0) {
+                    const double sl = d_last_component(A, B, m, th);
+                    sh_prev = th;
+                    sh_theta = th;
+                    sh_rho = bn * sl;
+                    stop = broke || (sh_rho < P.tol * fmax(1.0, fabs(th)));
+                }
+                __syncthreads();
+                theta = sh_theta;
+                rho = sh_rho;
+                if (stop) {
+                    conv = 1;
+                    break;
+                }
+            }
+            // f_{j+1} = r / beta_next; the old f becomes f_{j-1}
+            const double ib = 1.0 / bn;
+            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) g[j] *= ib;
+            double* tmp = f;
+            f = g;
+            g = tmp;
+            beta = bn;
+            __syncthreads();
+        }
+        if (rank == 0 && threadIdx.x == 0) {
+            lanczos_result r;
+            r.energy = theta;
+            r.residual = rho;
+            r.iters = m;
+            r.breakdown = broke;
+            r.status = conv ? HUB_OK : HUB_ENOTCONV;
+            r.reserved = 0;
+            P.res[task.sector] = r;
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+}  // namespace hub
+
+// ---------------------------------------------------------------------------
+struct hubbard_batch {
+    int device = 0;
+    int n = 0;
+    std::vector<hub::SectorDesc> sec;          // host copy
+    std::vector<int64_t> voff;                 // n + 1 vector offsets
+    int64_t total = 0;                         // sum of D
+    std::vector<double> cost;                  // per-sector work estimate
+    hub::SectorDesc* d_sec = nullptr;
+    int32_t* d_rp = nullptr;
+    uint32_t* d_ent = nullptr;
+    uint32_t* d_st = nullptr;
+    // schedule
+    int64_t elems_per_cta = 1 << 14;
+    int* d_cta_ptr = nullptr;
+    hub::Task* d_tasks = nullptr;
+    size_t tasks_cap = 0;
+    int grid = 0;
+    int smem_elems = 0;
+    int sched_max_iters = -1;
+    int64_t sched_elems = -1;
+};
+
+namespace hub {
+namespace {
+
+struct Cached {
+    int64_t rp_off, ent_off, st_off, D, W;
+    double hops;   // mean hops per state
+};
+
+int batch_upload(hubbard_batch* B, const std::vector<int32_t>& rp, const std::vector<uint32_t>& ent,
+                 const std::vector<uint32_t>& st) {
+    auto up = [](auto** dst, const auto& v) -> int {
+        using T = std::remove_reference_t<decltype(v[0])>;
+        const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+        cudaError_t e = cudaMalloc((void**)dst, bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch tables)");
+        if (!v.empty()) {
+            e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch tables)");
+        }
+        return HUB_OK;
+    };
+    int rc;
+    if ((rc = up(&B->d_rp, rp)) || (rc = up(&B->d_ent, ent)) || (rc = up(&B->d_st, st))) return rc;
+    return up(&B->d_sec, B->sec);
+}
+
+void batch_free(hubbard_batch* B) {
+    cudaFree(B->d_sec);
+    cudaFree(B->d_rp);
+    cudaFree(B->d_ent);
+    cudaFree(B->d_st);
+    cudaFree(B->d_cta_ptr);
+    cudaFree(B->d_tasks);
+}
+
+int batch_grid(hubbard_batch* B, int* smem_elems) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    // two CTAs per SM, each with ~100 KB of fixed-point staging
+    const int smem = std::min(optin, 100 * 1024);
+    *smem_elems = smem / (int)sizeof(int2);
+    cudaError_t e = cudaFuncSetAttribute(k_batch_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return -1;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_lanczos, kBatchThreads, smem);
+    if (e != cudaSuccess || per_sm < 1) return -1;
+    B->grid = sms * std::min(per_sm, 2);
+    return smem;
+}
+
+// LPT static schedule: largest work first; a sector of D elements gets a team
+// of ceil(D / elems_per_cta) CTAs (<= kMaxTeam, <= grid); each task goes to
+// the team members that become free first.  Lists stay in assignment order,
+// which is one global order for all CTAs.
+int batch_schedule(hubbard_batch* B) {
+    const int G = B->grid;
+    std::vector<int> order(B->n);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
+    std::vector<double> avail((size_t)G, 0.0);
+    std::vector<std::vector<Task>> lists((size_t)G);
+    for (int s : order) {
+        int team = (int)std::min<int64_t>({(B->sec[s].D + B->elems_per_cta - 1) / B->elems_per_cta, (int64_t)kMaxTeam,
+                                           (int64_t)G});
+        team = std::max(team, 1);
+        B->sec[s].team = team;
+        std::vector<int> idx((size_t)G);
+        std::iota(idx.begin(), idx.end(), 0);
+        std::partial_sort(idx.begin(), idx.begin() + team, idx.end(),
+                          [&](int a, int b) { return avail[a] < avail[b] || (avail[a] == avail[b] && a < b); });
+        double start = 0.0;
+        for (int r = 0; r < team; ++r) start = std::max(start, avail[idx[r]]);
+        const double dur = B->cost[s] / team;
+        for (int r = 0; r < team; ++r) {
+            lists[idx[r]].push_back(Task{s, r});
+            avail[idx[r]] = start + dur;
+        }
+    }
+    std::vector<int> ptr((size_t)G + 1, 0);
+    std::vector<Task> flat;
+    for (int c = 0; c < G; ++c) {
+        ptr[(size_t)c + 1] = ptr[(size_t)c] + (int)lists[c].size();
+        flat.insert(flat.end(), lists[c].begin(), lists[c].end());
+    }
+    cudaFree(B->d_cta_ptr);
+    cudaFree(B->d_tasks);
+    B->d_cta_ptr = nullptr;
+    B->d_tasks = nullptr;
+    cudaError_t e = cudaMalloc((void**)&B->d_cta_ptr, ptr.size() * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(flat.size(), 1) * sizeof(Task));
+    if (e == cudaSuccess) e = cudaMemcpy(B->d_cta_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !flat.empty())
+        e = cudaMemcpy(B->d_tasks, flat.data(), flat.size() * sizeof(Task), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch schedule upload");
+    // the team sizes live in the sector descriptors
+    e = cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
+    B->sched_elems = B->elems_per_cta;
+    return HUB_OK;
+}
+
+inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
+
+struct WsLayout {
+    size_t f, g, xg, ab, tri, partial, bar, res, err, total;
+};
+
+WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
+    WsLayout L{};
+    size_t o = 0;
+    const size_t T = (size_t)B->total, n = (size_t)B->n;
+    L.f = o; o += al256(T * 8);
+    L.g = o; o += al256(T * 8);
+    L.xg = o; o += al256(T * 8);
+    L.ab = o; o += al256(n * 2 * (size_t)max_iters * 8);
+    L.tri = o; o += al256((size_t)B->grid * 4 * (size_t)max_iters * 8);
+    L.partial = o; o += al256(n * 2 * kMaxTeam * 8);
+    L.bar = o; o += al256(n * 4);
+    L.res = o; o += al256(n * sizeof(lanczos_result));
+    L.err = o; o += 256;
+    L.total = o;
+    return L;
+}
+
+}  // namespace
+}  // namespace hub
+
+using namespace hub;
+
+extern "C" {
+
+int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubbard_batch_t* out) {
+    clear_error();
+    if (out == nullptr || n_sectors < 1 || sectors == nullptr) return fail(HUB_EINVAL, "bad batch arguments");
+    *out = nullptr;
+    hubbard_batch* B = new (std::nothrow) hubbard_batch();
+    if (B == nullptr) return fail(HUB_ENOMEM, "host allocation");
+    cudaGetDevice(&B->device);
+    B->n = n_sectors;
+    std::vector<int32_t> rp;
+    std::vector<uint32_t> ent, st;
+    std::map<std::tuple<int, std::vector<std::pair<int, int>>, int>, Cached> cache;
+    auto spin = [&](int ns, const std::vector<std::pair<int, int>>& bl, int N) -> Cached {
+        auto key = std::make_tuple(ns, bl, N);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+        SpinTables T;
+        build_spin_tables(ns, N, bl, T);
+        Cached c{(int64_t)rp.size(), (int64_t)ent.size(), (int64_t)st.size(), T.D, T.W,
+                 T.D ? (double)T.tgt.size() / (double)T.D : 0.0};
+        rp.insert(rp.end(), T.rowptr.begin(), T.rowptr.end());
+        for (size_t k = 0; k < T.tgt.size(); ++k) ent.push_back(((uint32_t)T.tgt[k] << 1) | (T.sign[k] < 0 ? 1u : 0u));
+        st.insert(st.end(), T.states.begin(), T.states.end());
+        cache.emplace(key, c);
+        return c;
+    };
+    B->voff.assign((size_t)n_sectors + 1, 0);
+    try {
+        for (int i = 0; i < n_sectors; ++i) {
+            const hubbard_sector_desc& d = sectors[i];
+            if (d.ns < 1 || d.ns > 32 || d.nup < 0 || d.nup > d.ns || d.ndn < 0 || d.ndn > d.ns ||
+                d.n_bonds < 0 || (d.n_bonds > 0 && d.bonds == nullptr) || !std::isfinite(d.t) || !std::isfinite(d.U)) {
+                delete B;
+                return fail(HUB_EINVAL, "batch: invalid sector " + std::to_string(i));
+            }
+            std::vector<std::pair<int, int>> bl;
+            std::vector<std::pair<int, int>> seen;
+            for (int b = 0; b < d.n_bonds; ++b) {
+                const int x = d.bonds[2 * b], y = d.bonds[2 * b + 1];
+                const std::pair<int, int> key(std::min(x, y), std::max(x, y));
+                if (x < 0 || x >= d.ns || y < 0 || y >= d.ns || x == y ||
+                    std::find(seen.begin(), seen.end(), key) != seen.end()) {
+                    delete B;
+                    return fail(HUB_EINVAL, "batch: bad or duplicate bond in sector " + std::to_string(i));
+                }
+                seen.push_back(key);
+                bl.emplace_back(x, y);
+            }
+            const Cached cu = spin(d.ns, bl, d.nup), cd = spin(d.ns, bl, d.ndn);
+            if (cu.W + cd.W > 127) {
+                delete B;
+                return fail(HUB_EINVAL, "batch: more than 127 hops per state in sector " + std::to_string(i));
+            }
+            SectorDesc s{};
+            s.Dup = cu.D;
+            s.Ddn = cd.D;
+            s.D = cu.D * cd.D;
+            if (s.D > (int64_t)1 << 31) {
+                delete B;
+                return fail(HUB_EINVAL, "batch: sector dimension above 2^31");
+            }
+            s.voff = B->total;
+            s.up_rp = cu.rp_off;
+            s.dn_rp = cd.rp_off;
+            s.up_ent = cu.ent_off;
+            s.dn_ent = cd.ent_off;
+            s.up_st = cu.st_off;
+            s.dn_st = cd.st_off;
+            s.t = d.t;
+            s.U = d.U;
+            s.team = 1;
+            B->sec.push_back(s);
+            B->cost.push_back((double)s.D * (cu.hops + cd.hops + 8.0));
+            B->total += (s.D + 1) / 2 * 2;           // keep every sector 16-byte aligned
+            B->voff[(size_t)i + 1] = B->total;
+        }
+    } catch (const std::bad_alloc&) {
+        delete B;
+        return fail(HUB_ENOMEM, "host allocation (batch tables)");
+    }
+    int rc = batch_upload(B, rp, ent, st);
+    if (rc == HUB_OK && batch_grid(B, &B->smem_elems) < 0) rc = fail(HUB_ECUDA, "batch kernel occupancy");
+    if (rc != HUB_OK) {
+        std::string msg = hubbard_last_error();
+        batch_free(B);
+        delete B;
+        return fail(rc, msg);
+    }
+    *out = B;
+    return HUB_OK;
+}
+
+void hubbard_batch_destroy(hubbard_batch_t B) {
+    if (B == nullptr) return;
+    cudaDeviceSynchronize();
+    batch_free(B);
+    delete B;
+}
+
+int hubbard_batch_vector_offsets(hubbard_batch_t B, int64_t* offsets) {
+    clear_error();
+    if (B == nullptr || offsets == nullptr) return fail(HUB_EINVAL, "null argument");
+    std::memcpy(offsets, B->voff.data(), B->voff.size() * sizeof(int64_t));
+    return HUB_OK;
+}
+
+size_t hubbard_batch_workspace_bytes(hubbard_batch_t B, int max_iters) {
+    if (B == nullptr || max_iters < 1) return 0;
+    return batch_layout(B, max_iters).total;
+}
+
+int hubbard_batch_set_schedule(hubbard_batch_t B, int64_t elems_per_cta) {
+    clear_error();
+    if (B == nullptr || elems_per_cta < 1) return fail(HUB_EINVAL, "bad schedule");
+    B->elems_per_cta = elems_per_cta;
+    return HUB_OK;
+}
+
+int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
+                              size_t ws_bytes, void* stream) {
+    clear_error();
+    if (B == nullptr || v0_all == nullptr || max_iters < 1) return fail(HUB_EINVAL, "bad batch solve arguments");
+    if ((reinterpret_cast<uintptr_t>(v0_all) & 15u) || workspace == nullptr ||
+        (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return fail(HUB_EINVAL, "v0 must be 16-byte and workspace 256-byte aligned");
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != B->device) return fail(HUB_EINVAL, "batch created on another device");
+    const WsLayout L = batch_layout(B, max_iters);
+    if (ws_bytes < L.total) return fail(HUB_ENOMEM, "batch workspace too small");
+    int rc;
+    // descriptors: a/b history offsets depend on max_iters, team sizes on the schedule
+    // (both uploaded synchronously: fix them before capturing this call in a graph)
+    bool dirty = false;
+    if (B->sched_max_iters != max_iters) {
+        for (int i = 0; i < B->n; ++i) B->sec[(size_t)i].ab = (int64_t)i * 2 * max_iters;
+        B->sched_max_iters = max_iters;
+        dirty = true;
+    }
+    if (B->sched_elems != B->elems_per_cta) {
+        if ((rc = batch_schedule(B))) return rc;      // uploads the descriptors too
+        dirty = false;
+    }
+    if (dirty) HUB_CUDA(cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice));
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    // barrier counters and the error word start at zero
+    HUB_CUDA(cudaMemsetAsync(ws + L.bar, 0, (size_t)B->n * 4, s));
+    HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
+    BatchParams P;
+    P.sec = B->d_sec;
+    P.cta_ptr = B->d_cta_ptr;
+    P.tasks = B->d_tasks;
+    P.rp = B->d_rp;
+    P.ent = B->d_ent;
+    P.st = B->d_st;
+    P.v0 = v0_all;
+    P.f = (double*)(ws + L.f);
+    P.g = (double*)(ws + L.g);
+    P.xg = (int2*)(ws + L.xg);
+    P.ab = (double*)(ws + L.ab);
+    P.tri = (double*)(ws + L.tri);
+    P.partial = (double*)(ws + L.partial);
+    P.bar = (unsigned int*)(ws + L.bar);
+    P.res = (lanczos_result*)(ws + L.res);
+    P.err = (int*)(ws + L.err);
+    P.max_iters = max_iters;
+    P.tol = tol > 0.0 ? tol : 1e-10;
+    P.smem_elems = B->smem_elems;
+    P.spin_limit = 20000000;            // ~2.5 s of 128 ns sleeps per barrier
+    void* args[] = {&P};
+    const size_t smem = (size_t)B->smem_elems * sizeof(int2);
+    HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(B->grid), dim3(kBatchThreads), args, smem, s));
+    count_launches(1);
+    return HUB_OK;
+}
+
+int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
+                          lanczos_result* results) {
+    clear_error();
+    if (B == nullptr || workspace == nullptr || results == nullptr) return fail(HUB_EINVAL, "null argument");
+    const WsLayout L = batch_layout(B, max_iters);
+    cudaStream_t s = (cudaStream_t)stream;
+    int err = 0;
+    HUB_CUDA(cudaMemcpyAsync(results, (const char*)workspace + L.res, (size_t)B->n * sizeof(lanczos_result),
+                             cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaMemcpyAsync(&err, (const char*)workspace + L.err, 4, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    if (err != 0) return fail(err, "batch: a team barrier timed out");
+    return HUB_OK;
+}
+
+int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
+                           size_t ws_bytes, void* stream, int64_t* chosen) {
+    clear_error();
+    if (B == nullptr) return fail(HUB_EINVAL, "null batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    HUB_CUDA(cudaEventCreate(&e0));
+    HUB_CUDA(cudaEventCreate(&e1));
+    const int64_t cands[] = {1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17};
+    float best = 1e30f;
+    int64_t best_e = B->elems_per_cta;
+    int rc = HUB_OK;
+    for (int64_t c : cands) {
+        B->elems_per_cta = c;
+        for (int rep = 0; rep < 2 && rc == HUB_OK; ++rep) {   // first run warms up
+            if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(HUB_ECUDA, "event");
+            if (rc == HUB_OK) rc = hubbard_batch_solve_async(B, v0_all, max_iters, tol, workspace, ws_bytes, stream);
+            if (rc == HUB_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = fail(HUB_ECUDA, "event");
+            if (rc == HUB_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(HUB_ECUDA, "event sync");
+        }
+        if (rc != HUB_OK) break;
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_e = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->elems_per_cta = best_e;
+    if (chosen) *chosen = best_e;
+    return rc;
+}
+
+}  // extern "C"

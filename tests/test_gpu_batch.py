@@ -1,0 +1,146 @@
+"""GPU tests of the batched persistent solver (many sectors in one launch)."""
+import numpy as np
+import pytest
+
+import paper_1204_3425_gb300 as hub
+from oracle.basis import Sector
+from workload import batch_sectors, lattice_by_name, start_vector
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+MAXIT = 1000
+TOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1204_3425_gb300 import build
+    build.build()
+    hub.load_library()
+    return torch.device("cuda:0")
+
+
+def _specs(reqs):
+    out = []
+    for r in reqs:
+        ns, bonds = lattice_by_name(r["lattice"])
+        out.append((ns, bonds, r["nup"], r["ndn"], r["t"], r["U"]))
+    return out
+
+
+def _v0(B, specs, seeds):
+    v = np.zeros(int(B.offsets[-1]))
+    for i, s in enumerate(seeds):
+        D = int(np.prod([__import__("math").comb(specs[i][0], specs[i][2]),
+                         __import__("math").comb(specs[i][0], specs[i][3])]))
+        v[B.offsets[i]:B.offsets[i] + D] = start_vector(D, seed=s)
+    return torch.from_numpy(v).to("cuda")
+
+
+def _solve(specs, seeds, elems=None, autotune=False):
+    B = hub.Batch(specs)
+    if elems is not None:
+        B.set_schedule(elems)
+    v0 = _v0(B, specs, seeds)
+    ws = torch.empty(B.workspace_bytes(MAXIT), dtype=torch.uint8, device="cuda")
+    if autotune:
+        B.autotune(v0, MAXIT, TOL, ws)
+    B.solve_async(v0, MAXIT, TOL, ws)
+    return B, v0, ws, B.results(ws, MAXIT)
+
+
+def _oracle(spec):
+    ns, bonds, nup, ndn, t, U = spec
+    S = Sector(ns, bonds, nup, ndn, t, U)
+    if S.D <= 1500:
+        return float(np.linalg.eigvalsh(S.dense())[0])
+    from scipy.sparse.linalg import eigsh
+    return float(eigsh(S.explicit(), k=1, which="SA", tol=1e-14, v0=start_vector(S.D, seed=9))[0][0])
+
+
+def _small_reqs(n, seed, dmax):
+    import math
+    out = []
+    for r in batch_sectors(4 * n, seed=seed):
+        ns, _ = lattice_by_name(r["lattice"])
+        if math.comb(ns, r["nup"]) * math.comb(ns, r["ndn"]) <= dmax:
+            out.append(r)
+        if len(out) == n:
+            break
+    return out
+
+
+def test_batch_matches_oracle(dev):
+    reqs = _small_reqs(48, 77, 60000)
+    specs = _specs(reqs)
+    B, _, _, res = _solve(specs, [r["seed"] for r in reqs])
+    for spec, r in zip(specs, res):
+        assert r["status"] == hub.HUB_OK, (spec[2:], r)
+        e = _oracle(spec)
+        assert abs(r["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (spec[2:], r, e)
+
+
+def test_batch_alone_equals_in_mix_and_single_path(dev):
+    reqs = _small_reqs(32, 5, 200000)
+    specs = _specs(reqs)
+    seeds = [r["seed"] for r in reqs]
+    _, _, _, mix = _solve(specs, seeds)
+    for i in (0, 7, 19, 31):
+        _, _, _, alone = _solve([specs[i]], [seeds[i]])
+        assert alone[0]["energy"] == mix[i]["energy"] and alone[0]["iters"] == mix[i]["iters"]
+        ns, bonds, nup, ndn, t, U = specs[i]
+        H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+        r1 = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(H.D, seed=seeds[i])).to(dev), MAXIT, 0.0 + TOL)
+        assert abs(r1["energy"] - mix[i]["energy"]) <= 1e-9 * max(1.0, abs(r1["energy"]))
+
+
+def test_batch_team_path(dev):
+    """Small elements-per-CTA forces multi-CTA teams (global fixed-point copy, team barriers)."""
+    reqs = _small_reqs(24, 11, 200000)
+    specs = _specs(reqs)
+    seeds = [r["seed"] for r in reqs]
+    _, _, _, solo = _solve(specs, seeds)
+    _, _, _, team = _solve(specs, seeds, elems=512)
+    for a, b in zip(solo, team):
+        assert b["status"] == hub.HUB_OK
+        assert abs(a["energy"] - b["energy"]) <= 1e-9 * max(1.0, abs(a["energy"]))
+
+
+def test_batch_autotune_and_graph_replay(dev):
+    reqs = _small_reqs(40, 13, 200000)
+    specs = _specs(reqs)
+    B, v0, ws, res = _solve(specs, [r["seed"] for r in reqs], autotune=True)
+    stream = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        B.solve_async(v0, MAXIT, TOL, ws, stream=stream)          # warm (descriptors fixed)
+        stream.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            B.solve_async(v0, MAXIT, TOL, ws, stream=stream)
+    graph.replay()
+    torch.cuda.synchronize()
+    again = B.results(ws, MAXIT)
+    assert [r["energy"] for r in again] == [r["energy"] for r in res]
+
+
+def test_batch_full_config(dev):
+    """2048 uneven sectors (rings 6-12, 2x3, 2x4, 3x3, 3x4; random fillings and U)."""
+    reqs = batch_sectors(2048, seed=1234)
+    specs = _specs(reqs)
+    B, v0, ws, res = _solve(specs, [r["seed"] for r in reqs])
+    assert all(r["status"] == hub.HUB_OK for r in res)
+    rng = np.random.default_rng(0)
+    import math
+    small = [i for i, s in enumerate(specs) if math.comb(s[0], s[2]) * math.comb(s[0], s[3]) <= 20000]
+    for i in rng.choice(small, 40, replace=False):
+        e = _oracle(specs[i])
+        assert abs(res[i]["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (i, specs[i][2:], res[i], e)
+    # the largest sectors against the single-sector GPU path
+    big = sorted(range(len(specs)), key=lambda i: -math.comb(specs[i][0], specs[i][2]) * math.comb(specs[i][0], specs[i][3]))[:3]
+    for i in big:
+        ns, bonds, nup, ndn, t, U = specs[i]
+        H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+        r1 = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(H.D, seed=reqs[i]["seed"])).to(dev), MAXIT, TOL)
+        assert abs(r1["energy"] - res[i]["energy"]) <= 1e-9 * max(1.0, abs(r1["energy"]))
