@@ -173,7 +173,13 @@ int hubbard_apply_noalloc(hubbard_t H, const void* v, void* w, void* stream);
 int hubbard_vec_dot(const void* x, const void* y, int64_t n, int dtype, void* stream, double* out);
 int hubbard_vec_nrm2(const void* x, int64_t n, int dtype, void* stream, double* out);
 /* y <- y + a*x  (asynchronous) */
+
+/* Seeded start vector on the device (the paper asks for a random start
+ * vector, Algorithm 1): v[i] = 2 x - 1 with x the top 53 bits of SplitMix64
+ * (Steele, Lea, Flood 2014) at counter seed * 2^40 + start + i, divided by
+ * 2^53; binary32 rounds the binary64 value.  Asynchronous. */
 int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, void* stream);
+int hubbard_fill_start_vector(void* v, int64_t n, uint64_t seed, int64_t start, int dtype, void* stream);
 
 /* ---------------------------------------------------------------------------
  * One step of Algorithm 1 in the two-vector form of Eqs. (split1):

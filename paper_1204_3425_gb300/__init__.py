@@ -47,6 +47,7 @@ SIGNATURES = {
     "hubbard_vec_dot": (ctypes.c_int, [P, P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_nrm2": (ctypes.c_int, [P, I64, ctypes.c_int, P, P]),
     "hubbard_vec_axpy": (ctypes.c_int, [D, P, P, I64, ctypes.c_int, P]),
+    "hubbard_fill_start_vector": (ctypes.c_int, [P, I64, ctypes.c_uint64, I64, ctypes.c_int, P]),
     "hubbard_lanczos_step": (ctypes.c_int, [P, P, P, D, ctypes.c_int, P, P, P]),
     "lanczos_workspace_bytes": (SZ, [P, ctypes.c_int]),
     "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P]),
@@ -225,6 +226,13 @@ def hubbard_vec_nrm2(x, stream=None):
 def hubbard_vec_axpy(a, x, y, stream=None):
     _check(load_library().hubbard_vec_axpy(float(a), _ptr(x), _ptr(y), x.numel(), _dtype_code(x), _stream(stream)))
     return y
+
+
+def hubbard_fill_start_vector(v, seed, start=0, stream=None):
+    """Fill a device tensor with the seeded SplitMix64 start vector (entries start .. start+n-1)."""
+    _check(load_library().hubbard_fill_start_vector(_ptr(v), v.numel(), int(seed), int(start), _dtype_code(v),
+                                                    _stream(stream)))
+    return v
 
 
 def hubbard_lanczos_step(H, f, g, beta_j, stream=None):

@@ -500,6 +500,14 @@ static double* reduction_scratch() {
     return p;
 }
 
+int hubbard_fill_start_vector(void* v, int64_t n, uint64_t seed, int64_t start, int dtype, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_vec(v, n, dtype))) return rc;
+    if (start < 0) return fail(HUB_EINVAL, "negative start");
+    return launch_fill_splitmix(v, n, (unsigned long long)seed, start, dtype, (cudaStream_t)stream);
+}
+
 int hubbard_vec_dot(const void* x, const void* y, int64_t n, int dtype, void* stream, double* out) {
     clear_error();
     int rc;

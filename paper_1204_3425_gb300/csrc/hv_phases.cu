@@ -560,25 +560,24 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
 }
 
 // ---------------------------------------------------------------------------
+// thread-safe (static initialisation runs once; callers on other threads wait)
 int smem_optin() {
-    static int v = 0;
-    if (v == 0) {
-        int dev = 0;
+    static const int v = [] {
+        int dev = 0, x = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (v <= 0) v = 48 * 1024;
-    }
+        cudaDeviceGetAttribute(&x, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        return x > 0 ? x : 48 * 1024;
+    }();
     return v;
 }
 
 int sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, x = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&x, cudaDevAttrMultiProcessorCount, dev);
+        return x > 0 ? x : 1;
+    }();
     return n;
 }
 
@@ -606,9 +605,16 @@ Launch shape(size_t smem, int ctas) {
     return L;
 }
 
+// The dynamic shared-memory limit is a per-kernel attribute shared by every
+// host thread: raise it once, to the device maximum, so that a concurrent
+// launch of the same kernel can never see a lower limit.
 template <typename K>
-void allow_smem(K kern, size_t bytes) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+void allow_smem(K kern, size_t /*bytes*/) {
+    static const bool once = [kern] {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
+        return true;
+    }();
+    (void)once;
 }
 
 // m such that max(|t|, |U| Ns, |beta|) * 2^m <= 2^61

@@ -116,6 +116,7 @@ int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, dou
 int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s);
 int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double inv_norm, cudaStream_t s);
 int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cudaStream_t s);
+int launch_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype, cudaStream_t s);
 int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s);
 
 // tridiag.cpp -----------------------------------------------------------------

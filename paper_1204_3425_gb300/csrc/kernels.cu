@@ -25,14 +25,14 @@ inline int grid_for(int64_t work, int per_block, int cap) {
     return (int)g;
 }
 
+// thread-safe (static initialisation runs once; callers on other threads wait)
 int sm_count() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, v = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 1;
+    }();
     return n;
 }
 
@@ -255,6 +255,22 @@ __global__ void k_psi_acc(const float* __restrict__ f, double* __restrict__ psi,
         psi[i] = init ? s * (double)f[i] : fma(s, (double)f[i], psi[i]);
 }
 
+// Seeded uniform [-1, 1) start vector: SplitMix64 (Steele, Lea, Flood 2014)
+// in counter mode, counter = seed * 2^40 + (start + i); the top 53 bits of
+// the output give x in [0, 1), v = 2x - 1 (exact in binary64).
+__global__ void k_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        unsigned long long z = seed * (1ull << 40) + (unsigned long long)(start + i) + 0x9E3779B97F4A7C15ull;
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        z ^= z >> 31;
+        const double x = (double)(z >> 11) * 0x1p-53;
+        const double val = 2.0 * x - 1.0;
+        if (dtype == HUB_F64) ((double*)v)[i] = val;
+        else ((float*)v)[i] = (float)val;
+    }
+}
+
 // sums partials[0..nb) in index order into partials[kRedSlots-1]
 __global__ void k_finish_sum(double* partials, int nb) {
     double s = 0.0;
@@ -366,6 +382,14 @@ int launch_scale(double a, void* y, int64_t n, int dtype, cudaStream_t s) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
     if (dtype == HUB_F64) k_scale<double><<<g, kThreads, 0, s>>>(a, (double*)y, n);
     else k_scale<float><<<g, kThreads, 0, s>>>((float)a, (float*)y, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_fill_splitmix<<<g, kThreads, 0, s>>>(v, n, seed, start, dtype);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;
