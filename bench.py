@@ -244,6 +244,14 @@ def run_ours(args):
                  iters=iters, max_rel_err=max(errs) if errs else None, all_within_1e9=all(ok),
                  tol="rho < 1e-10", includes="hubbard_sector_create + lanczos_ground_state + destroy")
 
+    extra = {}
+    if args.workload == "sq4x4_n8_8_U8_f64" and args.solves > 0:
+        extra["solve_refined"] = bench_refined(hub, torch, dev, bonds, golden, args.solves)
+    if args.batch and rank == 0:
+        extra["batch"] = bench_batch(hub, torch, dev)
+    if args.serve and rank == 0:
+        extra["serve"] = bench_serve(args.serve)
+
     peak, src = peaks()
     avg_kernel_ms = float(np.mean(per))
     achieved = nbytes / (avg_kernel_ms * 1e-3) / 1e9
@@ -264,6 +272,7 @@ def run_ours(args):
         "clocks": clk,
         "solve": solve,
     }
+    line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sq4x4_n8_8_U8_f64":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     H.close()
@@ -271,6 +280,77 @@ def run_ours(args):
         print(json.dumps(line))
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def bench_refined(hub, torch, dev, bonds, golden, n):
+    """4x4 (8,8) U=8 solved with binary32 Lanczos + binary64 refinement (same seed)."""
+    from workload import start_vector
+    v0 = torch.from_numpy(start_vector(12870 * 12870, seed=1234)).to(dev)
+    lat, errs, iters = [], [], []
+    for k in range(n + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H = hub.hubbard_sector_create(16, bonds, 8, 8, 1.0, 8.0)
+        r = hub.lanczos_ground_state_refined(H, v0, 1000, 1e-10)
+        H.close()
+        torch.cuda.synchronize()
+        if k == 0:
+            continue
+        lat.append(time.perf_counter() - t0)
+        errs.append(abs(r["energy"] - golden) / abs(golden))
+        iters.append((r["iters_f32"], r["iters_f64"]))
+    ok = [e <= 1e-9 for e in errs]
+    return dict(solves=n, solves_per_s=sum(ok) / sum(lat), p50_ms=1e3 * float(np.percentile(lat, 50)),
+                p99_ms=1e3 * float(np.percentile(lat, 99)), iters_f32_f64=iters, max_rel_err=max(errs),
+                all_within_1e9=all(ok), path="binary32 Lanczos + replayed Ritz vector + binary64 Rayleigh/polish")
+
+
+def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10):
+    """2048 uneven sectors in one persistent launch; schedule picked by the autotuner."""
+    from workload import batch_sectors, lattice_by_name
+    reqs = batch_sectors(count, seed=1234)
+    specs = []
+    for r in reqs:
+        ns, bonds = lattice_by_name(r["lattice"])
+        specs.append((ns, bonds, r["nup"], r["ndn"], r["t"], r["U"]))
+    t0 = time.perf_counter()
+    B = hub.Batch(specs)
+    create_s = time.perf_counter() - t0
+    v0 = torch.zeros(int(B.offsets[-1]), dtype=torch.float64, device=dev)
+    for k, (r, sp) in enumerate(zip(reqs, specs)):
+        D = math.comb(sp[0], sp[2]) * math.comb(sp[0], sp[3])
+        hub.hubbard_fill_start_vector(v0[int(B.offsets[k]):int(B.offsets[k]) + D], r["seed"])
+    ws = torch.empty(B.workspace_bytes(max_iters), dtype=torch.uint8, device=dev)
+    t0 = time.perf_counter()
+    chosen = B.autotune(v0, 40, tol, ws)            # short solves (40 steps) rank the schedules
+    tune_s = time.perf_counter() - t0
+    B.solve_async(v0, max_iters, tol, ws)
+    torch.cuda.synchronize()
+    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    ev[0].record()
+    B.solve_async(v0, max_iters, tol, ws)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1])
+    res = B.results(ws, max_iters)
+    B.close()
+    ok = sum(1 for r in res if r["status"] == 0)
+    return dict(sectors=count, ms=ms, solves_per_s=ok / (ms * 1e-3), converged=ok, elems_per_cta=chosen,
+                autotune_s=tune_s, create_s=create_s, iters_total=sum(r["iters"] for r in res),
+                launches_per_batch=1, tol="rho < 1e-10 max(1,|theta|)")
+
+
+def bench_serve(n):
+    """Poisson trace (mean 500 req/s) of rings 8-16 and 3x3, 3x4, 4x4 sectors."""
+    from paper_1204_3425_gb300.serve import Request, SolveServer
+    from workload import serve_requests
+    reqs = [Request(k, s, s["arrival_s"]) for k, s in enumerate(serve_requests(n, rate=500.0, seed=1234))]
+    srv = SolveServer(200e9, n_slots=6, small_max_dim=200_000)
+    st = srv.run_trace(reqs, timeout=3600)
+    srv.stop()
+    st["converged"] = sum(1 for r in reqs if r.result and r.result["status"] == 0)
+    st["rate_req_per_s"] = 500.0
+    return st
 
 
 def cpu_baseline(budget_s=15.0):
@@ -339,6 +419,8 @@ def main():
     ap.add_argument("--solves", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=1, help="also time the 2048-sector batched solve (0: skip)")
+    ap.add_argument("--serve", type=int, default=400, help="requests in the serving trace (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
