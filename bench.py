@@ -129,6 +129,22 @@ class ClockSampler:
                     reasons=sorted(reasons), samples=len(sm))
 
 
+def max_over_ranks(value, device="cpu"):
+    """MAX of a per-rank float over the default process group (identity on one rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(bytes_per_step, steps, total_ms, world):
+    """Whole-job GB/s: every rank runs its own replica of the same work."""
+    return world * bytes_per_step * steps / (total_ms * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -195,12 +211,9 @@ def run_ours(args):
         torch.distributed.barrier()
     clk = clocks.stop()
     per = [a.elapsed_time(b) for a, b in ev]
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, dev)
     ms = total_ms / args.steps
-    value = ws * nbytes * args.steps / (total_ms * 1e-3) / 1e9
+    value = job_throughput(nbytes, args.steps, total_ms, ws)
 
     # ---- end to end through the C ABI with host buffers -------------------
     w_pin = torch.empty(D, dtype=tdt).pin_memory()

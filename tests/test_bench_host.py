@@ -1,0 +1,57 @@
+"""Host logic of bench.py's multi-process path (replicas, max over ranks),
+checked with world_size-2 gloo process groups on CPU."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, values, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    got = bench.max_over_ranks(values[rank])
+    out[rank] = got
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo():
+    ctx = mp.get_context("spawn")
+    out = ctx.Manager().dict()
+    values = [12.5, 40.25]
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, values, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    assert out[0] == out[1] == 40.25
+
+
+def test_single_rank_identity_and_throughput():
+    assert bench.max_over_ranks(3.5) == 3.5
+    # two replicas of 2.652 GB each, 10 steps in 100 ms (slowest rank) -> 530.4 GB/s
+    assert bench.job_throughput(2.652e9, 10, 100.0, 2) == pytest.approx(530.4)
+
+
+def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+
+    class A:
+        steps, warmup = 1, 0
+    bench.run_reference(A())
+    assert capsys.readouterr().out == ""
