@@ -127,14 +127,16 @@ int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream);
  * Kept as the parity anchor for the fast path. */
 int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 
-/* Launch schedule of the two-phase shared-memory H*v for this handle (the
- * hook an autotuner drives; Sec. 4.3 reports the paper's own tuning knob,
- * several elements per thread).  vec_rows: rows of V staged per row-phase
- * block; vec_cols: columns per column-phase strip (each 0 = automatic, else
- * 1, 2 or 4; binary64 uses at most 2); ctas_rows / ctas_cols: CTAs per SM
- * for each phase (0 = automatic, 1 or 2).  A choice whose buffers do not fit
- * in shared memory falls back to the largest one that does.  Results do not
- * depend on the schedule (integer hop sums are order-independent). */
+/* Launch schedule of the two-phase H*v for this handle (the hook an
+ * autotuner drives; Sec. 4.3 reports the paper's own tuning knob, several
+ * elements per thread).  vec_rows: rows of V staged per row-phase block;
+ * vec_cols: columns per lane in the up phase (each 0 = automatic, else 1, 2
+ * or 4; binary64 uses at most 2, and a width the row length does not divide
+ * is narrowed); ctas_rows: row-phase CTAs per SM (0 = automatic, 1 or 2);
+ * ctas_cols: accepted (0, 1 or 2) and reserved.  A choice whose buffers do
+ * not fit in shared memory falls back to the largest one that does.
+ * Results do not depend on the schedule: every output sums its hops in one
+ * fixed order (binary32) or exactly (binary64 fixed point). */
 int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols);
 
 /* ---------------------------------------------------------------------------

@@ -50,6 +50,8 @@ def _compile(src, force, extra):
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         return obj, f"{' '.join(cmd)}\n{r.stdout}\n{r.stderr}"
+    if extra and r.stderr:
+        sys.stderr.write(f"== {src}\n{r.stderr}")
     return obj, None
 
 

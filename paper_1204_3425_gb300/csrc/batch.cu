@@ -151,89 +151,6 @@ __device__ __noinline__ int d_sturm(const double* a, const double* b, int m, dou
     return c;
 }
 
-// lowest eigenvalue of T_m and |last component| of its unit eigenvector.
-// prev: the lowest Ritz value of an earlier T_{m'} (m' < m) or NaN; the lowest
-// Ritz value never increases with m (interlacing), so prev bounds it above.
-__device__ __noinline__ void d_tridiag(const double* a, const double* b, int m, double* w, double prev,
-                                       double* theta, double* slast) {
-    double glo = a[0], ghi = a[0];
-    for (int i = 0; i < m; ++i) {
-        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < m ? fabs(b[i]) : 0.0);
-        glo = fmin(glo, a[i] - r);
-        ghi = fmax(ghi, a[i] + r);
-    }
-    double lo = glo, hi = ghi;
-    if (prev == prev) {                                  // warm start from the previous value
-        const double h = prev + 1e-12 * fmax(1.0, fabs(prev));
-        if (h < ghi && d_sturm(a, b, m, h) >= 1) {
-            hi = h;
-            double step = 1e-6 * fmax(1.0, fabs(prev));
-            while (true) {
-                const double l = prev - step;
-                if (l <= glo) break;
-                if (d_sturm(a, b, m, l) == 0) {
-                    lo = l;
-                    break;
-                }
-                hi = l;
-                step *= 16.0;
-            }
-        }
-    }
-    for (int it = 0; it < 200; ++it) {
-        const double mid = 0.5 * (lo + hi);
-        if (mid <= lo || mid >= hi) break;
-        if (d_sturm(a, b, m, mid) >= 1) hi = mid; else lo = mid;
-        if (hi - lo <= 4e-16 * fmax(fabs(lo), fabs(hi))) break;
-    }
-    const double th = 0.5 * (lo + hi);
-    *theta = th;
-    if (m == 1) {
-        *slast = 1.0;
-        return;
-    }
-    // inverse iteration, banded LU with partial pivoting on T - x I
-    double* d = w;
-    double* u1 = w + m;
-    double* u2 = w + 2 * m;
-    double* y = w + 3 * m;
-    const double x = th - 1e-14 * fmax(1.0, fabs(th));
-    for (int i = 0; i < m; ++i) y[i] = 1.0;
-    for (int rep = 0; rep < 3; ++rep) {
-        for (int i = 0; i < m; ++i) {
-            d[i] = a[i] - x;
-            u1[i] = i + 1 < m ? b[i] : 0.0;
-            u2[i] = 0.0;
-        }
-        for (int i = 0; i + 1 < m; ++i) {
-            double sub = b[i];
-            if (fabs(sub) > fabs(d[i])) {
-                double t0 = d[i]; d[i] = sub; sub = t0;
-                double t1 = u1[i]; u1[i] = d[i + 1]; d[i + 1] = t1;
-                double t2 = u2[i]; u2[i] = u1[i + 1]; u1[i + 1] = t2;
-                double t3 = y[i]; y[i] = y[i + 1]; y[i + 1] = t3;
-            }
-            if (d[i] == 0.0) d[i] = 1e-300;
-            const double f = sub / d[i];
-            d[i + 1] -= f * u1[i];
-            u1[i + 1] -= f * u2[i];
-            y[i + 1] -= f * y[i];
-        }
-        if (d[m - 1] == 0.0) d[m - 1] = 1e-300;
-        for (int i = m - 1; i >= 0; --i) {
-            double s = y[i];
-            if (i + 1 < m) s -= u1[i] * y[i + 1];
-            if (i + 2 < m) s -= u2[i] * y[i + 2];
-            y[i] = s / d[i];
-        }
-        double n2 = 0.0;
-        for (int i = 0; i < m; ++i) n2 += y[i] * y[i];
-        const double inv = 1.0 / sqrt(n2);
-        for (int i = 0; i < m; ++i) y[i] *= inv;
-    }
-    *slast = fabs(y[m - 1]);
-}
-
 // Lowest eigenvalue of T_m by multisection over the whole CTA: every thread
 // evaluates the Sturm count at its own point of the bracket, which shrinks by
 // blockDim + 1 per round.  prev (or NaN) is an upper bound from an earlier

@@ -212,13 +212,22 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     // SELL-32/8 for the row phase: per group, slots assigned by bank-conflict-free
     // colouring for the element size the row phase will stage (16 bytes when a
     // 16-byte-per-state row fits in shared memory, else 8, else 4), in blocks of
-    // 8 slots per lane, contiguous per lane; empty slots are padding (code 0).
+    // 8 slots per lane, contiguous per lane.  Entry = staged slot index, top bit
+    // set for sign -1.  The staged row is followed by 32 zero slots starting at
+    // Dr = D rounded up to 32; a slot a lane does not use points at the zero slot
+    // of a bank group no other lane of its wavefront phase uses (so padding adds
+    // zero without a branch and without a conflict).
     const int64_t smem_budget = 220 * 1024;
-    const int eb = (T.D * 16 <= smem_budget) ? 16 : ((T.D * 8 <= smem_budget) ? 8 : 4);
+    const int eb = ((T.D + 64) * 16 <= smem_budget) ? 16 : (((T.D + 64) * 8 <= smem_budget) ? 8 : 4);
+    const int ngroups = 128 / eb;
+    const int planes = std::min(32, ngroups);
+    const int64_t Dr = (T.D + 31) / 32 * 32;
+    const bool narrow = Dr + 32 <= 32767;            // 15-bit index + sign
+    const uint32_t negbit = narrow ? 0x8000u : 0x80000000u;
     std::vector<int64_t> boff((size_t)groups);
     std::vector<int32_t> bcnt((size_t)groups);
-    std::vector<SlotColouring> colours((size_t)groups);
     int64_t btotal = 0;
+    std::vector<SlotColouring> colours((size_t)groups);
     for (int64_t g = 0; g < groups; ++g) {
         std::vector<std::vector<int32_t>> lt;
         for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r)
@@ -228,14 +237,34 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
         bcnt[(size_t)g] = (colours[(size_t)g].slots + 7) / 8;
         btotal += (int64_t)bcnt[(size_t)g] * 32 * 8;
     }
-    std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), 0u);
-    for (int64_t r = 0; r < T.D; ++r) {
-        const int64_t g = r / 32, lane = r % 32;
-        const std::vector<int>& so = colours[(size_t)g].slot_of[(size_t)lane];
-        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c) {
-            const int slot = so[(size_t)c];
-            bent[(size_t)(boff[(size_t)g] + ((int64_t)(slot / 8) * 32 + lane) * 8 + slot % 8)] =
-                ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
+    std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), (uint32_t)Dr);
+    for (int64_t g = 0; g < groups; ++g) {
+        const SlotColouring& C = colours[(size_t)g];
+        const int nslot = bcnt[(size_t)g] * 8;
+        // entry[lane][slot], -1 = padding
+        std::vector<std::vector<int64_t>> grid(32, std::vector<int64_t>((size_t)nslot, -1));
+        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) {
+            const int lane = (int)(r % 32);
+            for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
+                grid[(size_t)lane][(size_t)C.slot_of[(size_t)lane][(size_t)c]] = k;
+        }
+        for (int s = 0; s < nslot; ++s) {
+            for (int p0 = 0; p0 < 32; p0 += planes) {
+                std::vector<char> used((size_t)ngroups, 0);
+                for (int l = p0; l < p0 + planes; ++l) {
+                    const int64_t k = grid[(size_t)l][(size_t)s];
+                    if (k >= 0) used[(size_t)(T.tgt[(size_t)k] % ngroups)] = 1;
+                }
+                int freeg = 0;
+                while (freeg < ngroups && used[(size_t)freeg]) ++freeg;
+                if (freeg == ngroups) freeg = 0;          // cannot happen: a padded lane leaves a group free
+                for (int l = p0; l < p0 + planes; ++l) {
+                    const int64_t k = grid[(size_t)l][(size_t)s];
+                    const uint32_t e = k >= 0 ? ((uint32_t)T.tgt[(size_t)k] | (T.sign[(size_t)k] < 0 ? negbit : 0u))
+                                              : (uint32_t)(Dr + freeg);
+                    bent[(size_t)(boff[(size_t)g] + ((int64_t)(s / 8) * 32 + l) * 8 + s % 8)] = e;
+                }
+            }
         }
     }
     // sign-split list: +1 targets first, then -1 targets, each ascending
@@ -255,7 +284,7 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     if ((rc = upload(&d.pn_list, pnl.data(), pnl.size()))) return rc;
     if ((rc = upload(&d.blk_off, boff.data(), boff.size()))) return rc;
     if ((rc = upload(&d.blk_cnt, bcnt.data(), bcnt.size()))) return rc;
-    if (T.D < (1 << 14)) {
+    if (narrow) {
         std::vector<uint16_t> e16(bent.size());
         for (size_t i = 0; i < bent.size(); ++i) e16[i] = (uint16_t)bent[i];
         if ((rc = upload(&d.ent16, e16.data(), e16.size()))) return rc;

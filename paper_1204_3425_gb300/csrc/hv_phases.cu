@@ -2,13 +2,14 @@
 //
 // V is the row-major D_up x D_dn matrix of Fig. 2.  The Kronecker sum of
 // Eq. (H-Kroneckersum) splits H*v into
-//   row phase    Y[u, :] = sum over down-hops inside row u        (Algorithm 3)
-//   column phase W[:, c] = sum over up-hops inside column c + Y[:, c]
-//                          + U * popcount(s_up & s_dn) * V[:, c]   (Algorithms 2, 4)
-// Each phase stages whole rows (row phase) or whole column strips (column
-// phase) of V in shared memory, so every gathered operand comes from shared
-// memory.  Rows per block / columns per strip (VEC) share one read of the
-// warp-sliced hop table: one 16-byte shared load feeds VEC outputs.
+//   row phase  Y[u, :] = sum over down-hops inside row u          (Algorithm 3)
+//   up phase   W[u, :] = sum over up-hops u -> u' of rows V[u', :] + Y[u, :]
+//                        + U * popcount(s_up & s_dn) * V[u, :]     (Algorithms 2, 4)
+// The row phase stages VEC whole rows of V in shared memory and gathers with a
+// warp-sliced, bank-coloured hop table (one 16-byte shared load feeds VEC
+// outputs).  The up phase combines whole row segments: a warp-uniform hop
+// list, lanes over columns, coalesced loads of a column chunk that stays
+// resident in L2 while every row of it is formed.
 //
 // Binary64 path: every element is rounded once to the fixed-point grid 2^-k
 // (k = 1070 - emax, emax = biased exponent bound of max|v|) and held as
@@ -110,7 +111,18 @@ __device__ __forceinline__ double i64_scaled_to_double(long long P, int e2) {
     return __longlong_as_double(bits + ((long long)e2 << 52));
 }
 
-__device__ __forceinline__ int hop_sign(uint32_t e) { return (int)(e & 1u) - (int)(e & 2u); }
+// row-phase entry: slot index in the low bits, top bit (15 or 31) = sign -1
+template <typename EntT> struct RowEnt;
+template <> struct RowEnt<uint16_t> {
+    static __device__ __forceinline__ uint32_t idx(uint32_t e) { return e & 0x7FFFu; }
+    static __device__ __forceinline__ int sgn(uint32_t e) { return ((int)(e << 16) >> 31) | 1; }
+};
+template <> struct RowEnt<uint32_t> {
+    static __device__ __forceinline__ uint32_t idx(uint32_t e) { return e & 0x7FFFFFFFu; }
+    static __device__ __forceinline__ int sgn(uint32_t e) { return ((int)e >> 31) | 1; }
+};
+// staged slots: D rounded up to 32, then 32 zero slots for padding entries
+__host__ __device__ __forceinline__ int64_t staged_slots(int64_t D) { return (D + 31) / 32 * 32 + 32; }
 
 template <int VEC> struct FxVec;
 template <> struct FxVec<1> { using T = int2; };
@@ -164,7 +176,8 @@ __device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int 
     }
 }
 
-// Row phase, binary64 fixed point: Y[u, d] = sum_{(d', s) in hops_dn(d)} s X[u, d']
+// Row phase, binary64 fixed point: Y[u, d] = sum_{(d', s) in hops_dn(d)} s X[u, d'];
+// also writes the fixed-point copy of V to Xg for the up phase
 template <int VEC, typename EntT>
 __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v, long long* __restrict__ Y,
                                                      int2* __restrict__ Xg, int64_t Dup, int64_t Ddn,
@@ -179,6 +192,13 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
     const int lane = threadIdx.x & 31;
     const int64_t nblk = (Dup + VEC - 1) / VEC;
     const int64_t step = blockDim.x;
+    {
+        const int64_t z0 = staged_slots(Ddn) - 32;
+        for (int i = threadIdx.x; i < 32; i += blockDim.x) {
+            if constexpr (VEC == 1) X[z0 + i] = make_int2(0, 0);
+            else X[z0 + i] = make_int4(0, 0, 0, 0);
+        }
+    }
     for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int64_t u0 = b * VEC;
         const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
@@ -212,15 +232,13 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
             const int64_t d = d0 + lane;
             int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
             for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
-                if (e & 3u) {                                 // padding slots read nothing
-                    const int s = hop_sign(e);
-                    const S x = X[e >> 2];
-                    a0 += s * x.x;
-                    a1 += s * x.y;
-                    if constexpr (VEC == 2) {
-                        a2 += s * x.z;
-                        a3 += s * x.w;
-                    }
+                const int s = RowEnt<EntT>::sgn(e);           // padding reads a zero slot
+                const S x = X[RowEnt<EntT>::idx(e)];
+                a0 += s * x.x;
+                a1 += s * x.y;
+                if constexpr (VEC == 2) {
+                    a2 += s * x.z;
+                    a3 += s * x.w;
                 }
             });
             if (d < Ddn) {
@@ -249,9 +267,10 @@ __global__ void __launch_bounds__(512) k_rows_global_f64x(const int2* __restrict
             const int64_t d = d0 + lane;
             int a0 = 0, a1 = 0;
             for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
-                if (e & 3u) {
-                    const int s = hop_sign(e);
-                    const int2 x = __ldg(X + (e >> 2));
+                const uint32_t i = RowEnt<EntT>::idx(e);
+                if (i < Ddn) {                                // padding: no zero slots in global rows
+                    const int s = RowEnt<EntT>::sgn(e);
+                    const int2 x = __ldg(X + i);
                     a0 += s * x.x;
                     a1 += s * x.y;
                 }
@@ -514,6 +533,10 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
     const int lane = threadIdx.x & 31;
     const int64_t nblk = (Dup + VEC - 1) / VEC;
     const int64_t step = blockDim.x;
+    {
+        const int64_t z0 = staged_slots(Ddn) - 32;
+        for (int i = threadIdx.x; i < 32 * VEC; i += blockDim.x) Xf[z0 * VEC + i] = 0.0f;
+    }
     for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int64_t u0 = b * VEC;
         const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
@@ -542,12 +565,10 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
 #pragma unroll
             for (int r = 0; r < VEC; ++r) acc[r] = 0.0f;
             for_each_hop<EntT>(ent + boff[g], bcnt[g], lane, [&](uint32_t e) {
-                if (e & 3u) {                                 // padding slots read nothing
-                    const float s = (float)hop_sign(e);
-                    const S x = X[e >> 2];
+                const float s = (float)RowEnt<EntT>::sgn(e);  // padding reads a zero slot
+                const S x = X[RowEnt<EntT>::idx(e)];
 #pragma unroll
-                    for (int r = 0; r < VEC; ++r) acc[r] = fmaf(s, comp(x, r), acc[r]);
-                }
+                for (int r = 0; r < VEC; ++r) acc[r] = fmaf(s, comp(x, r), acc[r]);
             });
             if (d < Ddn) {
 #pragma unroll
@@ -581,10 +602,11 @@ int sms() {
     return n;
 }
 
-// largest VEC in {4,2,1} (capped by vmax) whose staging buffer fits
+// largest VEC in {4,2,1} (capped by vmax) whose staging buffer (with the
+// zero slots) fits
 int pick_vec(int64_t len, int elem_bytes, int vmax, int reserve) {
     for (int v = vmax; v >= 1; v >>= 1)
-        if ((int64_t)len * elem_bytes * v + reserve <= smem_optin()) return v;
+        if (staged_slots(len) * elem_bytes * v + reserve <= smem_optin()) return v;
     return 0;
 }
 
@@ -606,13 +628,18 @@ Launch shape(size_t smem, int ctas) {
 }
 
 // The dynamic shared-memory limit is a per-kernel attribute shared by every
-// host thread: raise it once, to the device maximum, so that a concurrent
-// launch of the same kernel can never see a lower limit.
-template <typename K>
-void allow_smem(K kern, size_t /*bytes*/) {
-    static const bool once = [kern] {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin());
-        return true;
+// host thread: raise it once per kernel (the template parameter is the kernel
+// itself, so each instantiation has its own flag), to the device maximum, so
+// that a concurrent launch of the same kernel can never see a lower limit.
+// The limit is what the opt-in maximum leaves next to the kernel's static
+// shared memory.
+template <auto Kern>
+void allow_smem() {
+    static const bool once = [] {
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, Kern) != cudaSuccess) return false;
+        const int dyn = smem_optin() - (int)fa.sharedSizeBytes;
+        return cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) == cudaSuccess;
     }();
     (void)once;
 }
@@ -682,9 +709,11 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             launch_max_exponent((const double*)v, H->D, emax, s);
             if (w_old != nullptr) launch_max_exponent((const double*)w_old, H->D, emax, s);
         }
-        const Launch LA = shape((size_t)Ddn * 8 * std::max(va, 1), H->ctas_rows);
+        const Launch LA = shape((size_t)staged_slots(Ddn) * 8 * std::max(va, 1), H->ctas_rows);
         long long* Y = (long long*)ybuf;
         int2* Xg = (int2*)((char*)ybuf + (size_t)H->D * 8);
+        // columns per lane in the up phase: 2 when Ddn is even (16-byte loads)
+        const int vpl = ((Ddn & 1) == 0 && H->vec_cols != 1) ? 2 : 1;
         int extra = 0;
         if (va == 0) {
             // rows longer than shared memory: fixed-point copy first, then gathers through L1/L2
@@ -704,7 +733,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             extra = 2;
         } else {
 #define ROWS64(V, E, P)                                                                                     \
-    allow_smem(k_rows_f64x<V, E>, LA.smem);                                                                  \
+    allow_smem<k_rows_f64x<V, E>>();                                                                         \
     k_rows_f64x<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const double*)v, Y, Xg, Dup, Ddn, dn.blk_off,  \
                                                             dn.blk_cnt, P, emax, fixed_emax)
         if (va == 2) {
@@ -719,7 +748,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
 #define UP64(V, F)                                                                                          \
     k_up_f64x<V, F><<<up_blocks, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,  \
                                               up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax)
-        if ((Ddn & 1) == 0) {
+        if (vpl == 2) {
             if (ep.fast) { UP64(2, true); } else { UP64(2, false); }
         } else {
             if (ep.fast) { UP64(1, true); } else { UP64(1, false); }
@@ -732,10 +761,13 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     // binary32
     const int va = choose_vec(H->vec_rows, Ddn, 4, 4, 0);
     if (va == 0) return -1;
-    const Launch LA = shape((size_t)Ddn * 4 * va, H->ctas_rows);
+    const Launch LA = shape((size_t)staged_slots(Ddn) * 4 * va, H->ctas_rows);
     float* Y = (float*)ybuf;
+    // columns per lane in the up phase: the widest aligned vector load, capped by vec_cols
+    int vpl = (Ddn & 3) == 0 ? 4 : ((Ddn & 1) == 0 ? 2 : 1);
+    if (H->vec_cols > 0 && H->vec_cols < vpl) vpl = H->vec_cols;
 #define ROWS32(V, E, P)                                                                                    \
-    allow_smem(k_rows_f32<V, E>, LA.smem);                                                                  \
+    allow_smem<k_rows_f32<V, E>>();                                                                         \
     k_rows_f32<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const float*)v, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, P)
 #define BOTH32(M, V, F, P16, P32) if (F) { M(V, uint16_t, P16); } else { M(V, uint32_t, P32); }
     if (va == 4) { BOTH32(ROWS32, 4, dn16, dn.ent16, dn.ent32) }
@@ -746,7 +778,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
 #define UP32(V)                                                                                            \
     k_up_f32<V><<<up_blocks, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old, Dup, Ddn,   \
         up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t, (float)H->U, (float)-beta)
-    if ((Ddn & 3) == 0) { UP32(4); } else if ((Ddn & 1) == 0) { UP32(2); } else { UP32(1); }
+    if (vpl == 4) { UP32(4); } else if (vpl == 2) { UP32(2); } else { UP32(1); }
 #undef UP32
     HUB_CUDA(cudaGetLastError());
     count_launches(2);

@@ -49,10 +49,11 @@ struct DevSpin {
     int32_t* sell_cnt = nullptr;     // [groups]
     uint32_t* sell_ent = nullptr;    // [sum cnt * 32]
     int64_t sell_entries = 0;
-    // the same table in blocks of 8 slots per lane ("SELL-32/8"): group g has
-    // blk_cnt[g] blocks at blk_off[g] (in entries); block b of lane l holds
-    // slots 8b .. 8b+7 at blk_off[g] + (b*32 + l)*8.  Entries are 16-bit when
-    // D < 2^14 (ent16), else 32-bit (ent32); same (target << 2) | code packing.
+    // the row-phase table in blocks of 8 slots per lane ("SELL-32/8"): group g
+    // has blk_cnt[g] blocks at blk_off[g] (in entries); block b of lane l holds
+    // slots 8b .. 8b+7 at blk_off[g] + (b*32 + l)*8.  Entry = staged slot index
+    // with the top bit set for sign -1; 16-bit (ent16) when the index fits 15
+    // bits, else 32-bit (ent32).  Indices >= D point at zero slots (padding).
     int64_t* blk_off = nullptr;      // [groups]
     int32_t* blk_cnt = nullptr;      // [groups]
     uint16_t* ent16 = nullptr;
