@@ -567,22 +567,53 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
 // One Lanczos step (Eqs. split1 + Algorithm 1 lines 5-11) on caller vectors.
 // fixed_emax: 1023 when f and g are known to have norm <= 1 (inside the
 // solver), 0 to derive the fixed-point scale from the data.
+// One step of Algorithm 1 in the two-vector form: g <- H f - beta_j g,
+// a_j = <g, f>, beta_{j+1} = |g - a_j f|.  The H*v kernels also reduce <g, f>,
+// <g, g> and <f, f> (fused, deterministic), so that
+//   beta_{j+1}^2 = <g, g> - 2 a_j^2 + a_j^2 <f, f>
+// without another pass; when that difference cancels more than six digits of
+// <g, g> (near breakdown), or the kernel path cannot fuse, g - a_j f is formed
+// and its norm taken explicitly.  *pending (may be null when normalise) tells
+// how g is left:
+//   true : g = H f - beta_j g; finish with launch_axpy_scale(-a_j, 1/beta_{j+1})
+//   false: g = H f - beta_j g - a_j f; finish with launch_scale(1/beta_{j+1})
+// Both finishes round as axpy then scale, so either leaves the same f_{j+1}.
 static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
-                             double* alpha, double* beta_next, bool normalise, int fixed_emax) {
+                             double* alpha, double* beta_next, bool normalise, int fixed_emax,
+                             bool* pending = nullptr) {
     int rc;
     if (dtype == HUB_F64 && !fixed_point_ok(H))
         return fail(HUB_EINVAL, "lanczos step: more than 127 hops per state is not supported");
-    // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels
-    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s))) return rc;
-    if ((rc = launch_dot(H, g, f, H->D, dtype, H->red, s))) return rc;
-    double a = 0.0;
-    if ((rc = reduce_partials_host(H->red, s, &a))) return rc;
-    if ((rc = launch_axpy_nrm2(-a, f, g, H->D, dtype, H->red, s))) return rc;
-    double b2 = 0.0;
-    if ((rc = reduce_partials_host(H->red, s, &b2))) return rc;
+    bool fused = false;
+    // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels with the reductions
+    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s, H->red, &fused))) return rc;
+    double a = 0.0, b2 = 0.0;
+    bool pend = false;
+    if (fused) {
+        double r[3];
+        if ((rc = reduce_partials3_host(H->red, s, r))) return rc;
+        a = r[0];
+        b2 = r[1] - 2.0 * a * a + a * a * r[2];
+        pend = b2 > 1e-6 * r[1];
+    } else {
+        if ((rc = launch_dot(H, g, f, H->D, dtype, H->red, s))) return rc;
+        if ((rc = reduce_partials_host(H->red, s, &a))) return rc;
+    }
+    if (!pend) {
+        if ((rc = launch_axpy_nrm2(-a, f, g, H->D, dtype, H->red, s))) return rc;
+        if ((rc = reduce_partials_host(H->red, s, &b2))) return rc;
+    }
     const double b = std::sqrt(std::max(b2, 0.0));
-    if (normalise && b > 0.0)
-        if ((rc = launch_scale(1.0 / b, g, H->D, dtype, s))) return rc;
+    if (normalise && b > 0.0) {
+        if (pend) rc = launch_axpy_scale(-a, 1.0 / b, f, g, H->D, dtype, s);
+        else rc = launch_scale(1.0 / b, g, H->D, dtype, s);
+        if (rc) return rc;
+        pend = false;
+    } else if (normalise && pend) {
+        if ((rc = launch_axpy_nrm2(-a, f, g, H->D, dtype, H->red, s))) return rc;
+        pend = false;
+    }
+    if (pending != nullptr) *pending = pend;
     *alpha = a;
     *beta_next = b;
     return HUB_OK;
@@ -636,7 +667,8 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
     double bj = 0.0;
     for (int j = 0; j < m_cap; ++j) {
         double aj = 0.0, bn = 0.0;
-        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023))) return rc;
+        bool pending = false;
+        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023, &pending))) return rc;
         R.a.push_back(aj);
         double s_last = 1.0;
         tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
@@ -654,7 +686,9 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
             R.converged = true;
             break;
         }
-        if ((rc = launch_scale(1.0 / bn, g, H->D, dtype, s))) return rc;
+        if (pending) rc = launch_axpy_scale(-aj, 1.0 / bn, f, g, H->D, dtype, s);
+        else rc = launch_scale(1.0 / bn, g, H->D, dtype, s);
+        if (rc) return rc;
         std::swap(f, g);
         bj = bn;
     }
@@ -778,8 +812,7 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         for (int j = 0; j + 1 < m; ++j) {
             const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
             if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
-            if ((rc = launch_axpy_nrm2(-R.a[(size_t)j], ff, gg, H->D, HUB_F32, H->red, s))) return rc;
-            if ((rc = launch_scale(1.0 / R.b[(size_t)j], gg, H->D, HUB_F32, s))) return rc;
+            if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
             std::swap(ff, gg);
             if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
         }

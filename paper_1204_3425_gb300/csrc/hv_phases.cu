@@ -14,10 +14,13 @@
 // Binary64 path: every element is rounded once to the fixed-point grid 2^-k
 // (k = 1070 - emax, emax = biased exponent bound of max|v|) and held as
 // (lo, hi) int32 words, X = hi * 2^24 + lo; hop sums are exact integer sums.
-// The column phase forms, exactly in 128-bit integers,
+// The up phase forms, exactly in 128-bit integers,
 //   T*A + X_own*B[n] + G*Bbeta,   A = -t 2^m, B[n] = U n 2^m, Bbeta = -beta 2^m
 // (T = hop sum, G = fixed-point w_old) and rounds it once to binary64: the
-// FP64 pipe (1.7 op/clk/SM on this part) is not used per element.
+// FP64 pipe (1.7 op/clk/SM on this part) is not used per element.  When t is
+// a power of two and U a small dyadic number (the usual t = 1, integer U),
+// the H v part fits int64 exactly and is rounded once; a Lanczos -beta w_old
+// term is then one fused multiply-add.
 #include <cstdint>
 #include <cmath>
 #include <type_traits>
@@ -293,6 +296,7 @@ struct EpiParams {
     int tneg;             // t < 0
     int ju;
     long long Uint;       // U * 2^ju
+    double mbeta;         // -beta, applied after the exact part in the int64 path
 };
 
 // Up phase, binary64 fixed point (Algorithms 2 and 4):
@@ -351,6 +355,58 @@ __device__ __forceinline__ void add4(int2& A, int2 a, int2 b, int2 c, int2 d) {
 }
 __device__ __forceinline__ void add4(int2& A, int2 a) { A.x += a.x; A.y += a.y; }
 
+// Lanczos reductions fused into the up-phase epilogue (Algorithm 1): each
+// thread accumulates <w, f>, <w, w> and <f, f> over its outputs in a fixed
+// order, the CTA sums its threads in a fixed tree, and the per-CTA partials
+// (part[b], part[kPartStride + b], part[2 kPartStride + b]) are summed in
+// index order afterwards, so the result is deterministic.  binary32 outputs
+// use a float-float accumulator (exact product split + TwoSum), as the
+// stand-alone dot kernel does.
+struct FFAcc {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add_product(float x, float y) {
+        const float p = x * y;
+        const float e = fmaf(x, y, -p);
+        const float t = hi + p;
+        const float bb = t - hi;
+        lo += ((hi - (t - bb)) + (p - bb)) + e;
+        hi = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ void block_sum3_store(double a, double b, double c, double* part) {
+    __shared__ double red[3][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        red[0][wid] = a;
+        red[1][wid] = b;
+        red[2][wid] = c;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        a = lane < nw ? red[0][lane] : 0.0;
+        b = lane < nw ? red[1][lane] : 0.0;
+        c = lane < nw ? red[2][lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+            c += __shfl_xor_sync(0xffffffffu, c, o);
+        }
+        if (lane == 0) {
+            part[blockIdx.x] = a;
+            part[kPartStride + blockIdx.x] = b;
+            part[2 * kPartStride + blockIdx.x] = c;
+        }
+    }
+}
+
 // Up phase, binary64 fixed point (Algorithms 2 and 4):
 //   W[u, c] = -t (sum_{(u', s) in hops_up(u)} s X[u', c] + Y[u, c]) + U n(u, c) X[u, c]  [- beta w_old]
 // Row u of W is a signed combination of whole rows u' of X (Eq. H-Kroneckersum),
@@ -359,8 +415,9 @@ __device__ __forceinline__ void add4(int2& A, int2 a) { A.x += a.x; A.y += a.y; 
 // items are (column chunk, block of kUpRows rows); consecutive items share a
 // chunk, which keeps that chunk of X resident in L2 while all rows are
 // combined, and consecutive rows share part of their neighbours (L1 reuse).
+// RED: also accumulate <W, fv>, <W, W> and <fv, fv> into part (block_sum3_store).
 template <int VPL, bool FAST>
-__global__ void __launch_bounds__(256, 3) k_up_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
+__global__ void __launch_bounds__(256, 4) k_up_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
                                                      double* w, const double* w_old, int64_t Dup, int64_t Ddn,
                                                      const int32_t* __restrict__ ptr,
                                                      const int32_t* __restrict__ npos,
@@ -429,6 +486,7 @@ __global__ void __launch_bounds__(256, 3) k_up_f64x(const int2* __restrict__ X, 
                         if (ep.tneg == 0) Pv = -Pv;
                         Pv += ep.Uint * (long long)__popc(su_u & sdc[j]) * fx_join(xo[j].x, xo[j].y);
                         r[j] = i64_scaled_to_double(Pv, -(k + ep.ju));
+                        if (w_old != nullptr) r[j] = fma(ep.mbeta, w_old[J + j], r[j]);
                     } else {
                         I128 acc{0ull, 0ll};
                         mac128(acc, fx_join(lo[j], hi[j]) + yv[j], ep.A);
@@ -448,6 +506,135 @@ __global__ void __launch_bounds__(256, 3) k_up_f64x(const int2* __restrict__ X, 
     }
 }
 
+// Lanczos-step variant of k_up_f64x (Algorithm 1 fused with Algorithms 2, 4):
+// W = H f - beta w_old and, per CTA, the partials of <W, f>, <W, W> and
+// <f, f> (block_sum3_store).  Its epilogue streams four arrays (own element,
+// Y, w_old, f), so with 16-byte vectors their loads are issued before the
+// gathers; the extra live registers cost one CTA per SM (3 instead of 4).
+template <int VPL, bool FAST>
+__global__ void __launch_bounds__(256, 3) k_up_step_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
+                                                     double* w, const double* w_old, int64_t Dup, int64_t Ddn,
+                                                     const int32_t* __restrict__ ptr,
+                                                     const int32_t* __restrict__ npos,
+                                                     const uint32_t* __restrict__ list,
+                                                     const uint32_t* __restrict__ su,
+                                                     const uint32_t* __restrict__ sd, EpiParams ep,
+                                                     const int* __restrict__ emax_p, int fixed_emax,
+                                                     const double* __restrict__ fv, double* part) {
+    double s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    using IV = typename FxVec<VPL>::T;
+    __shared__ long long Bs[33];
+    for (int i = threadIdx.x; i < 33; i += blockDim.x) Bs[i] = i < ep.nB ? ep.B[i] : 0;
+    __syncthreads();
+    const int emax = fixed_emax > 0 ? fixed_emax : max(*emax_p, 1);
+    const int k = 1070 - emax;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    constexpr int CC = 32 * VPL;
+    const int64_t nchunk = (Ddn + CC - 1) / CC;
+    const int64_t nrb = (Dup + kUpRows - 1) / kUpRows;
+    // item = chunk * nrb + rb, advanced by gridDim.x without division
+    int64_t chunk = blockIdx.x / nrb, rb = blockIdx.x % nrb;
+    const int64_t dch = gridDim.x / nrb, drb = gridDim.x % nrb;
+    for (; chunk < nchunk; chunk += dch, rb += drb) {
+        if (rb >= nrb) {
+            rb -= nrb;
+            ++chunk;
+            if (chunk >= nchunk) break;
+        }
+        const int64_t c_raw = chunk * CC + (int64_t)lane * VPL;
+        const bool act = c_raw < Ddn;
+        const int64_t c = act ? c_raw : Ddn - VPL;     // tail lanes read a valid column, store nothing
+        uint32_t sdc[VPL];
+#pragma unroll
+        for (int j = 0; j < VPL; ++j) sdc[j] = sd[c + j];
+        const IV* base = reinterpret_cast<const IV*>(X + c);
+        const int64_t uend = min(rb * kUpRows + kUpRows, Dup);
+        for (int64_t u = rb * kUpRows + warp; u < uend; u += nw) {
+            const int32_t kb = ptr[u];
+            const int64_t J = u * Ddn + c;
+            // streamed operands of the epilogue, requested before the gathers
+            double wpre[VPL], fpre[VPL];
+            int4 t4p;
+            longlong2 y2p;
+            if constexpr (VPL == 2) {
+                t4p = __ldg(reinterpret_cast<const int4*>(X + J));
+                y2p = __ldcs(reinterpret_cast<const longlong2*>(Y + J));
+                if (w_old != nullptr) {
+                    const double2 q = __ldcs(reinterpret_cast<const double2*>(w_old + J));
+                    wpre[0] = q.x; wpre[1] = q.y;
+                }
+                {
+                    const double2 q = __ldcs(reinterpret_cast<const double2*>(fv + J));
+                    fpre[0] = q.x; fpre[1] = q.y;
+                }
+            }
+            IV P{}, N{};
+            uniform_hops<IV>(list, kb, ptr[u + 1] - kb, npos[u], lane, P, N,
+                [&](uint32_t t) { return __ldg(reinterpret_cast<const IV*>(reinterpret_cast<const int2*>(base) + (int64_t)t * Ddn)); },
+                [](IV& A, auto... xs) { add4(A, xs...); });
+            if (act) {
+                const uint32_t su_u = su[u];
+                int lo[VPL], hi[VPL];
+                int2 xo[VPL];
+                long long yv[VPL];
+                if constexpr (VPL == 2) {
+                    lo[0] = P.x - N.x; hi[0] = P.y - N.y; lo[1] = P.z - N.z; hi[1] = P.w - N.w;
+                    const int4 t4 = t4p;
+                    xo[0] = make_int2(t4.x, t4.y);
+                    xo[1] = make_int2(t4.z, t4.w);
+                    const longlong2 y2 = y2p;
+                    yv[0] = y2.x;
+                    yv[1] = y2.y;
+                } else {
+                    lo[0] = P.x - N.x; hi[0] = P.y - N.y;
+                    xo[0] = __ldg(X + J);
+                    yv[0] = __ldcs(Y + J);
+                }
+                double r[VPL];
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) {
+                    if constexpr (FAST) {
+                        // exact: |T| < 2^55, |X| <= 2^48, |Uint * n| < 2^14 and tshift <= 6
+                        long long Pv = (fx_join(lo[j], hi[j]) + yv[j]) << ep.tshift;
+                        if (ep.tneg == 0) Pv = -Pv;
+                        Pv += ep.Uint * (long long)__popc(su_u & sdc[j]) * fx_join(xo[j].x, xo[j].y);
+                        r[j] = i64_scaled_to_double(Pv, -(k + ep.ju));
+                        if (w_old != nullptr) r[j] = fma(ep.mbeta, VPL == 2 ? wpre[j] : w_old[J + j], r[j]);
+                    } else {
+                        I128 acc{0ull, 0ll};
+                        mac128(acc, fx_join(lo[j], hi[j]) + yv[j], ep.A);
+                        mac128(acc, fx_join(xo[j].x, xo[j].y), Bs[__popc(su_u & sdc[j])]);
+                        if (w_old != nullptr) {
+                            int glo, ghi;
+                            fx_split(w_old[J + j], emax, glo, ghi);
+                            mac128(acc, fx_join(glo, ghi), ep.Bbeta);
+                        }
+                        r[j] = i128_to_double(acc, -(k + ep.m));
+                    }
+                }
+                if constexpr (VPL == 2) __stcs(reinterpret_cast<double2*>(w + J), make_double2(r[0], r[1]));
+                else __stcs(w + J, r[0]);
+                {
+                    double fj[VPL];
+                    if constexpr (VPL == 2) {
+                        fj[0] = fpre[0];
+                        fj[1] = fpre[1];
+                    } else {
+                        fj[0] = __ldcs(fv + J);
+                    }
+#pragma unroll
+                    for (int j = 0; j < VPL; ++j) {
+                        s1 = fma(r[j], fj[j], s1);
+                        s2 = fma(r[j], r[j], s2);
+                        s3 = fma(fj[j], fj[j], s3);
+                    }
+                }
+            }
+        }
+    }
+    block_sum3_store(s1, s2, s3, part);
+}
+
 __device__ __forceinline__ void addf(float& A, float a, float b, float c, float d) { A += (a + b) + (c + d); }
 __device__ __forceinline__ void addf(float& A, float a) { A += a; }
 __device__ __forceinline__ void addf(float2& A, float2 a, float2 b, float2 c, float2 d) {
@@ -465,13 +652,18 @@ __device__ __forceinline__ void addf(float4& A, float4 a) { A.x += a.x; A.y += a
 
 // Up phase, binary32: same decomposition, float arithmetic
 template <int VPL>
-__global__ void __launch_bounds__(256, 3) k_up_f32(const float* __restrict__ v, const float* __restrict__ Y, float* w,
+constexpr int up32_ctas() { return VPL == 4 ? 4 : 5; }
+
+template <int VPL, bool RED>
+__global__ void __launch_bounds__(256, up32_ctas<VPL>()) k_up_f32(const float* __restrict__ v, const float* __restrict__ Y, float* w,
                                                     const float* w_old, int64_t Dup, int64_t Ddn,
                                                     const int32_t* __restrict__ ptr,
                                                     const int32_t* __restrict__ npos,
                                                     const uint32_t* __restrict__ list,
                                                     const uint32_t* __restrict__ su,
-                                                    const uint32_t* __restrict__ sd, float mt, float U, float mbeta) {
+                                                    const uint32_t* __restrict__ sd, float mt, float U, float mbeta,
+                                                    double* part) {
+    FFAcc s1, s2, s3;
     using V = typename F32Vec<VPL>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int CC = 32 * VPL;
@@ -514,9 +706,18 @@ __global__ void __launch_bounds__(256, 3) k_up_f32(const float* __restrict__ v, 
                 if constexpr (VPL == 4) __stcs(reinterpret_cast<float4*>(w + J), make_float4(r[0], r[1], r[2], r[3]));
                 else if constexpr (VPL == 2) __stcs(reinterpret_cast<float2*>(w + J), make_float2(r[0], r[1]));
                 else __stcs(w + J, r[0]);
+                if constexpr (RED) {
+#pragma unroll
+                    for (int j = 0; j < VPL; ++j) {
+                        s1.add_product(r[j], comp(xo, j));
+                        s2.add_product(r[j], r[j]);
+                        s3.add_product(comp(xo, j), comp(xo, j));
+                    }
+                }
             }
         }
     }
+    if constexpr (RED) block_sum3_store(s1.value(), s2.value(), s3.value(), part);
 }
 
 // ---------------------------------------------------------------------------
@@ -659,10 +860,13 @@ EpiParams make_epilogue(double t, double U, int ns, double beta) {
     p.Bbeta = (long long)std::llround(std::ldexp(-beta, m));
     p.nB = std::min(ns, 32) + 1;
     for (int n = 0; n < 33; ++n) p.B[n] = n < p.nB ? (long long)std::llround(std::ldexp(U * n, m)) : 0;
-    // exact int64 path: t = +-2^et (et in [-8, 6]), U * 2^ju integer for some ju in [0, 8] with
-    // |U 2^ju| * Ns < 2^14, no beta term; the shifted hop sum stays below 2^(55+6+8) ... bounded below
+    // int64 path: t = +-2^et and U * 2^ju an integer with |U 2^ju| Ns < 2^14 for some ju in [0, 8],
+    // et + ju in [0, 6].  Then |T 2^(et+ju)| < 2^55 * 2^6 and |U 2^ju n X| < 2^14 * 2^48, so
+    // H v is formed exactly in int64 and rounded once; a -beta w_old term is then added with
+    // one fused multiply-add (a second rounding)
     p.fast = 0;
-    if (beta == 0.0 && t != 0.0) {
+    p.mbeta = -beta;
+    if (t != 0.0) {
         int et = 0;
         const double mt = std::frexp(std::fabs(t), &et);   // |t| = mt * 2^et, mt in [0.5, 1)
         if (mt == 0.5) {
@@ -695,12 +899,18 @@ int choose_vec(int req, int64_t len, int elem_bytes, int vmax, int reserve) {
 // Returns HUB_OK and launches, or returns -1 when the staging buffers do not fit
 // (the caller then uses the single-pass gather kernel).
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                     void* ybuf, int fixed_emax, cudaStream_t s) {
+                     void* ybuf, int fixed_emax, cudaStream_t s, double* part, int* nparts) {
+    if (nparts != nullptr) *nparts = 0;
+    if (sms() * 5 > kPartStride) part = nullptr;        // partial arrays too short: no fused reduction
     const DevSpin& up = H->dev[0];
     const DevSpin& dn = H->dev[1];
     const int64_t Dup = H->Dup, Ddn = H->Ddn;
     const bool dn16 = dn.ent16 != nullptr;
-    const int up_blocks = sms() * 3;
+    // up-phase CTAs: as many as the launch bounds keep resident (the phase is
+    // bound by L2 latency, so occupancy is what counts: 4 per SM at <= 64
+    // registers for binary64 (3 for the Lanczos variant, whose prefetched
+    // epilogue operands need the registers), 5 at <= 51 for binary32 with up
+    // to 2 columns per lane; measured best)
     if (dtype == HUB_F64) {
         const int va = choose_vec(H->vec_rows, Ddn, 8, 2, 0);
         int* emax = H->status;
@@ -745,15 +955,21 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
         }
 #undef ROWS64
         const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
-#define UP64(V, F)                                                                                          \
-    k_up_f64x<V, F><<<up_blocks, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,  \
-                                              up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax)
+        const int up_grid = sms() * (part != nullptr ? 3 : 4);
+#define UP64(K, V, F)                                                                                       \
+    K<V, F><<<up_grid, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,             \
+        up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax
+#define UP64_R(V, F)                                                                                        \
+    if (part != nullptr) { UP64(k_up_step_f64x, V, F), (const double*)v, part); }                          \
+    else { UP64(k_up_f64x, V, F)); }
         if (vpl == 2) {
-            if (ep.fast) { UP64(2, true); } else { UP64(2, false); }
+            if (ep.fast) { UP64_R(2, true) } else { UP64_R(2, false) }
         } else {
-            if (ep.fast) { UP64(1, true); } else { UP64(1, false); }
+            if (ep.fast) { UP64_R(1, true) } else { UP64_R(1, false) }
         }
+#undef UP64_R
 #undef UP64
+        if (part != nullptr && nparts != nullptr) *nparts = up_grid;
         HUB_CUDA(cudaGetLastError());
         count_launches(1 + extra + (fixed_emax <= 0 ? (w_old ? 2 : 1) : 0));
         return HUB_OK;
@@ -775,11 +991,22 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     else { BOTH32(ROWS32, 1, dn16, dn.ent16, dn.ent32) }
 #undef BOTH32
 #undef ROWS32
+    int up_grid = 0;
 #define UP32(V)                                                                                            \
-    k_up_f32<V><<<up_blocks, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old, Dup, Ddn,   \
-        up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t, (float)H->U, (float)-beta)
-    if (vpl == 4) { UP32(4); } else if (vpl == 2) { UP32(2); } else { UP32(1); }
+    {                                                                                                      \
+        up_grid = sms() * up32_ctas<V>();                                                                  \
+        if (part != nullptr)                                                                               \
+            k_up_f32<V, true><<<up_grid, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old,  \
+                Dup, Ddn, up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t,           \
+                (float)H->U, (float)-beta, part);                                                          \
+        else                                                                                               \
+            k_up_f32<V, false><<<up_grid, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old, \
+                Dup, Ddn, up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t,           \
+                (float)H->U, (float)-beta, part);                                                          \
+    }
+    if (vpl == 4) { UP32(4) } else if (vpl == 2) { UP32(2) } else { UP32(1) }
 #undef UP32
+    if (part != nullptr && nparts != nullptr) *nparts = up_grid;
     HUB_CUDA(cudaGetLastError());
     count_launches(2);
     return HUB_OK;

@@ -91,19 +91,28 @@ struct hubbard_sector {
 namespace hub {
 constexpr int kRedSlots = 4096;      // partial-sum slots for block reductions
 constexpr int kRedBlocks = 1024;     // grid size of reduction kernels (<= kRedSlots/2)
+constexpr int kPartStride = 1024;    // stride of the partial arrays of a fused three-value reduction
 
 // process-wide count of kernel launches (hubbard_kernel_launches)
 void count_launches(int n);
 
 // kernels.cu launchers -------------------------------------------------------
 int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dtype, cudaStream_t s);
+// part != nullptr: also reduce <w, v>, <w, w> and <v, v> into
+// part[kRedSlots-1], part[kRedSlots-2], part[kRedSlots-3] (fused Lanczos
+// reductions); *fused tells whether that happened (the kernel path in use may
+// not support it).
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta,
-                   const void* w_old, int fixed_emax, cudaStream_t s);
+                   const void* w_old, int fixed_emax, cudaStream_t s, double* part = nullptr,
+                   bool* fused = nullptr);
 // hv_phases.cu: two-phase shared-memory H*v; -1 when the staging buffers do not fit.
 // fixed_emax > 0 fixes the fixed-point exponent bound (vectors of norm <= 1:
 // 1023); otherwise it is computed from v and w_old.
+// part != nullptr: the up phase writes per-CTA partials of <w, v>, <w, w> and
+// <v, v> at part[b], part[kPartStride + b], part[2 kPartStride + b];
+// *nparts = their count (<= kPartStride).
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                     void* ybuf, int fixed_emax, cudaStream_t s);
+                     void* ybuf, int fixed_emax, cudaStream_t s, double* part = nullptr, int* nparts = nullptr);
 // max biased binary64 exponent of |v| folded into *emax (atomicMax; caller zeroes it)
 void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s);
 // binary64 -> (lo, hi) fixed point with the exponent bound *emax (read on the device)
@@ -111,6 +120,10 @@ void launch_to_fixed(const double* v, int64_t n, void* X, const int* emax, cudaS
 int launch_dot(const hubbard_sector* H, const void* x, const void* y, int64_t n, int dtype,
                double* partials, cudaStream_t s);
 int reduce_partials_host(double* partials, cudaStream_t s, double* out);
+// the three sums of a fused reduction: out[k] = part[kRedSlots-1-k]
+int reduce_partials3_host(double* partials, cudaStream_t s, double out[3]);
+// y <- (y + a x) * inv, rounded as launch_axpy_nrm2 followed by launch_scale
+int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s);
 int launch_axpy(double a, const void* x, void* y, int64_t n, int dtype, cudaStream_t s);
 int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, double* partials,
                      cudaStream_t s);

@@ -238,6 +238,17 @@ __global__ void k_scale(T a, T* __restrict__ y, int64_t n) {
         y[i] *= a;
 }
 
+// y <- (y + a x) * inv with the roundings of k_axpy_nrm2 then k_scale
+__global__ void k_axpy_scale_f64(double a, double inv, const double* __restrict__ x, double* __restrict__ y,
+                                 int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fma(a, x[i], y[i]) * inv;
+}
+__global__ void k_axpy_scale_f32(float a, float inv, const float* __restrict__ x, float* __restrict__ y, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fmaf(a, x[i], y[i]) * inv;
+}
+
 template <typename T>
 __global__ void k_copy_scale(const T* __restrict__ x, T* __restrict__ y, int64_t n, T a) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -279,6 +290,25 @@ __global__ void k_finish_sum(double* partials, int nb) {
     if (threadIdx.x == 0) partials[kRedSlots - 1] = s;
 }
 
+// the three arrays of a fused reduction (part[q kPartStride .. + nb)), each
+// summed in a fixed order, into part[kRedSlots-1-q]
+__global__ void k_finish_sum3(double* partials, int nb) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += partials[i];
+        b += partials[kPartStride + i];
+        c += partials[2 * kPartStride + i];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    c = block_sum(c);
+    if (threadIdx.x == 0) {
+        partials[kRedSlots - 1] = a;
+        partials[kRedSlots - 2] = b;
+        partials[kRedSlots - 3] = c;
+    }
+}
+
 int red_grid(int64_t n) { return grid_for(n, kThreads * 4, kRedBlocks); }
 
 }  // namespace
@@ -311,13 +341,23 @@ void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s) 
 }
 
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                   int fixed_emax, cudaStream_t s) {
+                   int fixed_emax, cudaStream_t s, double* part, bool* fused) {
     const DevSpin& up = H->dev[0];
     const DevSpin& dn = H->dev[1];
     const int grid = grid_for(H->Dup, 1, sm_count() * 16);
+    if (fused != nullptr) *fused = false;
     if (H->fx_bytes >= (size_t)H->D * 16) {
-        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s);
-        if (rc != -1) return rc;
+        int np = 0;
+        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s, part, &np);
+        if (rc != -1) {
+            if (rc == HUB_OK && part != nullptr && np > 0) {
+                k_finish_sum3<<<1, 1024, 0, s>>>(part, np);
+                HUB_CUDA(cudaGetLastError());
+                count_launches(1);
+                if (fused != nullptr) *fused = true;
+            }
+            return rc;
+        }
     }
     if (dtype == HUB_F32) {
         if (w_old != nullptr || beta != 0.0) return fail(HUB_EINVAL, "f32 fused step not available");
@@ -375,6 +415,25 @@ int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, dou
     k_finish_sum<<<1, 1024, 0, s>>>(partials, g);
     HUB_CUDA(cudaGetLastError());
     count_launches(2);
+    return HUB_OK;
+}
+
+int reduce_partials3_host(double* partials, cudaStream_t s, double out[3]) {
+    double t[3];
+    HUB_CUDA(cudaMemcpyAsync(t, partials + (kRedSlots - 3), 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    out[0] = t[2];
+    out[1] = t[1];
+    out[2] = t[0];
+    return HUB_OK;
+}
+
+int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    if (dtype == HUB_F64) k_axpy_scale_f64<<<g, kThreads, 0, s>>>(a, inv, (const double*)x, (double*)y, n);
+    else k_axpy_scale_f32<<<g, kThreads, 0, s>>>((float)a, (float)inv, (const float*)x, (float*)y, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
     return HUB_OK;
 }
 

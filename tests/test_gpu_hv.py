@@ -135,6 +135,31 @@ def test_lanczos_step_matches_oracle(dev):
     assert np.abs(gd.cpu().numpy() - q / b).max() <= 1e-12
 
 
+@pytest.mark.parametrize("dt,norm_tol,ab_tol", [("f64", 1e-13, 1e-11), ("f32", 3e-6, 1e-4)])
+def test_fused_lanczos_steps_keep_unit_norm(dev, dt, norm_tol, ab_tol):
+    """120 steps with the reductions fused into H*v (beta^2 = <w,w> - 2a^2 + a^2 <f,f>):
+    every f_j stays a unit vector (normalisation errors do not compound) and each
+    (a, b) matches an explicit binary64 evaluation of the same update."""
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    H, S = _sector("sq4x2", 3, 5, 1.0, 2.0)
+    f = torch.from_numpy(start_vector(S.D, seed=11)).to(dev, tdt)
+    f /= f.norm()
+    g = torch.zeros_like(f)
+    hf = torch.empty_like(f)
+    beta = 0.0
+    for j in range(120):
+        hub.hubbard_apply(H, f, hf)
+        q = hf.double() - beta * g.double()
+        a_ref = float(q @ f.double())
+        b_ref = float(torch.linalg.norm(q - a_ref * f.double()))
+        a, b = hub.hubbard_lanczos_step(H, f, g, beta)
+        assert abs(a - a_ref) <= ab_tol * max(1.0, abs(a_ref)), (j, a, a_ref)
+        assert abs(b - b_ref) <= ab_tol * max(1.0, b_ref), (j, b, b_ref)
+        assert abs(float(torch.linalg.norm(g.double())) - 1.0) <= norm_tol, j
+        f, g = g, f
+        beta = b
+
+
 def test_lanczos_breakdown_tiny_sector(dev):
     # one electron on a 4-ring: eigenvalues -2, 0, 0, 2, so the Krylov space
     # of any start vector has dimension 3 and step 3 breaks down (b_4 ~ 0)
