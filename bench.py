@@ -60,7 +60,7 @@ def workload_config(name):
 # DRAM bytes per hubbard_apply from the ncu capture summarised in
 # profiles/hv_f64_sq4x4_n6_6_phases_ncu.md (small case scaled by D to the bench
 # sector); must be set back to None whenever the H*v kernels change.
-TRAFFIC = {"sq4x4_n8_8_U8_f64": None}
+TRAFFIC = {"sq4x4_n8_8_U8_f64": 9.16e9}
 
 
 def peaks():
