@@ -60,7 +60,7 @@ struct BatchParams {
     int2* xg;              // global fixed-point copies (team tasks)
     double* ab;            // a/b histories
     double* tri;           // tridiagonal scratch, 4 * max_iters per CTA
-    double* partial;       // [sector][2][kMaxTeam]
+    double* partial;       // [sector][2][3][kMaxTeam]
     unsigned int* bar;     // team barrier counters [sector]
     lanczos_result* res;   // [sector]
     int* err;              // batch error word
@@ -255,34 +255,46 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         const uint32_t* dst = P.st + S.dn_st;
         double* A = P.ab + S.ab;
         double* B = A + P.max_iters;
-        double* part = P.partial + (int64_t)task.sector * 2 * kMaxTeam;
+        double* part = P.partial + (int64_t)task.sector * 2 * 3 * kMaxTeam;
         unsigned* ctr = P.bar + task.sector;
         unsigned gen = 0;
-        bool alive = true;
-        // deterministic team sum: block tree, then the team's partials in rank order
-        auto team_sum = [&](double v) -> double {
-            const double s = block_reduce(v, red);
-            if (team == 1) return s;
+        // deterministic team sums of nv <= 3 values (in place): block tree, then
+        // the team's partials in rank order
+        auto team_sum = [&](int nv, double* v) -> bool {
+            for (int q = 0; q < nv; ++q) v[q] = block_reduce(v[q], red);
+            if (team == 1) return true;
             ++gen;
-            if (threadIdx.x == 0) part[(gen & 1) * kMaxTeam + rank] = s;
-            if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) {
-                alive = false;
-                return 0.0;
+            double* pg = part + (int64_t)(gen & 1) * 3 * kMaxTeam;
+            if (threadIdx.x == 0)
+                for (int q = 0; q < nv; ++q) pg[q * kMaxTeam + rank] = v[q];
+            if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) return false;
+            for (int q = 0; q < nv; ++q) {
+                double t = 0.0;
+                for (int r = 0; r < team; ++r) t += __ldcg(pg + q * kMaxTeam + r);
+                v[q] = t;
             }
-            double t = 0.0;
-            for (int r = 0; r < team; ++r) t += __ldcg(part + (gen & 1) * kMaxTeam + r);
-            return t;
+            return true;
         };
-        // f_1 = v0 / |v0|, f_0 = 0
-        double nn = 0.0;
-        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) nn = fma(v0[j], v0[j], nn);
-        nn = team_sum(nn);
-        if (!alive) return;
-        const double inv0 = 1.0 / sqrt(nn);
+        auto sync_team = [&]() -> bool {
+            if (team == 1) {
+                __syncthreads();
+                return true;
+            }
+            ++gen;
+            return team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag);
+        };
+        // f_1 = v0 / |v0|, f_0 = 0, and the fixed-point copy of f_1 (|f| <= 1)
+        double nn[1] = {0.0};
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) nn[0] = fma(v0[j], v0[j], nn[0]);
+        if (!team_sum(1, nn)) return;
+        const double inv0 = 1.0 / sqrt(nn[0]);
         for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            f[j] = v0[j] * inv0;
+            const double x = v0[j] * inv0;
+            f[j] = x;
             g[j] = 0.0;
+            X[j] = fixed47(x);
         }
+        if (!sync_team()) return;
         const double scale = -S.t * 0x1p-47;           // -t times the fixed-point unit
         const int mcap = (int)((int64_t)P.max_iters < D ? (int64_t)P.max_iters : D);
         double beta = 0.0, theta = 0.0, rho = 0.0;
@@ -290,16 +302,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         if (threadIdx.x == 0) sh_prev = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no previous value
         double amax = 1.0;
         for (int it = 0; it < mcap; ++it) {
-            // fixed-point copy of f (|f| <= 1) for the exact hop sums
-            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) X[j] = fixed47(f[j]);
-            if (team > 1) {
-                ++gen;
-                if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) return;
-            } else {
-                __syncthreads();
-            }
-            // q = H f - beta g  (Eqs. split1), alpha = q . f
-            double ap = 0.0;
+            // q = H f - beta g  (Eqs. split1) with <q, f>, <q, q>, <f, f>
+            double ap = 0.0, qq = 0.0, ff = 0.0;
             auto element = [&](int64_t u, int64_t d, int lo, int hi) {
                 const int64_t j = u * Ddn + d;
                 const long long Sx = ((long long)hi << 24) + (long long)lo;
@@ -307,21 +311,25 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                 const double q = fma(-beta, g[j], fma(S.U * (double)__popc(ust[u] & dst[d]), fj, scale * (double)Sx));
                 g[j] = q;
                 ap = fma(q, fj, ap);
+                qq = fma(q, q, qq);
+                ff = fma(fj, fj, ff);
             };
             if (in_smem) {
                 // whole fixed-point vector in shared memory: flat loop over elements
-                for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-                    const int64_t u = j / Ddn, d = j - u * Ddn;
+                // (D <= smem_elems, so 32-bit index arithmetic)
+                const int Dd = (int)Ddn;
+                for (int jj = (int)j0 + threadIdx.x; jj < (int)j1; jj += blockDim.x) {
+                    const int u = jj / Dd, d = jj - u * Dd;
                     int lo = 0, hi = 0;
                     for (int32_t k = urp[u]; k < urp[u + 1]; ++k) {
                         const uint32_t e = uent[k];
-                        const int2 x = X[(int64_t)(e >> 1) * Ddn + d];
+                        const int2 x = X[(int)(e >> 1) * Dd + d];
                         if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
                     }
-                    const int64_t rowb = u * Ddn;
+                    const int rowb = u * Dd;
                     for (int32_t k = drp[d]; k < drp[d + 1]; ++k) {
                         const uint32_t e = dent[k];
-                        const int2 x = X[rowb + (e >> 1)];
+                        const int2 x = X[rowb + (int)(e >> 1)];
                         if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
                     }
                     element(u, d, lo, hi);
@@ -329,7 +337,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             } else {
                 // global copy (L2): a warp per row; the row is staged in shared
                 // memory for the down-hops, up-hops read whole neighbour rows
-                // with lanes over columns (coalesced, warp-uniform hop list)
+                // with lanes over columns (coalesced, warp-uniform hop list held
+                // in the lanes); column loops are warp-uniform
                 int2* buf = xs + (int64_t)warp * Ddn;
                 for (int64_t u = r0 + warp; u < r1; u += nwarps) {
                     const int2* xr = X + u * Ddn;
@@ -339,35 +348,54 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                         xr = buf;
                     }
                     const int32_t kb = urp[u], ke = urp[u + 1];
-                    for (int64_t d = lane; d < Ddn; d += 32) {
+                    const int nh = ke - kb;
+                    const uint32_t mine = lane < nh ? uent[kb + lane] : 0u;
+                    for (int64_t d0 = 0; d0 < Ddn; d0 += 32) {
+                        const int64_t d = d0 + lane;
+                        const bool act = d < Ddn;
+                        const int64_t dd = act ? d : Ddn - 1;
                         int lo = 0, hi = 0;
+                        if (nh <= 32) {
 #pragma unroll 4
-                        for (int32_t k = kb; k < ke; ++k) {
-                            const uint32_t e = uent[k];
-                            const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + d);
-                            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                            for (int k = 0; k < nh; ++k) {
+                                const uint32_t e = __shfl_sync(0xffffffffu, mine, k);
+                                const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + dd);
+                                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                            }
+                        } else {
+                            for (int32_t k = kb; k < ke; ++k) {
+                                const uint32_t e = uent[k];
+                                const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + dd);
+                                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+                            }
                         }
-                        for (int32_t k = drp[d]; k < drp[d + 1]; ++k) {
+                        for (int32_t k = drp[dd]; k < drp[dd + 1]; ++k) {
                             const uint32_t e = dent[k];
                             const int2 x = rowbuf ? xr[e >> 1] : __ldcg(xr + (e >> 1));
                             if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
                         }
-                        element(u, d, lo, hi);
+                        if (act) element(u, d, lo, hi);
                     }
                     __syncwarp();
                 }
             }
-            const double alpha = team_sum(ap);
-            if (!alive) return;
-            // r = q - alpha f, beta_next = |r|
-            double bp = 0.0;
-            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-                const double r = fma(-alpha, f[j], g[j]);
-                g[j] = r;
-                bp = fma(r, r, bp);
+            double sv[3] = {ap, qq, ff};
+            if (!team_sum(3, sv)) return;
+            const double alpha = sv[0];
+            // |q - alpha f|^2 = <q,q> - 2 alpha <q,f> + alpha^2 <f,f>, unless that
+            // cancels more than six digits (near breakdown): then form it
+            double b2 = sv[1] - 2.0 * alpha * alpha + alpha * alpha * sv[2];
+            const bool fused = b2 > 1e-6 * sv[1];
+            if (!fused) {
+                double bp[1] = {0.0};
+                for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+                    const double r = fma(-alpha, f[j], g[j]);
+                    g[j] = r;
+                    bp[0] = fma(r, r, bp[0]);
+                }
+                if (!team_sum(1, bp)) return;
+                b2 = bp[0];
             }
-            const double b2 = team_sum(bp);
-            if (!alive) return;
             const double bn = sqrt(fmax(b2, 0.0));
             if (threadIdx.x == 0) {
                 A[it] = alpha;
@@ -395,14 +423,19 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                     break;
                 }
             }
-            // f_{j+1} = r / beta_next; the old f becomes f_{j-1}
+            // f_{j+1} = (q - alpha f) / beta_next (rounded as axpy then scale) and
+            // its fixed-point copy; the old f becomes f_{j-1}
             const double ib = 1.0 / bn;
-            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) g[j] *= ib;
+            for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+                const double x = (fused ? fma(-alpha, f[j], g[j]) : g[j]) * ib;
+                g[j] = x;
+                X[j] = fixed47(x);
+            }
+            if (!sync_team()) return;
             double* tmp = f;
             f = g;
             g = tmp;
             beta = bn;
-            __syncthreads();
         }
         if (rank == 0 && threadIdx.x == 0) {
             lanczos_result r;
@@ -563,7 +596,7 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     L.xg = o; o += al256(T * 8);
     L.ab = o; o += al256(n * 2 * (size_t)max_iters * 8);
     L.tri = o; o += al256((size_t)B->grid * 4 * (size_t)max_iters * 8);
-    L.partial = o; o += al256(n * 2 * kMaxTeam * 8);
+    L.partial = o; o += al256(n * 2 * 3 * kMaxTeam * 8);
     L.bar = o; o += al256(n * 4);
     L.res = o; o += al256(n * sizeof(lanczos_result));
     L.err = o; o += 256;
