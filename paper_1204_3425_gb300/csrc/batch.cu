@@ -26,7 +26,7 @@
 namespace hub {
 namespace {
 
-constexpr int kBatchThreads = 512;
+constexpr int kBatchThreads = 480;   // 15 warps: two CTAs per SM leave each warp a 945-element row slice
 constexpr int kMaxTeam = 32;
 constexpr int kCheckEvery = 4;        // Ritz-value test every few steps
 
@@ -68,6 +68,20 @@ struct BatchParams {
     double tol;
     int smem_elems;        // capacity of the shared fixed-point buffer
     long long spin_limit;  // bounded waits
+    // grid-synchronous sweep (sectors above the schedule's size threshold)
+    int nswp;
+    const int* swp;        // [nswp] sector ids
+    const int64_t* rowoff; // [nswp + 1] prefix sums of their D_up
+    double* rowpart;       // [rowoff[nswp]][3] per-row partial sums
+    struct SweepState* sst;// [nswp]
+    unsigned int* gbar;    // grid barrier counter
+    int* nactive;          // sectors of the sweep still iterating
+};
+
+// Lanczos state of a swept sector between the phases of one iteration.
+struct SweepState {
+    double beta, alpha, ib, amax, prev;
+    int fused, active, m, broke;
 };
 
 __device__ __forceinline__ int2 fixed47(double x) {
@@ -221,6 +235,270 @@ __device__ __noinline__ double d_last_component(const double* a, const double* b
     return exp2(-0.5 * scale_log) / sqrt(n2);
 }
 
+// One sector as seen by the element pass.
+struct SecView {
+    const int2* X;         // fixed-point copy of f (global)
+    const double* f;
+    double* g;
+    const int32_t *urp, *drp;
+    const uint32_t *uent, *dent, *ust, *dst;
+    int64_t Ddn;
+    double U, scale;       // scale = -t * 2^-47
+};
+
+// Row u of q = H f - beta g (Eqs. split1) by one warp, the fixed-point copy in
+// global memory (L2): the row is staged in buf (when given) for the
+// down-hops, up-hops read whole neighbour rows with lanes over columns
+// (coalesced; the row's hop list is held in the lanes, the column loop is
+// warp-uniform).  Adds this lane's <q,f>, <q,q>, <f,f> over the row.
+__device__ __forceinline__ void row_pass(const SecView& V, int64_t u, int2* buf, double beta, double& ap,
+                                         double& qq, double& ff) {
+    const int lane = threadIdx.x & 31;
+    const int64_t Ddn = V.Ddn;
+    const int2* xr = V.X + u * Ddn;
+    if (buf != nullptr) {
+        for (int64_t d = lane; d < Ddn; d += 32) buf[d] = __ldcg(xr + d);
+        __syncwarp();
+        xr = buf;
+    }
+    const int32_t kb = V.urp[u], ke = V.urp[u + 1];
+    const int nh = ke - kb;
+    const uint32_t mine = lane < nh ? V.uent[kb + lane] : 0u;
+    const uint32_t su_u = V.ust[u];
+    for (int64_t d0 = 0; d0 < Ddn; d0 += 32) {
+        const int64_t d = d0 + lane;
+        const bool act = d < Ddn;
+        const int64_t dd = act ? d : Ddn - 1;
+        int lo = 0, hi = 0;
+        if (nh <= 32) {
+#pragma unroll 4
+            for (int k = 0; k < nh; ++k) {
+                const uint32_t e = __shfl_sync(0xffffffffu, mine, k);
+                const int2 x = __ldcg(V.X + (int64_t)(e >> 1) * Ddn + dd);
+                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+            }
+        } else {
+            for (int32_t k = kb; k < ke; ++k) {
+                const uint32_t e = V.uent[k];
+                const int2 x = __ldcg(V.X + (int64_t)(e >> 1) * Ddn + dd);
+                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+            }
+        }
+        for (int32_t k = V.drp[dd]; k < V.drp[dd + 1]; ++k) {
+            const uint32_t e = V.dent[k];
+            const int2 x = buf != nullptr ? xr[e >> 1] : __ldcg(xr + (e >> 1));
+            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+        }
+        if (act) {
+            const int64_t j = u * Ddn + d;
+            const long long Sx = ((long long)hi << 24) + (long long)lo;
+            const double fj = __ldcg(V.f + j);
+            const double q = fma(-beta, __ldcg(V.g + j), fma(V.U * (double)__popc(su_u & V.dst[d]), fj, V.scale * (double)Sx));
+            V.g[j] = q;
+            ap = fma(q, fj, ap);
+            qq = fma(q, q, qq);
+            ff = fma(fj, fj, ff);
+        }
+    }
+    __syncwarp();
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Grid-synchronous sweep over the larger sectors (Algorithm 1 for all of them
+// in lock step).  Every phase spreads the rows of all active sectors over all
+// warps of the launch, so the load balances whatever the mix of sizes:
+//   E  q = H f - beta g for every row (row_pass); per-row partials of
+//      <q,f>, <q,q>, <f,f>;
+//   R  one CTA per sector: a_j, b_{j+1} from the partials (the explicit
+//      |q - a f| pass near breakdown), the Ritz test, the stop decision;
+//   U  f_{j+1} = (q - a f) / b_{j+1} and its fixed-point copy.
+// Phases are separated by bounded grid barriers; per-row partials are summed
+// in row order, so a sector's result does not depend on the rest of the batch.
+// Vector data written in one phase and read in another goes through L2
+// (__ldcg): the near-breakdown pass of phase R rewrites rows that other SMs
+// read next.
+__device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double* red, int* flag, int* sh_flags,
+                                         double* sh_k, int* sh_stop, double* sh_out) {
+    unsigned ggen = 0;
+    auto gsync = [&]() -> bool {
+        ++ggen;
+        return team_barrier(P.gbar, (int)gridDim.x, ggen, P.spin_limit, P.err, flag);
+    };
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw_all = (int64_t)gridDim.x * nwarps;
+    const int64_t nrows = P.rowoff[P.nswp];
+    auto locate = [&](int64_t r) -> int {          // k with rowoff[k] <= r < rowoff[k + 1]
+        int lo = 0, hi = P.nswp - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.rowoff[mid] <= r) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
+    if (blockIdx.x == 0 && threadIdx.x == 0) *P.nactive = P.nswp;
+    // |v0|^2 by rows, then per sector
+    for (int64_t r = gw; r < nrows; r += nw_all) {
+        const int k = locate(r);
+        const SectorDesc S = P.sec[P.swp[k]];
+        const double* v0 = P.v0 + S.voff + (r - P.rowoff[k]) * S.Ddn;
+        double nn = 0.0;
+        for (int64_t d = lane; d < S.Ddn; d += 32) nn = fma(v0[d], v0[d], nn);
+        nn = warp_sum(nn);
+        if (lane == 0) P.rowpart[3 * r] = nn;
+    }
+    if (!gsync()) return false;
+    for (int k = blockIdx.x; k < P.nswp; k += gridDim.x) {
+        const SectorDesc S = P.sec[P.swp[k]];
+        double nn = 0.0;
+        for (int64_t u = threadIdx.x; u < S.Dup; u += blockDim.x) nn += __ldcg(P.rowpart + 3 * (P.rowoff[k] + u));
+        nn = block_reduce(nn, red);
+        if (threadIdx.x == 0) {
+            SweepState st{};
+            st.ib = 1.0 / sqrt(nn);
+            st.amax = 1.0;
+            st.prev = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no previous Ritz value
+            st.active = 1;
+            P.sst[k] = st;
+        }
+    }
+    if (!gsync()) return false;
+    // f_1 = v0 / |v0|, f_0 = 0 and the fixed-point copy of f_1
+    for (int64_t r = gw; r < nrows; r += nw_all) {
+        const int k = locate(r);
+        const SectorDesc S = P.sec[P.swp[k]];
+        const double ib = __ldcg(&P.sst[k].ib);
+        const int64_t j0 = S.voff + (r - P.rowoff[k]) * S.Ddn;
+        for (int64_t d = lane; d < S.Ddn; d += 32) {
+            const double x = P.v0[j0 + d] * ib;
+            P.f[j0 + d] = x;
+            P.g[j0 + d] = 0.0;
+            P.xg[j0 + d] = fixed47(x);
+        }
+    }
+    if (!gsync()) return false;
+    int nact = P.nswp;
+    for (int it = 0; it < P.max_iters && nact > 0; ++it) {
+        double* fp = (it & 1) ? P.g : P.f;          // f_j and f_{j-1} swap pools each step
+        double* gp = (it & 1) ? P.f : P.g;
+        // E
+        for (int64_t r = gw; r < nrows; r += nw_all) {
+            const int k = locate(r);
+            if (!__ldcg(&P.sst[k].active)) continue;
+            const SectorDesc S = P.sec[P.swp[k]];
+            const SecView V{P.xg + S.voff, fp + S.voff, gp + S.voff, P.rp + S.up_rp, P.rp + S.dn_rp,
+                            P.ent + S.up_ent, P.ent + S.dn_ent, P.st + S.up_st, P.st + S.dn_st, S.Ddn, S.U,
+                            -S.t * 0x1p-47};
+            // warps of one CTA work on rows of different sectors: each owns a
+            // fixed slice of the shared buffer, long rows read from L2 instead
+            const int64_t slice = P.smem_elems / nwarps;
+            int2* buf = S.Ddn <= slice ? xs + (int64_t)warp * slice : nullptr;
+            double ap = 0.0, qq = 0.0, ff = 0.0;
+            row_pass(V, r - P.rowoff[k], buf, __ldcg(&P.sst[k].beta), ap, qq, ff);
+            ap = warp_sum(ap);
+            qq = warp_sum(qq);
+            ff = warp_sum(ff);
+            if (lane == 0) {
+                P.rowpart[3 * r] = ap;
+                P.rowpart[3 * r + 1] = qq;
+                P.rowpart[3 * r + 2] = ff;
+            }
+        }
+        if (!gsync()) return false;
+        // R
+        for (int k = blockIdx.x; k < P.nswp; k += gridDim.x) {
+            SweepState st = P.sst[k];
+            if (!st.active) continue;
+            const int sid = P.swp[k];
+            const SectorDesc S = P.sec[sid];
+            double sv[3] = {0.0, 0.0, 0.0};
+            for (int64_t u = threadIdx.x; u < S.Dup; u += blockDim.x)
+                for (int q = 0; q < 3; ++q) sv[q] += __ldcg(P.rowpart + 3 * (P.rowoff[k] + u) + q);
+            for (int q = 0; q < 3; ++q) sv[q] = block_reduce(sv[q], red);
+            const double alpha = sv[0];
+            double b2 = sv[1] - 2.0 * alpha * alpha + alpha * alpha * sv[2];
+            const bool fused = b2 > 1e-6 * sv[1];
+            if (!fused) {                               // near breakdown: form q - a f explicitly
+                double bp = 0.0;
+                for (int64_t j = S.voff + threadIdx.x; j < S.voff + S.D; j += blockDim.x) {
+                    const double x = fma(-alpha, __ldcg(fp + j), __ldcg(gp + j));
+                    gp[j] = x;
+                    bp = fma(x, x, bp);
+                }
+                b2 = block_reduce(bp, red);
+            }
+            const double bn = sqrt(fmax(b2, 0.0));
+            double* A = P.ab + S.ab;
+            double* B = A + P.max_iters;
+            if (threadIdx.x == 0) {
+                A[it] = alpha;
+                B[it] = bn;
+            }
+            const int m = it + 1;
+            const int mcap = (int)((int64_t)P.max_iters < S.D ? (int64_t)P.max_iters : S.D);
+            st.amax = fmax(st.amax, fmax(fabs(alpha), bn));
+            st.broke = bn <= 1e-13 * st.amax;
+            if (st.broke || (m >= 8 && (m % (m >= 32 ? 2 * kCheckEvery : kCheckEvery)) == 0) || m == mcap) {
+                __syncthreads();                         // A, B written by thread 0
+                const double th = cta_lowest_eig(A, B, m, st.prev, sh_flags, sh_k);
+                if (threadIdx.x == 0) {
+                    const double rho = bn * d_last_component(A, B, m, th);
+                    const int conv = st.broke || (rho < P.tol * fmax(1.0, fabs(th)));
+                    *sh_stop = conv || m == mcap;
+                    sh_out[0] = th;
+                    sh_out[1] = rho;
+                    if (*sh_stop) {
+                        lanczos_result res;
+                        res.energy = th;
+                        res.residual = rho;
+                        res.iters = m;
+                        res.breakdown = st.broke;
+                        res.status = conv ? HUB_OK : HUB_ENOTCONV;
+                        res.reserved = 0;
+                        P.res[sid] = res;
+                    }
+                }
+                __syncthreads();
+                st.prev = sh_out[0];
+                if (*sh_stop) st.active = 0;
+            }
+            if (threadIdx.x == 0) {
+                st.alpha = alpha;
+                st.beta = bn;
+                st.ib = 1.0 / bn;
+                st.fused = fused;
+                st.m = m;
+                P.sst[k] = st;
+                if (!st.active) atomicSub(P.nactive, 1);
+            }
+            __syncthreads();
+        }
+        if (!gsync()) return false;
+        // U
+        for (int64_t r = gw; r < nrows; r += nw_all) {
+            const int k = locate(r);
+            if (!__ldcg(&P.sst[k].active)) continue;
+            const SectorDesc S = P.sec[P.swp[k]];
+            const double alpha = __ldcg(&P.sst[k].alpha), ib = __ldcg(&P.sst[k].ib);
+            const int fused = __ldcg(&P.sst[k].fused);
+            const int64_t j0 = S.voff + (r - P.rowoff[k]) * S.Ddn;
+            for (int64_t d = lane; d < S.Ddn; d += 32) {
+                const int64_t j = j0 + d;
+                const double x = (fused ? fma(-alpha, __ldcg(fp + j), __ldcg(gp + j)) : __ldcg(gp + j)) * ib;
+                gp[j] = x;
+                P.xg[j] = fixed47(x);
+            }
+        }
+        if (!gsync()) return false;
+        nact = __ldcg(P.nactive);
+    }
+    return true;
+}
+
 __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams P) {
     extern __shared__ __align__(16) int2 xs[];
     __shared__ double red[kBatchThreads / 32];
@@ -229,6 +507,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     __shared__ double sh_prev;
     __shared__ int sh_flags[kBatchThreads];
     __shared__ double sh_k[1];
+    __shared__ double sh_out[2];
+    // the larger sectors first, in lock step over the whole grid; then each CTA
+    // walks its own list of smaller sectors
+    if (P.nswp > 0 && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out)) return;
     for (int ti = P.cta_ptr[blockIdx.x]; ti < P.cta_ptr[blockIdx.x + 1]; ++ti) {
         const Task task = P.tasks[ti];
         const SectorDesc S = P.sec[task.sector];
@@ -335,49 +617,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                     element(u, d, lo, hi);
                 }
             } else {
-                // global copy (L2): a warp per row; the row is staged in shared
-                // memory for the down-hops, up-hops read whole neighbour rows
-                // with lanes over columns (coalesced, warp-uniform hop list held
-                // in the lanes); column loops are warp-uniform
-                int2* buf = xs + (int64_t)warp * Ddn;
-                for (int64_t u = r0 + warp; u < r1; u += nwarps) {
-                    const int2* xr = X + u * Ddn;
-                    if (rowbuf) {
-                        for (int64_t d = lane; d < Ddn; d += 32) buf[d] = __ldcg(xr + d);
-                        __syncwarp();
-                        xr = buf;
-                    }
-                    const int32_t kb = urp[u], ke = urp[u + 1];
-                    const int nh = ke - kb;
-                    const uint32_t mine = lane < nh ? uent[kb + lane] : 0u;
-                    for (int64_t d0 = 0; d0 < Ddn; d0 += 32) {
-                        const int64_t d = d0 + lane;
-                        const bool act = d < Ddn;
-                        const int64_t dd = act ? d : Ddn - 1;
-                        int lo = 0, hi = 0;
-                        if (nh <= 32) {
-#pragma unroll 4
-                            for (int k = 0; k < nh; ++k) {
-                                const uint32_t e = __shfl_sync(0xffffffffu, mine, k);
-                                const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + dd);
-                                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
-                            }
-                        } else {
-                            for (int32_t k = kb; k < ke; ++k) {
-                                const uint32_t e = uent[k];
-                                const int2 x = __ldcg(X + (int64_t)(e >> 1) * Ddn + dd);
-                                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
-                            }
-                        }
-                        for (int32_t k = drp[dd]; k < drp[dd + 1]; ++k) {
-                            const uint32_t e = dent[k];
-                            const int2 x = rowbuf ? xr[e >> 1] : __ldcg(xr + (e >> 1));
-                            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
-                        }
-                        if (act) element(u, d, lo, hi);
-                    }
-                    __syncwarp();
-                }
+                // global copy (L2): a warp per row (row_pass)
+                const SecView V{X, f, g, urp, drp, uent, dent, ust, dst, Ddn, S.U, scale};
+                int2* buf = rowbuf ? xs + (int64_t)warp * Ddn : nullptr;
+                for (int64_t u = r0 + warp; u < r1; u += nwarps) row_pass(V, u, buf, beta, ap, qq, ff);
             }
             double sv[3] = {ap, qq, ff};
             if (!team_sum(3, sv)) return;
@@ -475,6 +718,11 @@ struct hubbard_batch {
     int smem_elems = 0;
     int sched_max_iters = -1;
     int64_t sched_elems = -1;
+    // grid-synchronous sweep: sectors above the threshold
+    int nswp = 0;
+    int* d_swp = nullptr;
+    int64_t* d_rowoff = nullptr;
+    int64_t rows_all = 0;                      // sum of D_up over all sectors (workspace bound)
 };
 
 namespace hub {
@@ -510,16 +758,24 @@ void batch_free(hubbard_batch* B) {
     cudaFree(B->d_st);
     cudaFree(B->d_cta_ptr);
     cudaFree(B->d_tasks);
+    cudaFree(B->d_swp);
+    cudaFree(B->d_rowoff);
 }
 
 int batch_grid(hubbard_batch* B, int* smem_elems) {
     int dev = 0;
     cudaGetDevice(&dev);
-    int sms = 0, optin = 0;
+    int sms = 0, optin = 0, per_sm_bytes = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    // two CTAs per SM, each with ~100 KB of fixed-point staging
-    const int smem = std::min(optin, 100 * 1024);
+    cudaDeviceGetAttribute(&per_sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_batch_lanczos) != cudaSuccess) return -1;
+    // two CTAs per SM, each with half of the SM's shared memory (less the
+    // per-CTA reservation and the kernel's static buffers) for fixed-point staging
+    int smem = per_sm_bytes / 2 - 1024 - (int)fa.sharedSizeBytes;
+    smem = std::min(smem, optin - (int)fa.sharedSizeBytes) / 16 * 16;
+    if (smem < 16 * 1024) return -1;
     *smem_elems = smem / (int)sizeof(int2);
     cudaError_t e = cudaFuncSetAttribute(k_batch_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return -1;
@@ -536,27 +792,43 @@ int batch_grid(hubbard_batch* B, int* smem_elems) {
 // which is one global order for all CTAs.
 int batch_schedule(hubbard_batch* B) {
     const int G = B->grid;
-    std::vector<int> order(B->n);
-    std::iota(order.begin(), order.end(), 0);
+    // sectors above the threshold: the grid-synchronous sweep (rows in order)
+    std::vector<int> swp;
+    std::vector<int64_t> rowoff(1, 0);
+    std::vector<int> order;
+    for (int s = 0; s < B->n; ++s) {
+        B->sec[s].team = 1;
+        if (B->sec[s].D > B->elems_per_cta) {
+            swp.push_back(s);
+            rowoff.push_back(rowoff.back() + B->sec[s].Dup);
+        } else {
+            order.push_back(s);
+        }
+    }
+    // the rest: one CTA per sector, largest work first to the CTA free first
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
     std::vector<double> avail((size_t)G, 0.0);
     std::vector<std::vector<Task>> lists((size_t)G);
     for (int s : order) {
-        int team = (int)std::min<int64_t>({(B->sec[s].D + B->elems_per_cta - 1) / B->elems_per_cta, (int64_t)kMaxTeam,
-                                           (int64_t)G});
-        team = std::max(team, 1);
-        B->sec[s].team = team;
-        std::vector<int> idx((size_t)G);
-        std::iota(idx.begin(), idx.end(), 0);
-        std::partial_sort(idx.begin(), idx.begin() + team, idx.end(),
-                          [&](int a, int b) { return avail[a] < avail[b] || (avail[a] == avail[b] && a < b); });
-        double start = 0.0;
-        for (int r = 0; r < team; ++r) start = std::max(start, avail[idx[r]]);
-        const double dur = B->cost[s] / team;
-        for (int r = 0; r < team; ++r) {
-            lists[idx[r]].push_back(Task{s, r});
-            avail[idx[r]] = start + dur;
-        }
+        int c = 0;
+        for (int i = 1; i < G; ++i)
+            if (avail[(size_t)i] < avail[(size_t)c]) c = i;
+        lists[(size_t)c].push_back(Task{s, 0});
+        avail[(size_t)c] += B->cost[s];
+    }
+    cudaFree(B->d_swp);
+    cudaFree(B->d_rowoff);
+    B->d_swp = nullptr;
+    B->d_rowoff = nullptr;
+    B->nswp = (int)swp.size();
+    {
+        cudaError_t e = cudaMalloc((void**)&B->d_swp, std::max<size_t>(swp.size(), 1) * sizeof(int));
+        if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_rowoff, rowoff.size() * sizeof(int64_t));
+        if (e == cudaSuccess && !swp.empty())
+            e = cudaMemcpy(B->d_swp, swp.data(), swp.size() * sizeof(int), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(B->d_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "batch sweep list upload");
     }
     std::vector<int> ptr((size_t)G + 1, 0);
     std::vector<Task> flat;
@@ -584,7 +856,7 @@ int batch_schedule(hubbard_batch* B) {
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct WsLayout {
-    size_t f, g, xg, ab, tri, partial, bar, res, err, total;
+    size_t f, g, xg, ab, tri, partial, bar, res, err, rowpart, sst, gbar, total;
 };
 
 WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
@@ -600,6 +872,9 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     L.bar = o; o += al256(n * 4);
     L.res = o; o += al256(n * sizeof(lanczos_result));
     L.err = o; o += 256;
+    L.rowpart = o; o += al256((size_t)B->rows_all * 3 * 8);
+    L.sst = o; o += al256(n * sizeof(SweepState));
+    L.gbar = o; o += 256;                  // grid barrier counter, then the active-sector count
     L.total = o;
     return L;
 }
@@ -683,6 +958,7 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
             s.team = 1;
             B->sec.push_back(s);
             B->cost.push_back((double)s.D * (cu.hops + cd.hops + 8.0));
+            B->rows_all += s.Dup;
             B->total += (s.D + 1) / 2 * 2;           // keep every sector 16-byte aligned
             B->voff[(size_t)i + 1] = B->total;
         }
@@ -758,6 +1034,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     // barrier counters and the error word start at zero
     HUB_CUDA(cudaMemsetAsync(ws + L.bar, 0, (size_t)B->n * 4, s));
     HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
+    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 4, s));
     BatchParams P;
     P.sec = B->d_sec;
     P.cta_ptr = B->d_cta_ptr;
@@ -779,6 +1056,13 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     P.tol = tol > 0.0 ? tol : 1e-10;
     P.smem_elems = B->smem_elems;
     P.spin_limit = 20000000;            // ~2.5 s of 128 ns sleeps per barrier
+    P.nswp = B->nswp;
+    P.swp = B->d_swp;
+    P.rowoff = B->d_rowoff;
+    P.rowpart = (double*)(ws + L.rowpart);
+    P.sst = (SweepState*)(ws + L.sst);
+    P.gbar = (unsigned int*)(ws + L.gbar);
+    P.nactive = (int*)(ws + L.gbar + 4);
     void* args[] = {&P};
     const size_t smem = (size_t)B->smem_elems * sizeof(int2);
     HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(B->grid), dim3(kBatchThreads), args, smem, s));
