@@ -274,11 +274,12 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
  * sector, entirely on the device; the paper notes that small sectors leave
  * the GPU idle, Sec. 5).  A batch owns the hopping tables of all its sectors
  * (tables are shared between sectors with the same lattice and filling).
- * Every sector's solve is run by a team of CTAs of one cooperative kernel;
- * sectors up to ~12800 elements per CTA keep their fixed-point Lanczos vector
- * in shared memory.  Team size = ceil(D / elems_per_cta) (the schedule knob
- * that hubbard_batch_autotune chooses).  Results do not depend on which other
- * sectors share the batch (fixed-order reductions).
+ * One cooperative kernel solves the batch: sectors above elems_per_cta
+ * elements (the schedule knob hubbard_batch_autotune chooses) advance in lock
+ * step, every Lanczos step spread over the whole grid; the others are solved
+ * by one CTA each, in shared memory when the vector fits (~14000 elements).
+ * Results do not depend on which other sectors share the batch (fixed-order
+ * reductions).
  * ------------------------------------------------------------------------- */
 typedef struct hubbard_batch* hubbard_batch_t;
 
@@ -300,7 +301,8 @@ int hubbard_batch_vector_offsets(hubbard_batch_t B, int64_t* offsets);
 /* Device workspace bytes for hubbard_batch_solve_async with this max_iters. */
 size_t hubbard_batch_workspace_bytes(hubbard_batch_t B, int max_iters);
 
-/* Elements per CTA of a sector's team (>= 1). */
+/* Size threshold (>= 1): sectors of more than elems_per_cta elements are
+ * solved by the whole grid in lock step, the others by one CTA each. */
 int hubbard_batch_set_schedule(hubbard_batch_t B, int64_t elems_per_cta);
 
 /* One launch solving every sector to rho < tol * max(1, |theta|) (or
@@ -313,7 +315,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
                               size_t ws_bytes, void* stream);
 
 /* Copies the per-sector results (host array of n_sectors); synchronises
- * `stream`.  HUB_ETIMEOUT if a team barrier gave up. */
+ * `stream`.  HUB_ETIMEOUT if a grid barrier gave up. */
 int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
                           lanczos_result* results);
 

@@ -1,16 +1,17 @@
-// Many small sectors solved in one persistent launch (Sec. 2.2, Algorithm 1,
+// Many sectors solved in one persistent launch (Sec. 2.2, Algorithm 1,
 // run entirely on the device for each sector).
 //
 // The paper measured that sectors below ~10 sites leave a GPU idle (Sec. 5:
-// 16 % occupancy at 8 sites).  Here every CTA of one cooperative launch walks
-// a static list of tasks; a task is one sector's whole ground-state solve, run
-// by a team of 1..kMaxTeam CTAs that split the sector's elements.  A solo
-// team keeps the fixed-point copy of its Lanczos vector in shared memory; a
-// larger team keeps it in global memory (L2-resident) and meets at team
-// barriers (bounded waits; a timeout sets an error word and ends the task).
-// Tasks are ordered globally and every CTA takes its own tasks in that order,
-// so team waits cannot form a cycle.  Reductions are summed in a fixed order
-// (block tree, then the team's partials in rank order): the result of a
+// 16 % occupancy at 8 sites).  Here one cooperative launch solves a whole
+// batch in two parts:
+//  * sectors above a size threshold advance in lock step, one Lanczos step per
+//    grid-synchronous sweep whose phases spread the rows of every active
+//    sector over all warps (sweep_solve);
+//  * the rest are tasks of one CTA each, walked from a static per-CTA list
+//    (largest work first); a task that fits keeps the fixed-point copy of its
+//    Lanczos vector in shared memory.
+// Grid barriers are bounded (a timeout sets an error word; later waits fail
+// fast).  Every reduction is summed in a fixed order, so the result of a
 // sector does not depend on which other sectors share the launch.
 #include <algorithm>
 #include <cmath>
@@ -27,7 +28,6 @@ namespace hub {
 namespace {
 
 constexpr int kBatchThreads = 480;   // 15 warps: two CTAs per SM leave each warp a 945-element row slice
-constexpr int kMaxTeam = 32;
 constexpr int kCheckEvery = 4;        // Ritz-value test every few steps
 
 struct SectorDesc {
@@ -38,30 +38,20 @@ struct SectorDesc {
     int64_t up_st, dn_st;
     int64_t ab;            // offset of its a/b history (2 * max_iters doubles)
     double t, U;
-    int team;
-    int pad;
-};
-
-struct Task {
-    int sector;
-    int rank;
 };
 
 struct BatchParams {
     const SectorDesc* sec;
     const int* cta_ptr;    // [gridDim.x + 1]
-    const Task* tasks;
+    const int* tasks;      // sector ids, CTA c's in tasks[cta_ptr[c] .. cta_ptr[c+1])
     const int32_t* rp;     // pooled row pointers
     const uint32_t* ent;   // pooled packed hop entries (target << 1) | neg
     const uint32_t* st;    // pooled basis words
     const double* v0;      // caller start vectors (concatenated)
     double* f;             // Lanczos vector pools (workspace)
     double* g;
-    int2* xg;              // global fixed-point copies (team tasks)
+    int2* xg;              // global fixed-point copies (sectors not staged in shared memory)
     double* ab;            // a/b histories
-    double* tri;           // tridiagonal scratch, 4 * max_iters per CTA
-    double* partial;       // [sector][2][3][kMaxTeam]
-    unsigned int* bar;     // team barrier counters [sector]
     lanczos_result* res;   // [sector]
     int* err;              // batch error word
     int max_iters;
@@ -109,13 +99,13 @@ __device__ __forceinline__ double block_reduce(double v, double* red) {
     return s;
 }
 
-// team barrier number `gen` (1, 2, ...): returns false on timeout
-__device__ bool team_barrier(unsigned int* ctr, int team, unsigned gen, long long limit, int* err, int* flag) {
+// barrier number `gen` (1, 2, ...) among `nctas` CTAs: returns false on timeout
+__device__ bool grid_barrier(unsigned int* ctr, int nctas, unsigned gen, long long limit, int* err, int* flag) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(ctr, 1u);
-        const unsigned target = (unsigned)team * gen;
+        const unsigned target = (unsigned)nctas * gen;
         long long it = 0;
         int ok = 1;
         while (true) {
@@ -326,7 +316,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
     unsigned ggen = 0;
     auto gsync = [&]() -> bool {
         ++ggen;
-        return team_barrier(P.gbar, (int)gridDim.x, ggen, P.spin_limit, P.err, flag);
+        return grid_barrier(P.gbar, (int)gridDim.x, ggen, P.spin_limit, P.err, flag);
     };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw_all = (int64_t)gridDim.x * nwarps;
@@ -512,18 +502,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     // walks its own list of smaller sectors
     if (P.nswp > 0 && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out)) return;
     for (int ti = P.cta_ptr[blockIdx.x]; ti < P.cta_ptr[blockIdx.x + 1]; ++ti) {
-        const Task task = P.tasks[ti];
-        const SectorDesc S = P.sec[task.sector];
-        const int team = S.team, rank = task.rank;
+        const int sid = P.tasks[ti];
+        const SectorDesc S = P.sec[sid];
         const int64_t D = S.D, Ddn = S.Ddn, Dup = S.Dup;
-        // the team splits the rows of V (row-major D_up x D_dn)
-        const int64_t rchunk = (Dup + team - 1) / team;
-        const int64_t r0 = ((int64_t)rank * rchunk < Dup) ? (int64_t)rank * rchunk : Dup;
-        const int64_t r1 = (r0 + rchunk < Dup) ? r0 + rchunk : Dup;
-        const int64_t j0 = r0 * Ddn, j1 = r1 * Ddn;
-        const bool in_smem = (team == 1) && (D <= P.smem_elems);
+        const int64_t j0 = 0, j1 = D;
+        const bool in_smem = D <= P.smem_elems;
         // per-warp row buffer for the global-memory path (rows of the fixed-point copy)
-        const int nwarps = blockDim.x >> 5, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
         const bool rowbuf = !in_smem && Ddn * nwarps <= P.smem_elems;
         int2* X = in_smem ? xs : (P.xg + S.voff);
         double* f = P.f + S.voff;
@@ -537,38 +522,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         const uint32_t* dst = P.st + S.dn_st;
         double* A = P.ab + S.ab;
         double* B = A + P.max_iters;
-        double* part = P.partial + (int64_t)task.sector * 2 * 3 * kMaxTeam;
-        unsigned* ctr = P.bar + task.sector;
-        unsigned gen = 0;
-        // deterministic team sums of nv <= 3 values (in place): block tree, then
-        // the team's partials in rank order
-        auto team_sum = [&](int nv, double* v) -> bool {
+        // block sums of nv <= 3 values (in place), in a fixed order
+        auto cta_sum = [&](int nv, double* v) {
             for (int q = 0; q < nv; ++q) v[q] = block_reduce(v[q], red);
-            if (team == 1) return true;
-            ++gen;
-            double* pg = part + (int64_t)(gen & 1) * 3 * kMaxTeam;
-            if (threadIdx.x == 0)
-                for (int q = 0; q < nv; ++q) pg[q * kMaxTeam + rank] = v[q];
-            if (!team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag)) return false;
-            for (int q = 0; q < nv; ++q) {
-                double t = 0.0;
-                for (int r = 0; r < team; ++r) t += __ldcg(pg + q * kMaxTeam + r);
-                v[q] = t;
-            }
-            return true;
-        };
-        auto sync_team = [&]() -> bool {
-            if (team == 1) {
-                __syncthreads();
-                return true;
-            }
-            ++gen;
-            return team_barrier(ctr, team, gen, P.spin_limit, P.err, &flag);
         };
         // f_1 = v0 / |v0|, f_0 = 0, and the fixed-point copy of f_1 (|f| <= 1)
         double nn[1] = {0.0};
         for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) nn[0] = fma(v0[j], v0[j], nn[0]);
-        if (!team_sum(1, nn)) return;
+        cta_sum(1, nn);
         const double inv0 = 1.0 / sqrt(nn[0]);
         for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
             const double x = v0[j] * inv0;
@@ -576,7 +537,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             g[j] = 0.0;
             X[j] = fixed47(x);
         }
-        if (!sync_team()) return;
+        __syncthreads();
         const double scale = -S.t * 0x1p-47;           // -t times the fixed-point unit
         const int mcap = (int)((int64_t)P.max_iters < D ? (int64_t)P.max_iters : D);
         double beta = 0.0, theta = 0.0, rho = 0.0;
@@ -620,10 +581,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                 // global copy (L2): a warp per row (row_pass)
                 const SecView V{X, f, g, urp, drp, uent, dent, ust, dst, Ddn, S.U, scale};
                 int2* buf = rowbuf ? xs + (int64_t)warp * Ddn : nullptr;
-                for (int64_t u = r0 + warp; u < r1; u += nwarps) row_pass(V, u, buf, beta, ap, qq, ff);
+                for (int64_t u = warp; u < Dup; u += nwarps) row_pass(V, u, buf, beta, ap, qq, ff);
             }
             double sv[3] = {ap, qq, ff};
-            if (!team_sum(3, sv)) return;
+            cta_sum(3, sv);
             const double alpha = sv[0];
             // |q - alpha f|^2 = <q,q> - 2 alpha <q,f> + alpha^2 <f,f>, unless that
             // cancels more than six digits (near breakdown): then form it
@@ -636,7 +597,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                     g[j] = r;
                     bp[0] = fma(r, r, bp[0]);
                 }
-                if (!team_sum(1, bp)) return;
+                cta_sum(1, bp);
                 b2 = bp[0];
             }
             const double bn = sqrt(fmax(b2, 0.0));
@@ -647,7 +608,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             m = it + 1;
             amax = fmax(amax, fmax(fabs(alpha), bn));
             if (bn <= 1e-13 * amax) broke = 1;
-            // Ritz test (thread 0; every CTA of the team reaches the same decision)
+            // Ritz test
             if (broke || (m >= 8 && (m % (m >= 32 ? 2 * kCheckEvery : kCheckEvery)) == 0) || m == mcap) {
                 __syncthreads();                             // A, B written by thread 0
                 const double th = cta_lowest_eig(A, B, m, sh_prev, sh_flags, sh_k);
@@ -674,13 +635,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                 g[j] = x;
                 X[j] = fixed47(x);
             }
-            if (!sync_team()) return;
+            __syncthreads();
             double* tmp = f;
             f = g;
             g = tmp;
             beta = bn;
         }
-        if (rank == 0 && threadIdx.x == 0) {
+        if (threadIdx.x == 0) {
             lanczos_result r;
             r.energy = theta;
             r.residual = rho;
@@ -688,7 +649,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             r.breakdown = broke;
             r.status = conv ? HUB_OK : HUB_ENOTCONV;
             r.reserved = 0;
-            P.res[task.sector] = r;
+            P.res[sid] = r;
         }
         __syncthreads();
     }
@@ -712,7 +673,7 @@ struct hubbard_batch {
     // schedule
     int64_t elems_per_cta = 1 << 14;
     int* d_cta_ptr = nullptr;
-    hub::Task* d_tasks = nullptr;
+    int* d_tasks = nullptr;
     size_t tasks_cap = 0;
     int grid = 0;
     int smem_elems = 0;
@@ -786,10 +747,9 @@ int batch_grid(hubbard_batch* B, int* smem_elems) {
     return smem;
 }
 
-// LPT static schedule: largest work first; a sector of D elements gets a team
-// of ceil(D / elems_per_cta) CTAs (<= kMaxTeam, <= grid); each task goes to
-// the team members that become free first.  Lists stay in assignment order,
-// which is one global order for all CTAs.
+// Sectors above elems_per_cta elements go to the sweep (in batch order, rows
+// in order); the rest are one-CTA tasks, largest work first to the CTA whose
+// list is shortest (LPT).  Lists stay in assignment order.
 int batch_schedule(hubbard_batch* B) {
     const int G = B->grid;
     // sectors above the threshold: the grid-synchronous sweep (rows in order)
@@ -797,7 +757,6 @@ int batch_schedule(hubbard_batch* B) {
     std::vector<int64_t> rowoff(1, 0);
     std::vector<int> order;
     for (int s = 0; s < B->n; ++s) {
-        B->sec[s].team = 1;
         if (B->sec[s].D > B->elems_per_cta) {
             swp.push_back(s);
             rowoff.push_back(rowoff.back() + B->sec[s].Dup);
@@ -808,12 +767,12 @@ int batch_schedule(hubbard_batch* B) {
     // the rest: one CTA per sector, largest work first to the CTA free first
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
     std::vector<double> avail((size_t)G, 0.0);
-    std::vector<std::vector<Task>> lists((size_t)G);
+    std::vector<std::vector<int>> lists((size_t)G);
     for (int s : order) {
         int c = 0;
         for (int i = 1; i < G; ++i)
             if (avail[(size_t)i] < avail[(size_t)c]) c = i;
-        lists[(size_t)c].push_back(Task{s, 0});
+        lists[(size_t)c].push_back(s);
         avail[(size_t)c] += B->cost[s];
     }
     cudaFree(B->d_swp);
@@ -831,7 +790,7 @@ int batch_schedule(hubbard_batch* B) {
         if (e != cudaSuccess) return cuda_fail(e, "batch sweep list upload");
     }
     std::vector<int> ptr((size_t)G + 1, 0);
-    std::vector<Task> flat;
+    std::vector<int> flat;
     for (int c = 0; c < G; ++c) {
         ptr[(size_t)c + 1] = ptr[(size_t)c] + (int)lists[c].size();
         flat.insert(flat.end(), lists[c].begin(), lists[c].end());
@@ -841,12 +800,11 @@ int batch_schedule(hubbard_batch* B) {
     B->d_cta_ptr = nullptr;
     B->d_tasks = nullptr;
     cudaError_t e = cudaMalloc((void**)&B->d_cta_ptr, ptr.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(flat.size(), 1) * sizeof(Task));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(flat.size(), 1) * sizeof(int));
     if (e == cudaSuccess) e = cudaMemcpy(B->d_cta_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !flat.empty())
-        e = cudaMemcpy(B->d_tasks, flat.data(), flat.size() * sizeof(Task), cudaMemcpyHostToDevice);
+        e = cudaMemcpy(B->d_tasks, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch schedule upload");
-    // the team sizes live in the sector descriptors
     e = cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
     B->sched_elems = B->elems_per_cta;
@@ -856,7 +814,7 @@ int batch_schedule(hubbard_batch* B) {
 inline size_t al256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct WsLayout {
-    size_t f, g, xg, ab, tri, partial, bar, res, err, rowpart, sst, gbar, total;
+    size_t f, g, xg, ab, res, err, rowpart, sst, gbar, total;
 };
 
 WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
@@ -867,9 +825,6 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     L.g = o; o += al256(T * 8);
     L.xg = o; o += al256(T * 8);
     L.ab = o; o += al256(n * 2 * (size_t)max_iters * 8);
-    L.tri = o; o += al256((size_t)B->grid * 4 * (size_t)max_iters * 8);
-    L.partial = o; o += al256(n * 2 * 3 * kMaxTeam * 8);
-    L.bar = o; o += al256(n * 4);
     L.res = o; o += al256(n * sizeof(lanczos_result));
     L.err = o; o += 256;
     L.rowpart = o; o += al256((size_t)B->rows_all * 3 * 8);
@@ -955,7 +910,6 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
             s.dn_st = cd.st_off;
             s.t = d.t;
             s.U = d.U;
-            s.team = 1;
             B->sec.push_back(s);
             B->cost.push_back((double)s.D * (cu.hops + cd.hops + 8.0));
             B->rows_all += s.Dup;
@@ -1016,7 +970,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     const WsLayout L = batch_layout(B, max_iters);
     if (ws_bytes < L.total) return fail(HUB_ENOMEM, "batch workspace too small");
     int rc;
-    // descriptors: a/b history offsets depend on max_iters, team sizes on the schedule
+    // descriptors: a/b history offsets depend on max_iters
     // (both uploaded synchronously: fix them before capturing this call in a graph)
     bool dirty = false;
     if (B->sched_max_iters != max_iters) {
@@ -1031,8 +985,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     if (dirty) HUB_CUDA(cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice));
     cudaStream_t s = (cudaStream_t)stream;
     char* ws = (char*)workspace;
-    // barrier counters and the error word start at zero
-    HUB_CUDA(cudaMemsetAsync(ws + L.bar, 0, (size_t)B->n * 4, s));
+    // the barrier counter and the error word start at zero
     HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
     HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 4, s));
     BatchParams P;
@@ -1047,9 +1000,6 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     P.g = (double*)(ws + L.g);
     P.xg = (int2*)(ws + L.xg);
     P.ab = (double*)(ws + L.ab);
-    P.tri = (double*)(ws + L.tri);
-    P.partial = (double*)(ws + L.partial);
-    P.bar = (unsigned int*)(ws + L.bar);
     P.res = (lanczos_result*)(ws + L.res);
     P.err = (int*)(ws + L.err);
     P.max_iters = max_iters;
@@ -1081,7 +1031,7 @@ int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iter
                              cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaMemcpyAsync(&err, (const char*)workspace + L.err, 4, cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaStreamSynchronize(s));
-    if (err != 0) return fail(err, "batch: a team barrier timed out");
+    if (err != 0) return fail(err, "batch: a grid barrier timed out");
     return HUB_OK;
 }
 

@@ -96,16 +96,24 @@ def test_batch_alone_equals_in_mix_and_single_path(dev):
         assert abs(r1["energy"] - mix[i]["energy"]) <= 1e-9 * max(1.0, abs(r1["energy"]))
 
 
-def test_batch_team_path(dev):
-    """Small elements-per-CTA forces multi-CTA teams (global fixed-point copy, team barriers)."""
+def test_batch_sweep_and_task_paths_agree(dev):
+    """The same sectors solved all in the grid-synchronous sweep (threshold 512),
+    all as one-CTA tasks (threshold above every D: shared-memory and global
+    fixed-point copies), and in the default split agree to 1e-9; a sweep
+    sector's result is bit-identical alone and among others."""
     reqs = _small_reqs(24, 11, 200000)
     specs = _specs(reqs)
     seeds = [r["seed"] for r in reqs]
-    _, _, _, solo = _solve(specs, seeds)
-    _, _, _, team = _solve(specs, seeds, elems=512)
-    for a, b in zip(solo, team):
-        assert b["status"] == hub.HUB_OK
+    _, _, _, tasks = _solve(specs, seeds, elems=1 << 30)
+    _, _, _, swept = _solve(specs, seeds, elems=512)
+    _, _, _, split = _solve(specs, seeds)
+    for a, b, c in zip(tasks, swept, split):
+        assert a["status"] == hub.HUB_OK and b["status"] == hub.HUB_OK and c["status"] == hub.HUB_OK
         assert abs(a["energy"] - b["energy"]) <= 1e-9 * max(1.0, abs(a["energy"]))
+        assert abs(a["energy"] - c["energy"]) <= 1e-9 * max(1.0, abs(a["energy"]))
+    for i in (0, 5, 23):
+        _, _, _, alone = _solve([specs[i]], [seeds[i]], elems=512)
+        assert alone[0]["energy"] == swept[i]["energy"] and alone[0]["iters"] == swept[i]["iters"]
 
 
 def test_batch_autotune_and_graph_replay(dev):
