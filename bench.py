@@ -304,7 +304,9 @@ def bench_refined(hub, torch, dev, bonds, golden, n):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         H = hub.hubbard_sector_create(16, bonds, 8, 8, 1.0, 8.0)
-        r = hub.lanczos_ground_state_refined(H, v0, 1000, 1e-10)
+        # room for 128 binary32 Lanczos vectors (85 GB): the Ritz vector needs no replay
+        r = hub.lanczos_ground_state_refined(H, v0, 1000, 1e-10, store_vectors=128)
+        replayed = r["replayed"]
         H.close()
         torch.cuda.synchronize()
         if k == 0:
@@ -315,7 +317,8 @@ def bench_refined(hub, torch, dev, bonds, golden, n):
     ok = [e <= 1e-9 for e in errs]
     return dict(solves=n, solves_per_s=sum(ok) / sum(lat), p50_ms=1e3 * float(np.percentile(lat, 50)),
                 p99_ms=1e3 * float(np.percentile(lat, 99)), iters_f32_f64=iters, max_rel_err=max(errs),
-                all_within_1e9=all(ok), path="binary32 Lanczos + replayed Ritz vector + binary64 Rayleigh/polish")
+                all_within_1e9=all(ok), ritz_vector="replayed" if replayed else "from stored binary32 vectors",
+                path="binary32 Lanczos + Ritz vector + binary64 Rayleigh/polish")
 
 
 def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10):
@@ -358,7 +361,7 @@ def bench_serve(n):
     from paper_1204_3425_gb300.serve import Request, SolveServer
     from workload import serve_requests
     reqs = [Request(k, s, s["arrival_s"]) for k, s in enumerate(serve_requests(n, rate=500.0, seed=1234))]
-    srv = SolveServer(200e9, n_slots=6, small_max_dim=200_000)
+    srv = SolveServer(200e9)
     st = srv.run_trace(reqs, timeout=3600)
     srv.stop()
     st["converged"] = sum(1 for r in reqs if r.result and r.result["status"] == 0)

@@ -270,19 +270,23 @@ def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None,
 class RefinedResult(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("error_bound", ctypes.c_double),
                 ("energy_f32", ctypes.c_double), ("gap", ctypes.c_double), ("iters_f32", ctypes.c_int32),
-                ("iters_f64", ctypes.c_int32), ("status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("iters_f64", ctypes.c_int32), ("status", ctypes.c_int32), ("replayed", ctypes.c_int32)]
 
 
-def lanczos_refined_workspace_bytes(H):
-    return int(load_library().lanczos_refined_workspace_bytes(H.handle))
+def lanczos_refined_workspace_bytes(H, store_vectors=0):
+    """Minimum workspace, plus room for store_vectors binary32 Lanczos vectors
+    (stored vectors let the solver skip the replay for the Ritz vector)."""
+    slot = (H.D * 4 + 255) // 256 * 256
+    return int(load_library().lanczos_refined_workspace_bytes(H.handle)) + int(store_vectors) * slot
 
 
 def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=None, psi_out=None, stream=None,
-                                 raise_on_notconv=False):
-    """binary32 Lanczos + binary64 refinement; v0 binary64.  Returns a dict of the result fields."""
+                                 raise_on_notconv=False, store_vectors=0):
+    """binary32 Lanczos + binary64 refinement; v0 binary64.  Returns a dict of the result fields.
+    Without a workspace, one is allocated with room for store_vectors stored vectors."""
     import torch
     lib = load_library()
-    need = lanczos_refined_workspace_bytes(H)
+    need = lanczos_refined_workspace_bytes(H, store_vectors)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=v0.device)
     res = RefinedResult()
@@ -292,7 +296,7 @@ def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=Non
                                           ctypes.byref(res))
     if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
         _check(rc)
-    return {f: getattr(res, f) for f, _ in RefinedResult._fields_ if f != "reserved"}
+    return {f: getattr(res, f) for f, _ in RefinedResult._fields_}
 
 
 class SectorDesc(ctypes.Structure):

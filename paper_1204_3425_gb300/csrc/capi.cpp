@@ -652,8 +652,11 @@ struct LanczosRun {
     bool broke = false, converged = false;
 };
 
+// store (optional): f_j is also copied to store + j * store_stride bytes for
+// j < store_cap (the Ritz vector is then one pass over the stored vectors).
 static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype, void* f,
-                        void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0) {
+                        void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0, char* store = nullptr,
+                        size_t store_stride = 0, int store_cap = 0) {
     int rc;
     double n0 = 0.0;
     if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
@@ -662,6 +665,9 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
     if (v0_dtype == dtype) rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / n0, s);
     else rc = launch_f64_to_f32_scaled((const double*)v0, (float*)f, H->D, 1.0 / n0, s);
     if (rc) return rc;
+    const size_t vbytes = (size_t)H->D * elem_size(dtype);
+    if (store_cap > 0 && cudaMemcpyAsync(store, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(HUB_ECUDA, "store f_0");
     if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
     const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
     double bj = 0.0;
@@ -689,6 +695,9 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
         if (pending) rc = launch_axpy_scale(-aj, 1.0 / bn, f, g, H->D, dtype, s);
         else rc = launch_scale(1.0 / bn, g, H->D, dtype, s);
         if (rc) return rc;
+        if (j + 1 < store_cap &&
+            cudaMemcpyAsync(store + (size_t)(j + 1) * store_stride, g, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(HUB_ECUDA, "store f_j");
         std::swap(f, g);
         bj = bn;
     }
@@ -777,10 +786,16 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
     float* f = (float*)((char*)w + align_up(D * 8, 256));
     float* g = (float*)((char*)f + align_up(D * 4, 256));
     ScratchGuard guard(H, scr, D * 16);
+    // workspace beyond the minimum stores the binary32 Lanczos vectors
+    const size_t base_bytes = lanczos_refined_workspace_bytes(H);
+    const size_t slot = align_up(D * 4, 256);
+    const int store_cap = (int)std::min<size_t>((ws_bytes - base_bytes) / slot, (size_t)kRedSlots);
+    char* store = ws + base_bytes;
 
     // 1. binary32 Lanczos: stop when the Ritz estimate reaches binary32 level
     LanczosRun R;
-    if ((rc = lanczos_core(H, v0, HUB_F64, max_iters, 0.0, HUB_F32, f, g, s, R, 2e-6))) return rc;
+    if ((rc = lanczos_core(H, v0, HUB_F64, max_iters, 0.0, HUB_F32, f, g, s, R, 2e-6, store, slot, store_cap)))
+        return rc;
     const int m = (int)R.a.size();
     std::vector<double> sv((size_t)m);
     double theta32 = 0.0;
@@ -798,24 +813,33 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
     out->iters_f32 = m;
     out->gap = gap;
 
-    // 2. Ritz vector: replay the same binary32 recurrence with the stored a, b
-    //    (every kernel is deterministic, so the f_j are bit-identical) and
-    //    accumulate psi = sum_j s_j f_j in binary64
-    double n0 = 0.0;
-    if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
-    if ((rc = launch_f64_to_f32_scaled((const double*)v0, f, H->D, 1.0 / std::sqrt(n0), s))) return rc;
-    if (cudaMemsetAsync(g, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
-    if ((rc = launch_psi_accumulate(f, psi, H->D, sv[0], true, s))) return rc;
-    {
-        float* ff = f;
-        float* gg = g;
-        for (int j = 0; j + 1 < m; ++j) {
-            const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
-            if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
-            if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
-            std::swap(ff, gg);
-            if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
+    // 2. Ritz vector psi = sum_j s_j f_j in binary64: one pass over the stored
+    //    f_j when they all fit in the workspace, else a replay of the same
+    //    binary32 recurrence with the stored a, b (every kernel is
+    //    deterministic, so the f_j are bit-identical; so is psi either way)
+    if (m <= store_cap) {
+        if (cudaMemcpyAsync(H->red, sv.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return fail(HUB_ECUDA, "upload s");
+        if ((rc = launch_psi_multi((const float*)store, (int64_t)(slot / 4), m, H->red, psi, H->D, s))) return rc;
+        out->replayed = 0;
+    } else {
+        double n0 = 0.0;
+        if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+        if ((rc = launch_f64_to_f32_scaled((const double*)v0, f, H->D, 1.0 / std::sqrt(n0), s))) return rc;
+        if (cudaMemsetAsync(g, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+        if ((rc = launch_psi_accumulate(f, psi, H->D, sv[0], true, s))) return rc;
+        {
+            float* ff = f;
+            float* gg = g;
+            for (int j = 0; j + 1 < m; ++j) {
+                const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
+                if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
+                if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
+                std::swap(ff, gg);
+                if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
+            }
         }
+        out->replayed = 1;
     }
     double pn = 0.0;
     if ((rc = launch_dot(H, psi, psi, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pn))) return rc;

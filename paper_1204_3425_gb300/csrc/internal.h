@@ -132,6 +132,10 @@ int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double i
 int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cudaStream_t s);
 int launch_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype, cudaStream_t s);
 int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s);
+// psi = sum_{j<m} s_j f_j, f_j = base + j * stride (binary32), s on the device;
+// bit-identical to m successive launch_psi_accumulate calls
+int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_dev, double* psi, int64_t n,
+                     cudaStream_t s);
 
 // tridiag.cpp -----------------------------------------------------------------
 // Lowest eigenvalue of the symmetric tridiagonal T (diag a[0..m-1], off-diag

@@ -266,6 +266,18 @@ __global__ void k_psi_acc(const float* __restrict__ f, double* __restrict__ psi,
         psi[i] = init ? s * (double)f[i] : fma(s, (double)f[i], psi[i]);
 }
 
+// psi = sum_j s_j f_j over m stored binary32 vectors f_j = base + j * stride,
+// accumulated per element in j order with the same operations as successive
+// k_psi_acc launches (so the result is bit-identical to that sequence)
+__global__ void k_psi_multi(const float* __restrict__ base, int64_t stride, int m, const double* __restrict__ s,
+                            double* __restrict__ psi, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double acc = s[0] * (double)base[i];
+        for (int j = 1; j < m; ++j) acc = fma(s[j], (double)__ldcs(base + (int64_t)j * stride + i), acc);
+        psi[i] = acc;
+    }
+}
+
 // Seeded uniform [-1, 1) start vector: SplitMix64 (Steele, Lea, Flood 2014)
 // in counter mode, counter = seed * 2^40 + (start + i); the top 53 bits of
 // the output give x in [0, 1), v = 2x - 1 (exact in binary64).
@@ -465,6 +477,15 @@ int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cud
 int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
     k_psi_acc<<<g, kThreads, 0, s>>>(f, psi, n, sj, init ? 1 : 0);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_dev, double* psi, int64_t n,
+                     cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_psi_multi<<<g, kThreads, 0, s>>>(base, stride, m, s_dev, psi, n);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;

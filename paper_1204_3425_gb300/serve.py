@@ -61,10 +61,15 @@ class GPUSolver:
         self.device = torch.device(device)
         hub.load_library()
 
-    # bytes of device memory a request holds while it runs
+    # binary32 Lanczos vectors kept for the Ritz vector (no replay) when they fit in 8 GB
     @staticmethod
-    def large_footprint(D):
-        return 48 * D + (1 << 20)
+    def store_vectors(D):
+        return 128 if 128 * (4 * D + 256) <= 8e9 else 0
+
+    # bytes of device memory a request holds while it runs
+    @classmethod
+    def large_footprint(cls, D):
+        return 48 * D + cls.store_vectors(D) * (4 * D + 256) + (1 << 20)
 
     @staticmethod
     def small_footprint(D):
@@ -77,7 +82,8 @@ class GPUSolver:
             try:
                 v0 = torch.empty(req.D, dtype=torch.float64, device=self.device)
                 hub.hubbard_fill_start_vector(v0, req.seed, stream=stream)
-                ws = torch.empty(hub.lanczos_refined_workspace_bytes(H), dtype=torch.uint8, device=self.device)
+                ws = torch.empty(hub.lanczos_refined_workspace_bytes(H, self.store_vectors(req.D)), dtype=torch.uint8,
+                                 device=self.device)
                 r = hub.lanczos_ground_state_refined(H, v0, self.max_iters, self.tol, workspace=ws, stream=stream)
                 del v0, ws
             finally:
@@ -108,7 +114,10 @@ class GPUSolver:
 
 
 class SolveServer:
-    def __init__(self, hbm_budget, n_slots=4, small_max_dim=200_000, batch_max=1024, solver=None):
+    # Defaults measured on the 500 req/s trace: a cooperative micro-batch needs
+    # the whole GPU, so batching only sectors that stay in one CTA's shared
+    # memory (<= 20000 elements) interferes least with the refined slots.
+    def __init__(self, hbm_budget, n_slots=12, small_max_dim=20_000, batch_max=1024, solver=None):
         self.solver = solver if solver is not None else GPUSolver()
         self.budget = int(hbm_budget)
         self.free = int(hbm_budget)
@@ -194,7 +203,8 @@ class SolveServer:
                     p50_ms=1e3 * q(0.50), p99_ms=1e3 * q(0.99), max_ms=1e3 * lat[-1],
                     max_backlog=self.max_backlog, peak_bytes=self.peak_in_use, budget_bytes=self.budget,
                     n_batches=len(self.batches), mean_batch=(sum(self.batches) / len(self.batches)) if self.batches else 0,
-                    large=sum(1 for r in requests if r.path == "refined"))
+                    large=sum(1 for r in requests if r.path == "refined"), slots=self.n_slots,
+                    small_max_dim=self.small_max_dim)
 
     # ---- internals --------------------------------------------------------------
     def _take(self, nbytes):
