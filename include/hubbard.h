@@ -322,6 +322,15 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
 int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
                           lanczos_result* results);
 
+/* Failure-path self-test (the paper has no counterpart): launches two CTAs
+ * on the batch kernel's bounded grid barrier set to expect three, so the wait
+ * cannot complete; each CTA gives up after 2000 polls (well under a
+ * millisecond) and sets the error word.  Returns HUB_ETIMEOUT when the bound
+ * and the error path work (the expected result), HUB_EDEVICE if the timeout
+ * was not reported, HUB_ECUDA on a CUDA error.  Allocates 256 bytes of device
+ * memory for the call; synchronises `stream`. */
+int hubbard_selftest_wait_timeout(void* stream);
+
 /* Times full solves for elems_per_cta in {2^12 .. 2^17} and keeps the fastest
  * (written to *chosen).  Synchronises `stream`. */
 int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,

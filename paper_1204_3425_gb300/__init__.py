@@ -62,6 +62,7 @@ SIGNATURES = {
     "hubbard_batch_solve_async": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P]),
     "hubbard_batch_results": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "hubbard_batch_autotune": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P]),
+    "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
     "hubbard_last_error": (ctypes.c_char_p, []),
 }
@@ -297,6 +298,12 @@ def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=Non
     if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
         _check(rc)
     return {f: getattr(res, f) for f, _ in RefinedResult._fields_}
+
+
+def hubbard_selftest_wait_timeout(stream=None):
+    """Runs the bounded-wait self-test; returns the status code (HUB_ETIMEOUT expected)."""
+    rc = load_library().hubbard_selftest_wait_timeout(_stream(stream))
+    return rc, load_library().hubbard_last_error().decode()
 
 
 class SectorDesc(ctypes.Structure):

@@ -655,6 +655,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     }
 }
 
+// A bounded grid barrier that cannot complete (it expects one CTA more than
+// launched): every CTA gives up after `limit` polls and sets the error word.
+__global__ void k_wait_probe(unsigned int* ctr, long long limit, int* err) {
+    __shared__ int flag;
+    grid_barrier(ctr, (int)gridDim.x + 1, 1, limit, err, &flag);
+}
+
 }  // namespace
 }  // namespace hub
 
@@ -1033,6 +1040,26 @@ int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iter
     HUB_CUDA(cudaStreamSynchronize(s));
     if (err != 0) return fail(err, "batch: a grid barrier timed out");
     return HUB_OK;
+}
+
+int hubbard_selftest_wait_timeout(void* stream) {
+    clear_error();
+    cudaStream_t s = (cudaStream_t)stream;
+    char* buf = nullptr;
+    HUB_CUDA(cudaMalloc((void**)&buf, 256));
+    int err = 0;
+    cudaError_t e = cudaMemsetAsync(buf, 0, 256, s);
+    if (e == cudaSuccess) {
+        k_wait_probe<<<2, 64, 0, s>>>((unsigned int*)buf, 2000, (int*)(buf + 128));
+        count_launches(1);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, buf + 128, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(e, "wait probe");
+    if (err == HUB_ETIMEOUT) return fail(HUB_ETIMEOUT, "bounded wait gave up as intended");
+    return fail(HUB_EDEVICE, "bounded wait did not report its timeout");
 }
 
 int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,

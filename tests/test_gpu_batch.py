@@ -152,3 +152,14 @@ def test_batch_full_config(dev):
         H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
         r1 = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(H.D, seed=reqs[i]["seed"])).to(dev), MAXIT, TOL)
         assert abs(r1["energy"] - res[i]["energy"]) <= 1e-9 * max(1.0, abs(r1["energy"]))
+
+
+def test_bounded_wait_times_out_and_context_survives(dev):
+    """The batch kernel's grid barrier, made to wait for a CTA that does not
+    exist, gives up and reports HUB_ETIMEOUT; the device stays usable."""
+    rc, msg = hub.hubbard_selftest_wait_timeout()
+    assert rc == hub.HUB_ETIMEOUT, (rc, msg)
+    reqs = _small_reqs(8, 3, 60000)
+    specs = _specs(reqs)
+    _, _, _, res = _solve(specs, [r["seed"] for r in reqs])
+    assert all(r["status"] == hub.HUB_OK for r in res)
