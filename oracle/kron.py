@@ -42,12 +42,19 @@ def _load():
         lib.kron_dot.argtypes = [ctypes.c_int64, P, P]
         lib.kron_dot.restype = ctypes.c_double
         lib.kron_axpy.argtypes = [ctypes.c_int64, ctypes.c_double, P, P]
+        lib.kron_set_threads.argtypes = [ctypes.c_int]
+        lib.kron_set_threads.restype = ctypes.c_int
         _lib = lib
     return _lib
 
 
 def _p(a):
     return ctypes.c_void_p(a.ctypes.data)
+
+
+def set_threads(n):
+    """OpenMP threads of the C kernels (n > 0); returns the previous maximum."""
+    return int(_load().kron_set_threads(int(n)))
 
 
 class KronHamiltonian:

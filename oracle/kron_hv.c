@@ -14,6 +14,7 @@
  * Plain loops, parallelised over subvectors with OpenMP; double throughout.
  */
 #include <stdint.h>
+#include <omp.h>
 
 static int popcount32(uint32_t w) {
     int n = 0;
@@ -68,4 +69,12 @@ void kron_axpy(int64_t n, double a, const double* x, double* y)
 {
     #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) y[i] += a * x[i];
+}
+
+/* OpenMP threads for the calls above (n > 0); returns the previous maximum. */
+int kron_set_threads(int n)
+{
+    const int prev = omp_get_max_threads();
+    if (n > 0) omp_set_num_threads(n);
+    return prev;
 }
