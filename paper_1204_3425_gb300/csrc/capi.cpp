@@ -234,13 +234,18 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
             lt.emplace_back(T.tgt.begin() + T.rowptr[(size_t)r], T.tgt.begin() + T.rowptr[(size_t)r + 1]);
         colours[(size_t)g] = colour_group(lt, eb);
         boff[(size_t)g] = btotal;
-        bcnt[(size_t)g] = (colours[(size_t)g].slots + 7) / 8;
-        btotal += (int64_t)bcnt[(size_t)g] * 32 * 8;
+        bcnt[(size_t)g] = (colours[(size_t)g].slots + 3) / 4;      // half-blocks of 4 slots
+        btotal += (int64_t)bcnt[(size_t)g] * 32 * 4;
     }
     std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), (uint32_t)Dr);
     for (int64_t g = 0; g < groups; ++g) {
         const SlotColouring& C = colours[(size_t)g];
-        const int nslot = bcnt[(size_t)g] * 8;
+        const int nslot = bcnt[(size_t)g] * 4;
+        const int nfull = bcnt[(size_t)g] / 2;                        // blocks of 8 slots, then maybe one of 4
+        auto pos = [&](int l, int s) -> int64_t {
+            if (s < nfull * 8) return boff[(size_t)g] + ((int64_t)(s / 8) * 32 + l) * 8 + s % 8;
+            return boff[(size_t)g] + (int64_t)nfull * 32 * 8 + (int64_t)l * 4 + (s - nfull * 8);
+        };
         // entry[lane][slot], -1 = padding
         std::vector<std::vector<int64_t>> grid(32, std::vector<int64_t>((size_t)nslot, -1));
         for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) {
@@ -262,7 +267,7 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
                     const int64_t k = grid[(size_t)l][(size_t)s];
                     const uint32_t e = k >= 0 ? ((uint32_t)T.tgt[(size_t)k] | (T.sign[(size_t)k] < 0 ? negbit : 0u))
                                               : (uint32_t)(Dr + freeg);
-                    bent[(size_t)(boff[(size_t)g] + ((int64_t)(s / 8) * 32 + l) * 8 + s % 8)] = e;
+                    bent[(size_t)pos(l, s)] = e;
                 }
             }
         }

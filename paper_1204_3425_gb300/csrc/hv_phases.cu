@@ -141,16 +141,18 @@ __device__ __forceinline__ float comp(float2 x, int i) { return i == 0 ? x.x : x
 __device__ __forceinline__ float comp(float4 x, int i) { return i == 0 ? x.x : (i == 1 ? x.y : (i == 2 ? x.z : x.w)); }
 
 // ---------------------------------------------------------------------------
-// Hop sums of one lane over its group's slots (warp-sliced table, blocks of 8
-// slots per lane).  All blocks of a chunk are loaded with 16-byte loads before
-// any gather, so one table-load latency is paid per chunk rather than per hop.
-// add(e) receives each packed entry (target << 2) | code; padding entries are 0
-// (target 0, weight 0).
+// Hop sums of one lane over its group's slots (warp-sliced table): nhalf
+// half-blocks of 4 slots per lane, stored as nhalf / 2 blocks of 8 slots
+// ((b * 32 + lane) * 8 entries in) and, when nhalf is odd, one trailing
+// block of 4 (at nblk * 256 + lane * 4).  Blocks are read with 16-byte loads,
+// all blocks of a chunk before any gather, so one table-load latency is paid
+// per chunk rather than per hop.  add(e) receives each entry.
 template <typename EntT, typename F>
-__device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int nblk, int lane, F&& add) {
+__device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int nhalf, int lane, F&& add) {
     constexpr int LOADS = (int)sizeof(EntT);          // 16-byte loads per 8-slot block: 2 (u16) -> 1, 4 (u32) -> 2
     constexpr int NL = LOADS == 2 ? 1 : 2;
     constexpr int CH = NL == 1 ? 4 : 2;               // blocks per chunk
+    const int nblk = nhalf >> 1;
     const uint4* p = reinterpret_cast<const uint4*>(base) + (int64_t)lane * NL;
     for (int b0 = 0; b0 < nblk; b0 += CH) {
         uint4 buf[CH][NL];
@@ -175,6 +177,22 @@ __device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int 
                     }
                 }
             }
+        }
+    }
+    if (nhalf & 1) {
+        const EntT* h = base + (int64_t)nblk * 256;
+        if constexpr (NL == 1) {
+            const uint2 q = __ldg(reinterpret_cast<const uint2*>(h) + lane);
+            add(q.x & 0xFFFFu);
+            add(q.x >> 16);
+            add(q.y & 0xFFFFu);
+            add(q.y >> 16);
+        } else {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(h) + lane);
+            add(q.x);
+            add(q.y);
+            add(q.z);
+            add(q.w);
         }
     }
 }

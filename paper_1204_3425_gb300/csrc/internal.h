@@ -50,10 +50,12 @@ struct DevSpin {
     uint32_t* sell_ent = nullptr;    // [sum cnt * 32]
     int64_t sell_entries = 0;
     // the row-phase table in blocks of 8 slots per lane ("SELL-32/8"): group g
-    // has blk_cnt[g] blocks at blk_off[g] (in entries); block b of lane l holds
-    // slots 8b .. 8b+7 at blk_off[g] + (b*32 + l)*8.  Entry = staged slot index
-    // with the top bit set for sign -1; 16-bit (ent16) when the index fits 15
-    // bits, else 32-bit (ent32).  Indices >= D point at zero slots (padding).
+    // starts at blk_off[g] (in entries) and has blk_cnt[g] half-blocks of 4
+    // slots: blk_cnt[g] / 2 blocks of 8 (block b of lane l holds slots
+    // 8b .. 8b+7 at blk_off[g] + (b*32 + l)*8), then, when blk_cnt[g] is odd,
+    // one block of 4 (lane l's at blk_off[g] + nfull*256 + l*4).  Entry = staged
+    // slot index with the top bit set for sign -1; 16-bit (ent16) when the index
+    // fits 15 bits, else 32-bit (ent32).  Indices >= D point at zero slots.
     int64_t* blk_off = nullptr;      // [groups]
     int32_t* blk_cnt = nullptr;      // [groups]
     uint16_t* ent16 = nullptr;
