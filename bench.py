@@ -186,6 +186,7 @@ def run_ours(args):
     torch.cuda.synchronize()
 
     # ---- H*v steps (inputs resident) -------------------------------------
+    schedule = hub.hubbard_autotune_schedule(H, v, w)      # fastest (vec_rows, vec_cols, ctas_rows, -)
     for _ in range(args.warmup):
         hub.hubbard_apply(H, v, w)
     torch.cuda.synchronize()
@@ -279,7 +280,8 @@ def run_ours(args):
         "arith": ("exact int32-pair fixed-point hop sums, binary64 storage and rounding" if dts == "f64"
                   else "binary32"),
         "data": "synthetic (seeded SplitMix64 start vector)",
-        "config": dict(cfg, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single"),
+        "config": dict(cfg, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single",
+                       schedule=dict(zip(("vec_rows", "vec_cols", "ctas_rows", "ctas_cols"), schedule))),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": TRAFFIC.get(args.workload), "peak_source": src,
                      "algorithmic_bytes_per_launch": nbytes,
@@ -345,20 +347,28 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10):
     t0 = time.perf_counter()
     chosen = B.autotune(v0, 40, tol, ws)            # short solves (40 steps) rank the schedules
     tune_s = time.perf_counter() - t0
-    B.solve_async(v0, max_iters, tol, ws)
-    torch.cuda.synchronize()
-    ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-    ev[0].record()
-    B.solve_async(v0, max_iters, tol, ws)
-    ev[1].record()
-    torch.cuda.synchronize()
+    # the solve (two memsets + one cooperative launch) captured once as a CUDA graph, then replayed
+    stream = torch.cuda.Stream(device=dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(stream):
+        B.solve_async(v0, max_iters, tol, ws, stream=stream)      # fixes the descriptors before capture
+        stream.synchronize()
+        with torch.cuda.graph(graph, stream=stream):
+            B.solve_async(v0, max_iters, tol, ws, stream=stream)
+        graph.replay()                                           # warm replay
+        stream.synchronize()
+        ev = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        ev[0].record(stream)
+        graph.replay()
+        ev[1].record(stream)
+        stream.synchronize()
     ms = ev[0].elapsed_time(ev[1])
-    res = B.results(ws, max_iters)
+    res = B.results(ws, max_iters, stream=stream)
     B.close()
     ok = sum(1 for r in res if r["status"] == 0)
     return dict(sectors=count, ms=ms, solves_per_s=ok / (ms * 1e-3), converged=ok, elems_per_cta=chosen,
                 autotune_s=tune_s, create_s=create_s, iters_total=sum(r["iters"] for r in res),
-                launches_per_batch=1, tol="rho < 1e-10 max(1,|theta|)")
+                launches_per_batch=1, timed="CUDA graph replay", tol="rho < 1e-10 max(1,|theta|)")
 
 
 def bench_serve(n):

@@ -139,6 +139,14 @@ int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void
  * fixed order (binary32) or exactly (binary64 fixed point). */
 int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols);
 
+/* Autotuner for the schedule above: times three hubbard_apply calls (after a
+ * warm one) for every vec_rows x vec_cols in {1, 2 (, 4 for binary32)} and
+ * ctas_rows in {1, 2} on the caller's v, w (device, dtype, as hubbard_apply;
+ * w is overwritten), keeps the fastest on the handle and writes it to
+ * chosen[4] = {vec_rows, vec_cols, ctas_rows, ctas_cols} (nullable).
+ * Synchronises `stream`.  On error the previous schedule is kept. */
+int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, void* stream, int* chosen);
+
 /* ---------------------------------------------------------------------------
  * Binary64 w = H v that allocates no device memory.
  *

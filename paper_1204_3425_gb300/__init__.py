@@ -63,6 +63,7 @@ SIGNATURES = {
     "hubbard_batch_results": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "hubbard_batch_autotune": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
+    "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
     "hubbard_last_error": (ctypes.c_char_p, []),
 }
@@ -188,6 +189,13 @@ def hubbard_apply(H, v, w, stream=None):
 def hubbard_apply_reference(H, v, w, stream=None):
     _check(load_library().hubbard_apply_reference(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
     return w
+
+
+def hubbard_autotune_schedule(H, v, w, stream=None):
+    """Times the H*v schedules on (v, w) and keeps the fastest; returns it as a tuple."""
+    out = (ctypes.c_int * 4)()
+    _check(load_library().hubbard_autotune_schedule(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream), out))
+    return tuple(out)
 
 
 def hubbard_set_schedule(H, vec_rows=0, vec_cols=0, ctas_rows=0, ctas_cols=0):

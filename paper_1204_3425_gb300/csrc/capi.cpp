@@ -504,6 +504,63 @@ int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows,
     return HUB_OK;
 }
 
+int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, void* stream, int* chosen) {
+    clear_error();
+    int rc = check_apply(H, v, w, dtype);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int vmax = dtype == HUB_F64 ? 2 : 4;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return fail(HUB_ECUDA, "autotune events");
+    }
+    const int saved[4] = {H->vec_rows, H->vec_cols, H->ctas_rows, H->ctas_cols};
+    float best = -1.0f;
+    int pick[4] = {0, 0, 0, 0};
+    for (int vr = 1; vr <= vmax && rc == HUB_OK; vr *= 2)
+        for (int vc = 1; vc <= vmax && rc == HUB_OK; vc *= 2)
+            for (int cr = 1; cr <= 2 && rc == HUB_OK; ++cr) {
+                H->vec_rows = vr;
+                H->vec_cols = vc;
+                H->ctas_rows = cr;
+                H->ctas_cols = 0;
+                if ((rc = hubbard_apply(H, v, w, dtype, stream))) break;    // warm (allocates scratch)
+                cudaEventRecord(e0, s);
+                for (int k = 0; k < 3 && rc == HUB_OK; ++k) rc = hubbard_apply(H, v, w, dtype, stream);
+                cudaEventRecord(e1, s);
+                if (rc) break;
+                if (cudaEventSynchronize(e1) != cudaSuccess) {
+                    rc = fail(HUB_ECUDA, "autotune timing");
+                    break;
+                }
+                float ms = 0.0f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (best < 0.0f || ms < best) {
+                    best = ms;
+                    pick[0] = vr;
+                    pick[1] = vc;
+                    pick[2] = cr;
+                    pick[3] = 0;
+                }
+            }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        H->vec_rows = saved[0];
+        H->vec_cols = saved[1];
+        H->ctas_rows = saved[2];
+        H->ctas_cols = saved[3];
+        return rc;
+    }
+    H->vec_rows = pick[0];
+    H->vec_cols = pick[1];
+    H->ctas_rows = pick[2];
+    H->ctas_cols = pick[3];
+    if (chosen != nullptr) std::memcpy(chosen, pick, sizeof(pick));
+    return HUB_OK;
+}
+
 int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream) {
     clear_error();
     int rc = check_apply(H, v, w, dtype);
