@@ -669,11 +669,13 @@ __device__ __forceinline__ void addf(float4& A, float4 a, float4 b, float4 c, fl
 __device__ __forceinline__ void addf(float4& A, float4 a) { A.x += a.x; A.y += a.y; A.z += a.z; A.w += a.w; }
 
 // Up phase, binary32: same decomposition, float arithmetic
-template <int VPL>
-constexpr int up32_ctas() { return VPL == 4 ? 4 : 5; }
+// CTAs per SM of the binary32 up phase: 5 at <= 51 registers, 4 where 4
+// columns per lane or the Lanczos variant's prefetched operands need more
+template <int VPL, bool RED = false>
+constexpr int up32_ctas() { return (RED || VPL == 4) ? 4 : 5; }
 
 template <int VPL, bool RED>
-__global__ void __launch_bounds__(256, up32_ctas<VPL>()) k_up_f32(const float* __restrict__ v, const float* __restrict__ Y, float* w,
+__global__ void __launch_bounds__(256, up32_ctas<VPL, RED>()) k_up_f32(const float* __restrict__ v, const float* __restrict__ Y, float* w,
                                                     const float* w_old, int64_t Dup, int64_t Ddn,
                                                     const int32_t* __restrict__ ptr,
                                                     const int32_t* __restrict__ npos,
@@ -705,21 +707,27 @@ __global__ void __launch_bounds__(256, up32_ctas<VPL>()) k_up_f32(const float* _
         const int64_t uend = min(rb * kUpRows + kUpRows, Dup);
         for (int64_t u = rb * kUpRows + warp; u < uend; u += nw) {
             const int32_t kb = ptr[u];
+            const int64_t J = u * Ddn + c;
+            V xpre{}, ypre{}, wpre{};
+            if constexpr (RED) {                      // Lanczos step: epilogue operands before the gathers
+                xpre = __ldg(reinterpret_cast<const V*>(v + J));
+                ypre = __ldcs(reinterpret_cast<const V*>(Y + J));
+                if (w_old != nullptr) wpre = __ldcs(reinterpret_cast<const V*>(w_old + J));
+            }
             V P{}, N{};
             uniform_hops<V>(list, kb, ptr[u + 1] - kb, npos[u], lane, P, N,
                 [&](uint32_t t) { return __ldg(reinterpret_cast<const V*>(base + (int64_t)t * Ddn)); },
                 [](V& A, auto... xs) { addf(A, xs...); });
             if (act) {
                 const uint32_t su_u = su[u];
-                const int64_t J = u * Ddn + c;
-                const V xo = __ldg(reinterpret_cast<const V*>(v + J));
-                const V yv = __ldcs(reinterpret_cast<const V*>(Y + J));
+                const V xo = RED ? xpre : __ldg(reinterpret_cast<const V*>(v + J));
+                const V yv = RED ? ypre : __ldcs(reinterpret_cast<const V*>(Y + J));
                 float r[VPL];
 #pragma unroll
                 for (int j = 0; j < VPL; ++j) {
                     const float nd = (float)__popc(su_u & sdc[j]);
                     r[j] = fmaf(mt, (comp(P, j) - comp(N, j)) + comp(yv, j), U * nd * comp(xo, j));
-                    if (w_old != nullptr) r[j] = fmaf(mbeta, w_old[J + j], r[j]);
+                    if (w_old != nullptr) r[j] = fmaf(mbeta, RED ? comp(wpre, j) : w_old[J + j], r[j]);
                 }
                 if constexpr (VPL == 4) __stcs(reinterpret_cast<float4*>(w + J), make_float4(r[0], r[1], r[2], r[3]));
                 else if constexpr (VPL == 2) __stcs(reinterpret_cast<float2*>(w + J), make_float2(r[0], r[1]));
@@ -1012,7 +1020,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     int up_grid = 0;
 #define UP32(V)                                                                                            \
     {                                                                                                      \
-        up_grid = sms() * up32_ctas<V>();                                                                  \
+        up_grid = sms() * (part != nullptr ? up32_ctas<V, true>() : up32_ctas<V, false>());               \
         if (part != nullptr)                                                                               \
             k_up_f32<V, true><<<up_grid, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old,  \
                 Dup, Ddn, up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t,           \
