@@ -81,8 +81,9 @@ struct hubbard_sector {
     // fixed-point scratch for the F64 fast path, allocated on first use
     void* fx_scratch = nullptr;
     size_t fx_bytes = 0;
-    // two-phase H*v schedule (0 = automatic): rows / columns per staged block
-    // and CTAs per SM for the row and column phases (hubbard_set_schedule)
+    // two-phase H*v schedule (0 = automatic; hubbard_set_schedule): rows per
+    // row-phase block, up-phase columns per lane, row-phase CTAs per SM
+    // (ctas_cols is accepted and reserved)
     int vec_rows = 0, vec_cols = 0, ctas_rows = 0, ctas_cols = 0;
     int fixed_emax_host = 1023;      // host copy for the device word used by the fixed-scale fallback
     // small device scratch for reductions: partial sums, status words
