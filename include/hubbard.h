@@ -64,8 +64,12 @@ typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
  * (Eq. J-formula) and the per-spin hopping tables of H_up and H_dn
  * (Eq. H-Kroneckersum): for every rank r and every bond with exactly one end
  * occupied, the target rank r' and the Jordan-Wigner sign of Sec. 2.1.  It
- * copies them to the current device and returns an opaque handle that owns
- * them.
+ * copies them to the current device and returns an opaque handle.  The
+ * tables of one spin depend only on (device, Ns, bonds, N): handles with the
+ * same ones share a single read-only device copy (also between the two spins
+ * when Nup = Ndn), and the library keeps the 64 most recently built table
+ * sets after their last handle is gone, so re-creating a sector skips the
+ * build.  Each handle has its own t, U, schedule and scratch.
  *   Ns      number of sites, 1..32
  *   bonds   host array of 2*n_bonds int32: (i0, j0, i1, j1, ...), 0 <= i,j < Ns,
  *           i != j, no unordered pair repeated.  n_bonds may be 0.
@@ -80,7 +84,9 @@ typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
 int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn,
                           double t, double U, hubbard_t* out);
 
-/* Frees the device tables (synchronising the device first).  NULL is a no-op. */
+/* Releases the handle (synchronising the device first): its scratch is freed,
+ * and its tables when no other handle or the recent-table cache holds them.
+ * NULL is a no-op. */
 void hubbard_sector_destroy(hubbard_t H);
 
 /* Dimensions D_up, D_dn and maximum hops per state W_up, W_dn (any may be NULL). */

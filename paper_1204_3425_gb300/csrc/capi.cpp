@@ -4,8 +4,12 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <list>
+#include <map>
+#include <mutex>
 #include <new>
 #include <set>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -60,24 +64,29 @@ int upload(T** dst, const T* src, size_t n) {
     return HUB_OK;
 }
 
+void free_spin_dev(DevSpin& d) {
+    cudaFree(d.states);
+    cudaFree(d.rowptr);
+    cudaFree(d.ent);
+    cudaFree(d.ell);
+    cudaFree(d.cnt);
+    cudaFree(d.sell_off);
+    cudaFree(d.sell_cnt);
+    cudaFree(d.sell_ent);
+    cudaFree(d.blk_off);
+    cudaFree(d.blk_cnt);
+    cudaFree(d.ent16);
+    cudaFree(d.ent32);
+    cudaFree(d.pn_ptr);
+    cudaFree(d.pn_npos);
+    cudaFree(d.pn_list);
+    d = DevSpin{};
+}
+
 void free_dev(hubbard_sector* H) {
-    for (auto& d : H->dev) {
-        cudaFree(d.states);
-        cudaFree(d.rowptr);
-        cudaFree(d.ent);
-        cudaFree(d.ell);
-        cudaFree(d.cnt);
-        cudaFree(d.sell_off);
-        cudaFree(d.sell_cnt);
-        cudaFree(d.sell_ent);
-        cudaFree(d.blk_off);
-        cudaFree(d.blk_cnt);
-        cudaFree(d.ent16);
-        cudaFree(d.ent32);
-        cudaFree(d.pn_ptr);
-        cudaFree(d.pn_npos);
-        cudaFree(d.pn_list);
-        d = DevSpin{};
+    for (int s = 0; s < 2; ++s) {
+        H->dev[s] = DevSpin{};                 // owned by the shared entry
+        H->spin_owner[s].reset();
     }
     cudaFree(H->fx_scratch);
     H->fx_scratch = nullptr;
@@ -326,6 +335,77 @@ bool fixed_point_ok(const hubbard_sector* H) { return H->host[0].W + H->host[1].
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 }  // namespace
+
+struct SpinEntry {
+    SpinTables host;
+    DevSpin dev;
+    int device = 0;
+    ~SpinEntry() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (cur != device) cudaSetDevice(device);
+        free_spin_dev(dev);
+        if (cur >= 0 && cur != device) cudaSetDevice(cur);
+    }
+};
+
+namespace {
+// Process-wide table cache: (device, Ns, bonds, N) -> entry.  Handles share
+// entries; the most recently used kSpinCacheKeep entries stay alive after
+// their last handle is gone, so creating the same sector again (a solve
+// loop, a server) skips the table build, colouring and upload.
+using SpinKey = std::tuple<int, int, std::vector<std::pair<int, int>>, int>;
+constexpr size_t kSpinCacheKeep = 64;
+std::mutex g_spin_mu;
+std::map<SpinKey, std::weak_ptr<SpinEntry>> g_spin_index;
+std::list<std::shared_ptr<SpinEntry>> g_spin_recent;
+
+std::shared_ptr<SpinEntry> spin_lookup(const SpinKey& key) {
+    std::lock_guard<std::mutex> lk(g_spin_mu);
+    auto it = g_spin_index.find(key);
+    if (it == g_spin_index.end()) return nullptr;
+    std::shared_ptr<SpinEntry> e = it->second.lock();
+    if (e == nullptr) g_spin_index.erase(it);
+    return e;
+}
+
+// registers e (or returns the entry another thread registered meanwhile)
+std::shared_ptr<SpinEntry> spin_insert(const SpinKey& key, std::shared_ptr<SpinEntry> e) {
+    std::shared_ptr<SpinEntry> dropped;
+    std::lock_guard<std::mutex> lk(g_spin_mu);
+    auto it = g_spin_index.find(key);
+    if (it != g_spin_index.end()) {
+        std::shared_ptr<SpinEntry> other = it->second.lock();
+        if (other != nullptr) return other;
+    }
+    g_spin_index[key] = e;
+    g_spin_recent.push_front(e);
+    if (g_spin_recent.size() > kSpinCacheKeep) {
+        dropped = std::move(g_spin_recent.back());     // freed after the lock is released
+        g_spin_recent.pop_back();
+    }
+    return e;
+}
+
+int spin_tables(int device, int ns, const std::vector<std::pair<int, int>>& bl, int n,
+                std::shared_ptr<SpinEntry>& out) {
+    const SpinKey key(device, ns, bl, n);
+    out = spin_lookup(key);
+    if (out != nullptr) return HUB_OK;
+    auto e = std::make_shared<SpinEntry>();
+    e->device = device;
+    try {
+        build_spin_tables(ns, n, bl, e->host);
+    } catch (const std::bad_alloc&) {
+        return fail(HUB_ENOMEM, "host allocation (tables)");
+    }
+    const int rc = upload_spin(e->host, e->dev);
+    if (rc != HUB_OK) return rc;
+    out = spin_insert(key, e);
+    return HUB_OK;
+}
+}  // namespace
+
 }  // namespace hub
 
 using namespace hub;
@@ -405,18 +485,21 @@ int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, in
     H->t = t;
     H->U = U;
     H->bonds = bl;
-    try {
-        build_spin_tables(Ns, Nup, bl, H->host[0]);
-        build_spin_tables(Ns, Ndn, bl, H->host[1]);
-    } catch (const std::bad_alloc&) {
-        delete H;
-        return fail(HUB_ENOMEM, "host allocation (tables)");
+    int rc = spin_tables(H->device, Ns, bl, Nup, H->spin_owner[0]);
+    if (rc == HUB_OK) rc = spin_tables(H->device, Ns, bl, Ndn, H->spin_owner[1]);
+    if (rc == HUB_OK) {
+        try {
+            for (int s = 0; s < 2; ++s) {
+                H->host[s] = H->spin_owner[s]->host;
+                H->dev[s] = H->spin_owner[s]->dev;
+            }
+        } catch (const std::bad_alloc&) {
+            rc = fail(HUB_ENOMEM, "host allocation (tables)");
+        }
     }
     H->Dup = H->host[0].D;
     H->Ddn = H->host[1].D;
     H->D = H->Dup * H->Ddn;
-    int rc = upload_spin(H->host[0], H->dev[0]);
-    if (rc == HUB_OK) rc = upload_spin(H->host[1], H->dev[1]);
     if (rc == HUB_OK) {
         cudaError_t e = cudaMalloc((void**)&H->red, kRedSlots * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void**)&H->status, 4 * sizeof(int));

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <cstddef>
+#include <memory>
 #include <string>
 #include <vector>
 #include <cuda_runtime.h>
@@ -70,13 +71,21 @@ struct DevSpin {
 
 }  // namespace hub
 
+namespace hub {
+// Host and device tables of one spin species, shared by every handle with the
+// same device, lattice and particle number (read-only once uploaded; the
+// device arrays are freed with the last owner).
+struct SpinEntry;
+}
+
 struct hubbard_sector {
     int device = 0;
     int ns = 0, nup = 0, ndn = 0;
     double t = 0.0, U = 0.0;
     std::vector<std::pair<int, int>> bonds;
-    hub::SpinTables host[2];
-    hub::DevSpin dev[2];
+    hub::SpinTables host[2];                   // copies of the shared host tables
+    hub::DevSpin dev[2];                       // device pointers owned by spin_owner
+    std::shared_ptr<hub::SpinEntry> spin_owner[2];
     int64_t Dup = 0, Ddn = 0, D = 0;
     // fixed-point scratch for the F64 fast path, allocated on first use
     void* fx_scratch = nullptr;

@@ -277,3 +277,30 @@ def test_schedules_bit_identical_and_autotune(dev, dt):
     assert chosen[0] in (1, 2, 4) and chosen[1] in (1, 2, 4) and chosen[2] in (1, 2)
     hub.hubbard_apply(H, v, w)
     assert torch.equal(w, ref)
+
+
+def test_shared_tables_between_handles(dev):
+    """Handles of the same lattice and fillings share one set of device tables
+    (and N_up = N_dn shares it between the spins); each handle keeps its own
+    t, U and scratch, and destroying one leaves the others intact."""
+    ns, bonds = lattice_by_name("sq3x3")
+    S1 = Sector(ns, bonds, 4, 4, 1.0, 3.0)
+    S2 = Sector(ns, bonds, 4, 4, 0.5, 7.0)
+    H1 = hub.hubbard_sector_create(ns, bonds, 4, 4, 1.0, 3.0)
+    H2 = hub.hubbard_sector_create(ns, bonds, 4, 4, 0.5, 7.0)
+    x = start_vector(S1.D, seed=8)
+    v = torch.from_numpy(x).to(dev)
+    w = torch.empty_like(v)
+    hub.hubbard_apply(H1, v, w)
+    assert np.abs(w.cpu().numpy() - S1.explicit() @ x).max() <= 1e-12 * np.linalg.norm(x)
+    H1.close()
+    hub.hubbard_apply(H2, v, w)
+    assert np.abs(w.cpu().numpy() - S2.explicit() @ x).max() <= 1e-12 * np.linalg.norm(x)
+    H3 = hub.hubbard_sector_create(ns, bonds, 4, 4, 1.0, 3.0)       # tables from the cache
+    hub.hubbard_apply(H3, v, w)
+    assert np.abs(w.cpu().numpy() - S1.explicit() @ x).max() <= 1e-12 * np.linalg.norm(x)
+    for spin in (0, 1):
+        for g, r in zip(hub.hubbard_export_tables(H3, spin), S1.spin_table(spin)):
+            assert np.array_equal(g, r)
+    H2.close()
+    H3.close()
