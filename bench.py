@@ -61,6 +61,7 @@ def workload_config(name):
 # profiles/hv_f64_sq4x4_n6_6_phases_ncu.md (small case scaled by D to the bench
 # sector); must be set back to None whenever the H*v kernels change.
 TRAFFIC = {"sq4x4_n8_8_U8_f64": 9.16e9}
+NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal per GPU (vendor figure)
 
 
 def peaks():
@@ -279,6 +280,10 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": TRAFFIC.get(args.workload), "peak_source": src,
                      "algorithmic_bytes_per_launch": nbytes,
+                     "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
+                     "dram_gbs_from_traffic": (TRAFFIC[args.workload] / (avg_kernel_ms * 1e-3) / 1e9
+                                               if TRAFFIC.get(args.workload) else None),
+                     "amplification": (TRAFFIC[args.workload] / nbytes if TRAFFIC.get(args.workload) else None),
                      "kernel": "hubbard_apply (row phase + up phase kernels)"},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * esize, "d2h_bytes_per_step": D * esize,
                 "ms_per_step": e2e_ms, "pipelined": "3 streams: upload i+1 | H*v i | download i-1"},
