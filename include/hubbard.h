@@ -249,10 +249,10 @@ uint64_t hubbard_kernel_launches(void);
  * run in binary32; the paper benchmarks both precisions, Sec. 5).
  *   1. binary32 Lanczos (H*v and vectors binary32; a_j, b_j reductions
  *      accumulated in float-float, ~48 bits) until rho < 2e-6 max(1,|theta|);
- *   2. Ritz vector psi = sum_j s_j f_j accumulated in binary64: from the
- *      stored f_j when the workspace holds them all, else by replaying the
- *      same binary32 recurrence with the stored a_j, b_j (bit-identical f_j,
- *      so psi is the same either way);
+ *   2. Ritz vector psi = sum_j s_j f_j accumulated in binary64: from the f_j
+ *      stored in the workspace's spare room, and past the last stored one
+ *      by replaying the same binary32 recurrence with the stored a_j, b_j
+ *      (bit-identical f_j, so psi is the same however many were stored);
  *   3. binary64 Rayleigh quotient theta = <psi|H|psi> and residual
  *      |H psi - theta psi| with the binary64 H*v;
  *   4. if residual^2 / gap > tol max(1,|theta|): a short binary64 Lanczos
@@ -260,7 +260,7 @@ uint64_t hubbard_kernel_launches(void);
  *   v0          binary64 device start vector (normalised inside)
  *   workspace   >= lanczos_refined_workspace_bytes(H) bytes (40 D), 256-aligned;
  *               every further 4 D bytes (rounded up to 256) stores one more
- *               binary32 Lanczos vector (the replay is skipped when all fit)
+ *               binary32 Lanczos vector, i.e. saves one replayed step
  *   psi_out     optional binary64 device vector receiving the normalised psi
  *               of step 2
  *   out         energy (binary64 Rayleigh quotient or polished Ritz value),
@@ -278,7 +278,7 @@ typedef struct {
     int32_t iters_f32;
     int32_t iters_f64;
     int32_t status;
-    int32_t replayed;          /* 1: psi came from the replay, 0: from stored vectors */
+    int32_t replayed;          /* Lanczos steps replayed for psi (0: all vectors were stored) */
 } lanczos_refined_result;
 
 size_t lanczos_refined_workspace_bytes(hubbard_t H);

@@ -958,33 +958,43 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
     out->iters_f32 = m;
     out->gap = gap;
 
-    // 2. Ritz vector psi = sum_j s_j f_j in binary64: one pass over the stored
-    //    f_j when they all fit in the workspace, else a replay of the same
-    //    binary32 recurrence with the stored a, b (every kernel is
-    //    deterministic, so the f_j are bit-identical; so is psi either way)
-    if (m <= store_cap) {
-        if (cudaMemcpyAsync(H->red, sv.data(), (size_t)m * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // 2. Ritz vector psi = sum_j s_j f_j in binary64, accumulated in j order:
+    //    one pass over the k = min(m, store_cap) stored f_j, then (k < m) a
+    //    replay of the same binary32 recurrence with the stored a, b from the
+    //    last two stored vectors (every kernel is deterministic, so the f_j
+    //    and psi are bit-identical whatever k is)
+    const int k = std::min(m, store_cap);
+    if (k >= 1) {
+        if (cudaMemcpyAsync(H->red, sv.data(), (size_t)k * sizeof(double), cudaMemcpyHostToDevice, s) != cudaSuccess)
             return fail(HUB_ECUDA, "upload s");
-        if ((rc = launch_psi_multi((const float*)store, (int64_t)(slot / 4), m, H->red, psi, H->D, s))) return rc;
-        out->replayed = 0;
-    } else {
-        double n0 = 0.0;
-        if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
-        if ((rc = launch_f64_to_f32_scaled((const double*)v0, f, H->D, 1.0 / std::sqrt(n0), s))) return rc;
-        if (cudaMemsetAsync(g, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
-        if ((rc = launch_psi_accumulate(f, psi, H->D, sv[0], true, s))) return rc;
-        {
-            float* ff = f;
-            float* gg = g;
-            for (int j = 0; j + 1 < m; ++j) {
-                const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
-                if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
-                if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
-                std::swap(ff, gg);
-                if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
-            }
+        if ((rc = launch_psi_multi((const float*)store, (int64_t)(slot / 4), k, H->red, psi, H->D, s))) return rc;
+    }
+    out->replayed = m - std::max(k, 1);
+    if (k < m) {
+        float* ff = f;
+        float* gg = g;
+        int j0 = 0;
+        if (k >= 2) {
+            // resume from the stored f_{k-2}, f_{k-1}
+            if (cudaMemcpyAsync(ff, store + (size_t)(k - 1) * slot, D * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(gg, store + (size_t)(k - 2) * slot, D * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail(HUB_ECUDA, "resume from stored vectors");
+            j0 = k - 1;
+        } else {
+            double n0 = 0.0;
+            if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0)))
+                return rc;
+            if ((rc = launch_f64_to_f32_scaled((const double*)v0, ff, H->D, 1.0 / std::sqrt(n0), s))) return rc;
+            if (cudaMemsetAsync(gg, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+            if (k == 0 && (rc = launch_psi_accumulate(ff, psi, H->D, sv[0], true, s))) return rc;
         }
-        out->replayed = 1;
+        for (int j = j0; j + 1 < m; ++j) {
+            const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
+            if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
+            if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
+            std::swap(ff, gg);
+            if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
+        }
     }
     double pn = 0.0;
     if ((rc = launch_dot(H, psi, psi, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pn))) return rc;

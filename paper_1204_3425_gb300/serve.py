@@ -61,10 +61,11 @@ class GPUSolver:
         self.device = torch.device(device)
         hub.load_library()
 
-    # binary32 Lanczos vectors kept for the Ritz vector (no replay) when they fit in 8 GB
+    # binary32 Lanczos vectors kept for the Ritz vector (each one saves a replayed
+    # step): up to 128, within 16 GB per request
     @staticmethod
     def store_vectors(D):
-        return 128 if 128 * (4 * D + 256) <= 8e9 else 0
+        return int(min(128, 16e9 // (4 * D + 256)))
 
     # bytes of device memory a request holds while it runs
     @classmethod
