@@ -62,10 +62,10 @@ class GPUSolver:
         hub.load_library()
 
     # binary32 Lanczos vectors kept for the Ritz vector (each one saves a replayed
-    # step): up to 128, within 16 GB per request
+    # step): up to 128, within 32 GB per request
     @staticmethod
     def store_vectors(D):
-        return int(min(128, 16e9 // (4 * D + 256)))
+        return int(min(128, 32e9 // (4 * D + 256)))
 
     # bytes of device memory a request holds while it runs
     @classmethod
