@@ -66,6 +66,7 @@ struct BatchParams {
     struct SweepState* sst;// [nswp]
     unsigned int* gbar;    // grid barrier counter
     int* nactive;          // sectors of the sweep still iterating
+    unsigned long long* claim; // [2] row counters of the sweep's element and update phases
 };
 
 // Lanczos state of a swept sector between the phases of one iteration.
@@ -331,6 +332,13 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         return lo;
     };
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.nactive = P.nswp;
+    // rows of the element and update phases are claimed one at a time (heaviest
+    // sectors first), so warps that drew cheap rows take more of them
+    auto claim = [&](int c) -> int64_t {
+        unsigned long long r = 0ull;
+        if (lane == 0) r = atomicAdd(P.claim + c, 1ull);
+        return (int64_t)__shfl_sync(0xffffffffu, r, 0);
+    };
     // |v0|^2 by rows, then per sector
     for (int64_t r = gw; r < nrows; r += nw_all) {
         const int k = locate(r);
@@ -376,7 +384,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         double* fp = (it & 1) ? P.g : P.f;          // f_j and f_{j-1} swap pools each step
         double* gp = (it & 1) ? P.f : P.g;
         // E
-        for (int64_t r = gw; r < nrows; r += nw_all) {
+        for (int64_t r = claim(0); r < nrows; r = claim(0)) {
             const int k = locate(r);
             if (!__ldcg(&P.sst[k].active)) continue;
             const SectorDesc S = P.sec[P.swp[k]];
@@ -400,6 +408,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         }
         if (!gsync()) return false;
         // R
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.claim[1] = 0ull;   // U of this step starts after a barrier
         for (int k = blockIdx.x; k < P.nswp; k += gridDim.x) {
             SweepState st = P.sst[k];
             if (!st.active) continue;
@@ -469,7 +478,8 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         }
         if (!gsync()) return false;
         // U
-        for (int64_t r = gw; r < nrows; r += nw_all) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) P.claim[0] = 0ull;   // E of the next step starts after a barrier
+        for (int64_t r = claim(1); r < nrows; r = claim(1)) {
             const int k = locate(r);
             if (!__ldcg(&P.sst[k].active)) continue;
             const SectorDesc S = P.sec[P.swp[k]];
@@ -764,13 +774,14 @@ int batch_schedule(hubbard_batch* B) {
     std::vector<int64_t> rowoff(1, 0);
     std::vector<int> order;
     for (int s = 0; s < B->n; ++s) {
-        if (B->sec[s].D > B->elems_per_cta) {
-            swp.push_back(s);
-            rowoff.push_back(rowoff.back() + B->sec[s].Dup);
-        } else {
-            order.push_back(s);
-        }
+        if (B->sec[s].D > B->elems_per_cta) swp.push_back(s);
+        else order.push_back(s);
     }
+    // heaviest rows first (rows are claimed dynamically in this order)
+    std::stable_sort(swp.begin(), swp.end(), [&](int a, int b) {
+        return B->cost[a] / (double)B->sec[a].Dup > B->cost[b] / (double)B->sec[b].Dup;
+    });
+    for (int s : swp) rowoff.push_back(rowoff.back() + B->sec[s].Dup);
     // the rest: one CTA per sector, largest work first to the CTA free first
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
     std::vector<double> avail((size_t)G, 0.0);
@@ -836,7 +847,7 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     L.err = o; o += 256;
     L.rowpart = o; o += al256((size_t)B->rows_all * 3 * 8);
     L.sst = o; o += al256(n * sizeof(SweepState));
-    L.gbar = o; o += 256;                  // grid barrier counter, then the active-sector count
+    L.gbar = o; o += 256;                  // grid barrier counter, active-sector count, two row counters
     L.total = o;
     return L;
 }
@@ -994,7 +1005,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     char* ws = (char*)workspace;
     // the barrier counter and the error word start at zero
     HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
-    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 4, s));
+    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 32, s));
     BatchParams P;
     P.sec = B->d_sec;
     P.cta_ptr = B->d_cta_ptr;
@@ -1020,6 +1031,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     P.sst = (SweepState*)(ws + L.sst);
     P.gbar = (unsigned int*)(ws + L.gbar);
     P.nactive = (int*)(ws + L.gbar + 4);
+    P.claim = (unsigned long long*)(ws + L.gbar + 16);
     void* args[] = {&P};
     const size_t smem = (size_t)B->smem_elems * sizeof(int2);
     HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(B->grid), dim3(kBatchThreads), args, smem, s));
