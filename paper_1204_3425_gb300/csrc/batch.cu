@@ -42,8 +42,8 @@ struct SectorDesc {
 
 struct BatchParams {
     const SectorDesc* sec;
-    const int* cta_ptr;    // [gridDim.x + 1]
-    const int* tasks;      // sector ids, CTA c's in tasks[cta_ptr[c] .. cta_ptr[c+1])
+    const int* tasks;      // one-CTA sector ids, largest work first, claimed through claim[2]
+    int ntasks;
     const int32_t* rp;     // pooled row pointers
     const uint32_t* ent;   // pooled packed hop entries (target << 1) | neg
     const uint32_t* st;    // pooled basis words
@@ -66,7 +66,7 @@ struct BatchParams {
     struct SweepState* sst;// [nswp]
     unsigned int* gbar;    // grid barrier counter
     int* nactive;          // sectors of the sweep still iterating
-    unsigned long long* claim; // [2] row counters of the sweep's element and update phases
+    unsigned long long* claim; // [3] row counters of the sweep's element and update phases, task counter
 };
 
 // Lanczos state of a swept sector between the phases of one iteration.
@@ -508,10 +508,17 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     __shared__ int sh_flags[kBatchThreads];
     __shared__ double sh_k[1];
     __shared__ double sh_out[2];
-    // the larger sectors first, in lock step over the whole grid; then each CTA
-    // walks its own list of smaller sectors
+    // the larger sectors first, in lock step over the whole grid; then the
+    // smaller ones, one CTA each
     if (P.nswp > 0 && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out)) return;
-    for (int ti = P.cta_ptr[blockIdx.x]; ti < P.cta_ptr[blockIdx.x + 1]; ++ti) {
+    __shared__ int sh_task;
+    while (true) {
+        // the next task (largest work first) goes to the CTA that asks first
+        if (threadIdx.x == 0) sh_task = (int)atomicAdd(P.claim + 2, 1ull);
+        __syncthreads();
+        const int ti = sh_task;
+        __syncthreads();
+        if (ti >= P.ntasks) break;
         const int sid = P.tasks[ti];
         const SectorDesc S = P.sec[sid];
         const int64_t D = S.D, Ddn = S.Ddn, Dup = S.Dup;
@@ -689,8 +696,8 @@ struct hubbard_batch {
     uint32_t* d_st = nullptr;
     // schedule
     int64_t elems_per_cta = 1 << 14;
-    int* d_cta_ptr = nullptr;
     int* d_tasks = nullptr;
+    int ntasks = 0;
     size_t tasks_cap = 0;
     int grid = 0;
     int smem_elems = 0;
@@ -734,7 +741,6 @@ void batch_free(hubbard_batch* B) {
     cudaFree(B->d_rp);
     cudaFree(B->d_ent);
     cudaFree(B->d_st);
-    cudaFree(B->d_cta_ptr);
     cudaFree(B->d_tasks);
     cudaFree(B->d_swp);
     cudaFree(B->d_rowoff);
@@ -764,12 +770,11 @@ int batch_grid(hubbard_batch* B, int* smem_elems) {
     return smem;
 }
 
-// Sectors above elems_per_cta elements go to the sweep (in batch order, rows
-// in order); the rest are one-CTA tasks, largest work first to the CTA whose
-// list is shortest (LPT).  Lists stay in assignment order.
+// Sectors above elems_per_cta elements go to the sweep, ordered by the cost of
+// their rows (heaviest first); the rest are one-CTA tasks ordered by work
+// (largest first).  The kernel hands both out dynamically in these orders.
 int batch_schedule(hubbard_batch* B) {
-    const int G = B->grid;
-    // sectors above the threshold: the grid-synchronous sweep (rows in order)
+    // sectors above the threshold: the grid-synchronous sweep
     std::vector<int> swp;
     std::vector<int64_t> rowoff(1, 0);
     std::vector<int> order;
@@ -782,17 +787,8 @@ int batch_schedule(hubbard_batch* B) {
         return B->cost[a] / (double)B->sec[a].Dup > B->cost[b] / (double)B->sec[b].Dup;
     });
     for (int s : swp) rowoff.push_back(rowoff.back() + B->sec[s].Dup);
-    // the rest: one CTA per sector, largest work first to the CTA free first
+    // the rest: one CTA per sector, largest work first (claimed dynamically)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
-    std::vector<double> avail((size_t)G, 0.0);
-    std::vector<std::vector<int>> lists((size_t)G);
-    for (int s : order) {
-        int c = 0;
-        for (int i = 1; i < G; ++i)
-            if (avail[(size_t)i] < avail[(size_t)c]) c = i;
-        lists[(size_t)c].push_back(s);
-        avail[(size_t)c] += B->cost[s];
-    }
     cudaFree(B->d_swp);
     cudaFree(B->d_rowoff);
     B->d_swp = nullptr;
@@ -807,21 +803,12 @@ int batch_schedule(hubbard_batch* B) {
             e = cudaMemcpy(B->d_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "batch sweep list upload");
     }
-    std::vector<int> ptr((size_t)G + 1, 0);
-    std::vector<int> flat;
-    for (int c = 0; c < G; ++c) {
-        ptr[(size_t)c + 1] = ptr[(size_t)c] + (int)lists[c].size();
-        flat.insert(flat.end(), lists[c].begin(), lists[c].end());
-    }
-    cudaFree(B->d_cta_ptr);
     cudaFree(B->d_tasks);
-    B->d_cta_ptr = nullptr;
     B->d_tasks = nullptr;
-    cudaError_t e = cudaMalloc((void**)&B->d_cta_ptr, ptr.size() * sizeof(int));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(flat.size(), 1) * sizeof(int));
-    if (e == cudaSuccess) e = cudaMemcpy(B->d_cta_ptr, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !flat.empty())
-        e = cudaMemcpy(B->d_tasks, flat.data(), flat.size() * sizeof(int), cudaMemcpyHostToDevice);
+    B->ntasks = (int)order.size();
+    cudaError_t e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(order.size(), 1) * sizeof(int));
+    if (e == cudaSuccess && !order.empty())
+        e = cudaMemcpy(B->d_tasks, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch schedule upload");
     e = cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
@@ -847,7 +834,7 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     L.err = o; o += 256;
     L.rowpart = o; o += al256((size_t)B->rows_all * 3 * 8);
     L.sst = o; o += al256(n * sizeof(SweepState));
-    L.gbar = o; o += 256;                  // grid barrier counter, active-sector count, two row counters
+    L.gbar = o; o += 256;                  // grid barrier counter, active-sector count, row and task counters
     L.total = o;
     return L;
 }
@@ -1005,11 +992,11 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     char* ws = (char*)workspace;
     // the barrier counter and the error word start at zero
     HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
-    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 32, s));
+    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 64, s));
     BatchParams P;
     P.sec = B->d_sec;
-    P.cta_ptr = B->d_cta_ptr;
     P.tasks = B->d_tasks;
+    P.ntasks = B->ntasks;
     P.rp = B->d_rp;
     P.ent = B->d_ent;
     P.st = B->d_st;
