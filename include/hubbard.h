@@ -181,20 +181,20 @@ int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, vo
 int hubbard_apply_noalloc(hubbard_t H, const void* v, void* w, void* stream);
 
 /* ---------------------------------------------------------------------------
- * Lanczos vector operations (Algorithm 1, lines 5-7), n elements of dtype,
- * results accumulated in binary64 in a fixed reduction order (deterministic
- * for a given n and dtype).  Device vectors; host scalar results; these
- * synchronise `stream`.
+ * Lanczos vector operations (the dot product, norm and update of
+ * Algorithm 1), n elements of dtype, results accumulated in binary64 in a
+ * fixed reduction order (deterministic for a given n and dtype).  Device
+ * vectors; host scalar results; dot and nrm2 synchronise `stream`.
  * ------------------------------------------------------------------------- */
 int hubbard_vec_dot(const void* x, const void* y, int64_t n, int dtype, void* stream, double* out);
 int hubbard_vec_nrm2(const void* x, int64_t n, int dtype, void* stream, double* out);
 /* y <- y + a*x  (asynchronous) */
+int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, void* stream);
 
 /* Seeded start vector on the device (the paper asks for a random start
  * vector, Algorithm 1): v[i] = 2 x - 1 with x the top 53 bits of SplitMix64
  * (Steele, Lea, Flood 2014) at counter seed * 2^40 + start + i, divided by
  * 2^53; binary32 rounds the binary64 value.  Asynchronous. */
-int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, void* stream);
 int hubbard_fill_start_vector(void* v, int64_t n, uint64_t seed, int64_t start, int dtype, void* stream);
 
 /* ---------------------------------------------------------------------------
@@ -203,6 +203,10 @@ int hubbard_fill_start_vector(void* v, int64_t n, uint64_t seed, int64_t start, 
  *   beta_{j+1} = |g|;  g <- g / beta_{j+1}  (skipped when beta_{j+1} == 0)
  * f must have norm 1.  f, g device vectors of D elements.  Writes alpha_j
  * and beta_{j+1} to *alpha, *beta_next (host).  Synchronises `stream`.
+ * The H*v kernels also reduce g.f, g.g and f.f, so beta_{j+1}^2 =
+ * g.g - 2 alpha_j^2 + alpha_j^2 f.f without another pass; when that
+ * difference cancels more than six digits of g.g, |g - alpha_j f| is formed
+ * explicitly.  The update rounds as an axpy followed by a scale.
  * ------------------------------------------------------------------------- */
 int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int dtype,
                          void* stream, double* alpha, double* beta_next);

@@ -709,7 +709,7 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
     return launch_axpy(a, x, y, n, dtype, (cudaStream_t)stream);
 }
 
-// One Lanczos step (Eqs. split1 + Algorithm 1 lines 5-11) on caller vectors.
+// One Lanczos step (Eqs. split1, Algorithm 1) on caller vectors.
 // fixed_emax: 1023 when f and g are known to have norm <= 1 (inside the
 // solver), 0 to derive the fixed-point scale from the data.
 // One step of Algorithm 1 in the two-vector form: g <- H f - beta_j g,
