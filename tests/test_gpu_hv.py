@@ -304,3 +304,30 @@ def test_shared_tables_between_handles(dev):
             assert np.array_equal(g, r)
     H2.close()
     H3.close()
+
+
+@pytest.mark.parametrize("scale", [2.0 ** 900, 2.0 ** -900, 1e-310, 3.7e12])
+@pytest.mark.parametrize("case", [("sq3x3", 4, 5, 1.0, 6.0), ("ring6", 3, 3, 0.75, 2.5)])
+def test_hv_f64_extreme_scales(dev, case, scale):
+    """The fixed-point grid follows max|v| wherever it lies in the binary64
+    range (huge, tiny, subnormal inputs), both in the standalone H*v and in a
+    Lanczos step; an all-zero vector gives zero."""
+    H, S = _sector(*case)
+    t = case[3]
+    u = start_vector(S.D, seed=79)
+    v = u * scale
+    ref = (S.explicit() @ u) * scale                   # no overflow in the reference
+    vd = torch.from_numpy(v).to(dev)
+    w = torch.full_like(vd, np.nan)
+    hub.hubbard_apply(H, vd, w)
+    got = w.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    nrm = np.linalg.norm(u) * scale
+    # subnormal inputs: the fixed-point grid cannot go below the smallest subnormal
+    floor = 4.95e-324 * (S.D ** 0.5) * 64 * max(1.0, abs(t))
+    err = np.abs(got - ref).max()
+    tol = 1e-12 * nrm * max(1.0, abs(t)) + floor
+    assert err <= tol, (err, tol, np.abs(ref).max())
+    z = torch.zeros_like(vd)
+    hub.hubbard_apply(H, z, w)
+    assert torch.count_nonzero(w).item() == 0
