@@ -284,7 +284,7 @@ class RefinedResult(ctypes.Structure):
 
 def lanczos_refined_workspace_bytes(H, store_vectors=0):
     """Minimum workspace, plus room for store_vectors binary32 Lanczos vectors
-    (stored vectors let the solver skip the replay for the Ritz vector)."""
+    (each stored vector saves one replayed step for the Ritz vector)."""
     slot = (H.D * 4 + 255) // 256 * 256
     return int(load_library().lanczos_refined_workspace_bytes(H.handle)) + int(store_vectors) * slot
 
