@@ -262,7 +262,7 @@ def run_ours(args):
     if args.workload == "sq4x4_n8_8_U8_f64" and args.solves > 0:
         extra["solve_refined"] = bench_refined(hub, torch, dev, bonds, golden, args.solves)
     if args.batch and rank == 0:
-        extra["batch"] = bench_batch(hub, torch, dev)
+        extra["batch"] = bench_batch(hub, torch, dev, count=args.batch_sectors, autotune=not args.no_autotune)
     if args.serve and rank == 0:
         extra["serve"] = bench_serve(args.serve)
 
@@ -369,7 +369,7 @@ def bench_refined(hub, torch, dev, bonds, golden, n):
                 path="binary32 Lanczos + Ritz vector + binary64 Rayleigh/polish")
 
 
-def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10):
+def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune=True):
     """2048 uneven sectors in one persistent launch; schedule picked by the autotuner."""
     from workload import batch_sectors, lattice_by_name
     reqs = batch_sectors(count, seed=1234)
@@ -386,7 +386,11 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10):
         hub.hubbard_fill_start_vector(v0[int(B.offsets[k]):int(B.offsets[k]) + D], r["seed"])
     ws = torch.empty(B.workspace_bytes(max_iters), dtype=torch.uint8, device=dev)
     t0 = time.perf_counter()
-    chosen = B.autotune(v0, 40, tol, ws)            # short solves (40 steps) rank the schedules
+    if autotune:
+        chosen = B.autotune(v0, 40, tol, ws)        # short solves (40 steps) rank the schedules
+    else:
+        chosen = 16384                              # the library's default threshold
+        B.set_schedule(chosen)
     tune_s = time.perf_counter() - t0
     # the solve (two memsets + one cooperative launch) captured once as a CUDA graph, then replayed
     stream = torch.cuda.Stream(device=dev)
@@ -503,8 +507,11 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="time the default H*v schedule (profiling commands use it: no tuning launches)")
+                    help="time the default H*v schedule and batch threshold (profiling commands use it: "
+                         "no tuning launches)")
     ap.add_argument("--batch", type=int, default=1, help="also time the 2048-sector batched solve (0: skip)")
+    ap.add_argument("--batch-sectors", type=int, default=2048,
+                    help="sectors in the batched solve (smaller: the profiling case)")
     ap.add_argument("--serve", type=int, default=400, help="requests in the serving trace (0: skip)")
     args = ap.parse_args()
     if args.impl == "reference":
