@@ -725,13 +725,14 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
 // Both finishes round as axpy then scale, so either leaves the same f_{j+1}.
 static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
                              double* alpha, double* beta_next, bool normalise, int fixed_emax,
-                             bool* pending = nullptr) {
+                             bool* pending = nullptr, const RowUpdate* upd = nullptr) {
     int rc;
     if (dtype == HUB_F64 && !fixed_point_ok(H))
         return fail(HUB_EINVAL, "lanczos step: more than 127 hops per state is not supported");
     bool fused = false;
-    // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels with the reductions
-    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s, H->red, &fused))) return rc;
+    // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels with the
+    // reductions; upd: f itself is first completed by the previous step's update
+    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s, H->red, &fused, upd))) return rc;
     double a = 0.0, b2 = 0.0;
     bool pend = false;
     if (fused) {
@@ -816,10 +817,21 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
     if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
     const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
     double bj = 0.0;
+    // f_{j+1} = (g - a_j f_j) / b_{j+1} is left to the next step's row phase,
+    // which completes it while staging its rows
+    RowUpdate upd{};
+    bool have_upd = false;
     for (int j = 0; j < m_cap; ++j) {
         double aj = 0.0, bn = 0.0;
         bool pending = false;
-        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023, &pending))) return rc;
+        if ((rc = lanczos_step_impl(H, f, g, bj, dtype, s, &aj, &bn, false, 1023, &pending,
+                                    have_upd ? &upd : nullptr)))
+            return rc;
+        have_upd = false;
+        // f holds the final f_j from here on
+        if (j >= 1 && j < store_cap &&
+            cudaMemcpyAsync(store + (size_t)j * store_stride, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            return fail(HUB_ECUDA, "store f_j");
         R.a.push_back(aj);
         double s_last = 1.0;
         tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
@@ -837,12 +849,12 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
             R.converged = true;
             break;
         }
-        if (pending) rc = launch_axpy_scale(-aj, 1.0 / bn, f, g, H->D, dtype, s);
-        else rc = launch_scale(1.0 / bn, g, H->D, dtype, s);
-        if (rc) return rc;
-        if (j + 1 < store_cap &&
-            cudaMemcpyAsync(store + (size_t)(j + 1) * store_stride, g, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-            return fail(HUB_ECUDA, "store f_j");
+        if (pending) {
+            upd = RowUpdate{f, -aj, 1.0 / bn};
+            have_upd = true;
+        } else if ((rc = launch_scale(1.0 / bn, g, H->D, dtype, s))) {
+            return rc;
+        }
         std::swap(f, g);
         bj = bn;
     }
@@ -988,12 +1000,23 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
             if (cudaMemsetAsync(gg, 0, D * 4, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
             if (k == 0 && (rc = launch_psi_accumulate(ff, psi, H->D, sv[0], true, s))) return rc;
         }
+        // each update f_{j+1} = (g - a_j f_j) / b_{j+1} is completed by the next
+        // step's row phase (same roundings as launch_axpy_scale), the last one
+        // by a pass of its own
+        RowUpdate ru{};
+        bool have = false;
         for (int j = j0; j + 1 < m; ++j) {
             const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
-            if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s))) return rc;
-            if ((rc = launch_axpy_scale(-R.a[(size_t)j], 1.0 / R.b[(size_t)j], ff, gg, H->D, HUB_F32, s))) return rc;
+            if ((rc = launch_hv_fast(H, ff, gg, HUB_F32, bj, gg, 1023, s, nullptr, nullptr, have ? &ru : nullptr)))
+                return rc;
+            if (have && (rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j], false, s))) return rc;
+            ru = RowUpdate{ff, -R.a[(size_t)j], 1.0 / R.b[(size_t)j]};
+            have = true;
             std::swap(ff, gg);
-            if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)j + 1], false, s))) return rc;
+        }
+        if (have) {
+            if ((rc = launch_axpy_scale(ru.a, ru.inv, ru.fo, ff, H->D, HUB_F32, s))) return rc;
+            if ((rc = launch_psi_accumulate(ff, psi, H->D, sv[(size_t)m - 1], false, s))) return rc;
         }
     }
     double pn = 0.0;

@@ -198,14 +198,18 @@ __device__ __forceinline__ void for_each_hop(const EntT* __restrict__ base, int 
 }
 
 // Row phase, binary64 fixed point: Y[u, d] = sum_{(d', s) in hops_dn(d)} s X[u, d'];
-// also writes the fixed-point copy of V to Xg for the up phase
-template <int VEC, typename EntT>
-__global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v, long long* __restrict__ Y,
+// also writes the fixed-point copy of V to Xg for the up phase.
+// UPD: the previous Lanczos step's update is applied on the way in,
+// v <- (v + ua fo) * uinv, rounded as k_axpy_scale_f64, and written back to v.
+template <int VEC, typename EntT, bool UPD>
+__global__ void __launch_bounds__(1024, 1) k_rows_f64x(std::conditional_t<UPD, double*, const double*> __restrict__ v,
+                                                     long long* __restrict__ Y,
                                                      int2* __restrict__ Xg, int64_t Dup, int64_t Ddn,
                                                      const int64_t* __restrict__ boff,
                                                      const int32_t* __restrict__ bcnt,
                                                      const EntT* __restrict__ ent,
-                                                     const int* __restrict__ emax_p, int fixed_emax) {
+                                                     const int* __restrict__ emax_p, int fixed_emax,
+                                                     const double* __restrict__ fo, double ua, double uinv) {
     using S = typename FxVec<VEC>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* X = reinterpret_cast<S*>(smem_raw);
@@ -213,6 +217,7 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
     const int lane = threadIdx.x & 31;
     const int64_t nblk = (Dup + VEC - 1) / VEC;
     const int64_t step = blockDim.x;
+    constexpr int NL = UPD ? 2 : 4;                       // row elements per thread in flight
     {
         const int64_t z0 = staged_slots(Ddn) - 32;
         for (int i = threadIdx.x; i < 32; i += blockDim.x) {
@@ -223,18 +228,34 @@ __global__ void __launch_bounds__(1024) k_rows_f64x(const double* __restrict__ v
     for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int64_t u0 = b * VEC;
         const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
-        // stage rows u0 .. u0+nrow-1 as fixed point, 4 loads per row in flight
-        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += 4 * step) {
-            double xv[4][VEC];
+        // stage rows u0 .. u0+nrow-1 as fixed point, NL loads per row in flight
+        // (with UPD every load of a group is issued before the first store)
+        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += NL * step) {
+            double xv[NL][VEC];
+            [[maybe_unused]] double fv[NL][VEC];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NL; ++i)
 #pragma unroll
                 for (int r = 0; r < VEC; ++r) {
                     const int64_t d = d0 + i * step;
-                    xv[i][r] = (d < Ddn && r < nrow) ? v[(u0 + r) * Ddn + d] : 0.0;
+                    const bool in = d < Ddn && r < nrow;
+                    xv[i][r] = in ? v[(u0 + r) * Ddn + d] : 0.0;
+                    if constexpr (UPD) fv[i][r] = in ? fo[(u0 + r) * Ddn + d] : 0.0;
                 }
+            if constexpr (UPD) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < NL; ++i)
+#pragma unroll
+                    for (int r = 0; r < VEC; ++r) {
+                        const int64_t d = d0 + i * step;
+                        if (d < Ddn && r < nrow) {
+                            xv[i][r] = fma(ua, fv[i][r], xv[i][r]) * uinv;
+                            __stcs(v + (u0 + r) * Ddn + d, xv[i][r]);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < NL; ++i) {
                 const int64_t d = d0 + i * step;
                 if (d >= Ddn) break;
                 int w[2 * VEC];
@@ -747,12 +768,15 @@ __global__ void __launch_bounds__(256, up32_ctas<VPL, RED>()) k_up_f32(const flo
 }
 
 // ---------------------------------------------------------------------------
-// binary32 variants: same structure, float arithmetic
-template <int VEC, typename EntT>
-__global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, float* __restrict__ Y, int64_t Dup,
+// binary32 variants: same structure, float arithmetic (UPD: the deferred
+// Lanczos update, rounded as k_axpy_scale_f32)
+template <int VEC, typename EntT, bool UPD>
+__global__ void __launch_bounds__(1024, 1) k_rows_f32(std::conditional_t<UPD, float*, const float*> __restrict__ v,
+                                                    float* __restrict__ Y, int64_t Dup,
                                                     int64_t Ddn, const int64_t* __restrict__ boff,
                                                     const int32_t* __restrict__ bcnt,
-                                                    const EntT* __restrict__ ent) {
+                                                    const EntT* __restrict__ ent,
+                                                    const float* __restrict__ fo, float ua, float uinv) {
     using S = typename F32Vec<VEC>::T;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* X = reinterpret_cast<S*>(smem_raw);
@@ -760,6 +784,7 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
     const int lane = threadIdx.x & 31;
     const int64_t nblk = (Dup + VEC - 1) / VEC;
     const int64_t step = blockDim.x;
+    constexpr int NL = UPD ? 2 : 4;                       // row elements per thread in flight
     {
         const int64_t z0 = staged_slots(Ddn) - 32;
         for (int i = threadIdx.x; i < 32 * VEC; i += blockDim.x) Xf[z0 * VEC + i] = 0.0f;
@@ -767,17 +792,33 @@ __global__ void __launch_bounds__(1024) k_rows_f32(const float* __restrict__ v, 
     for (int64_t b = blockIdx.x; b < nblk; b += gridDim.x) {
         const int64_t u0 = b * VEC;
         const int nrow = (int)((Dup - u0) < VEC ? (Dup - u0) : VEC);
-        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += 4 * step) {
-            float xv[4][VEC];
+        // NL loads per row in flight (with UPD all issued before the first store)
+        for (int64_t d0 = threadIdx.x; d0 < Ddn; d0 += NL * step) {
+            float xv[NL][VEC];
+            [[maybe_unused]] float fv[NL][VEC];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < NL; ++i)
 #pragma unroll
                 for (int r = 0; r < VEC; ++r) {
                     const int64_t d = d0 + i * step;
-                    xv[i][r] = (d < Ddn && r < nrow) ? v[(u0 + r) * Ddn + d] : 0.0f;
+                    const bool in = d < Ddn && r < nrow;
+                    xv[i][r] = in ? v[(u0 + r) * Ddn + d] : 0.0f;
+                    if constexpr (UPD) fv[i][r] = in ? fo[(u0 + r) * Ddn + d] : 0.0f;
                 }
+            if constexpr (UPD) {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
+                for (int i = 0; i < NL; ++i)
+#pragma unroll
+                    for (int r = 0; r < VEC; ++r) {
+                        const int64_t d = d0 + i * step;
+                        if (d < Ddn && r < nrow) {
+                            xv[i][r] = fmaf(ua, fv[i][r], xv[i][r]) * uinv;
+                            __stcs(v + (u0 + r) * Ddn + d, xv[i][r]);
+                        }
+                    }
+            }
+#pragma unroll
+            for (int i = 0; i < NL; ++i) {
                 const int64_t d = d0 + i * step;
                 if (d >= Ddn) break;
 #pragma unroll
@@ -925,7 +966,8 @@ int choose_vec(int req, int64_t len, int elem_bytes, int vmax, int reserve) {
 // Returns HUB_OK and launches, or returns -1 when the staging buffers do not fit
 // (the caller then uses the single-pass gather kernel).
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                     void* ybuf, int fixed_emax, cudaStream_t s, double* part, int* nparts) {
+                     void* ybuf, int fixed_emax, cudaStream_t s, double* part, int* nparts,
+                     const RowUpdate* upd) {
     if (nparts != nullptr) *nparts = 0;
     if (sms() * 5 > kPartStride) part = nullptr;        // partial arrays too short: no fused reduction
     const DevSpin& up = H->dev[0];
@@ -940,6 +982,12 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     if (dtype == HUB_F64) {
         const int va = choose_vec(H->vec_rows, Ddn, 8, 2, 0);
         int* emax = H->status;
+        // the deferred update goes into the row phase when it stages rows in
+        // shared memory with a fixed exponent bound; otherwise it is one pass first
+        if (upd != nullptr && (va == 0 || fixed_emax <= 0)) {
+            if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s)) return rc;
+            upd = nullptr;
+        }
         if (fixed_emax <= 0) {
             HUB_CUDA(cudaMemsetAsync(emax, 0, sizeof(int), s));
             launch_max_exponent((const double*)v, H->D, emax, s);
@@ -968,10 +1016,12 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             }
             extra = 2;
         } else {
-#define ROWS64(V, E, P)                                                                                     \
-    allow_smem<k_rows_f64x<V, E>>();                                                                         \
-    k_rows_f64x<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const double*)v, Y, Xg, Dup, Ddn, dn.blk_off,  \
-                                                            dn.blk_cnt, P, emax, fixed_emax)
+#define ROWS64_U(V, E, P, U)                                                                                \
+    allow_smem<k_rows_f64x<V, E, U>>();                                                                      \
+    k_rows_f64x<V, E, U><<<LA.blocks, LA.threads, LA.smem, s>>>((double*)const_cast<void*>(v), Y, Xg, Dup,   \
+        Ddn, dn.blk_off, dn.blk_cnt, P, emax, fixed_emax, upd ? (const double*)upd->fo : nullptr,            \
+        upd ? upd->a : 0.0, upd ? upd->inv : 1.0)
+#define ROWS64(V, E, P) if (upd) { ROWS64_U(V, E, P, true); } else { ROWS64_U(V, E, P, false); }
         if (va == 2) {
             if (dn16) { ROWS64(2, uint16_t, dn.ent16); } else { ROWS64(2, uint32_t, dn.ent32); }
         } else {
@@ -980,6 +1030,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
         extra = 1;
         }
 #undef ROWS64
+#undef ROWS64_U
         const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
         const int up_grid = sms() * (part != nullptr ? 3 : 4);
 #define UP64(K, V, F)                                                                                       \
@@ -1008,15 +1059,19 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     // columns per lane in the up phase: the widest aligned vector load, capped by vec_cols
     int vpl = (Ddn & 3) == 0 ? 4 : ((Ddn & 1) == 0 ? 2 : 1);
     if (H->vec_cols > 0 && H->vec_cols < vpl) vpl = H->vec_cols;
-#define ROWS32(V, E, P)                                                                                    \
-    allow_smem<k_rows_f32<V, E>>();                                                                         \
-    k_rows_f32<V, E><<<LA.blocks, LA.threads, LA.smem, s>>>((const float*)v, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, P)
+#define ROWS32_U(V, E, P, U)                                                                               \
+    allow_smem<k_rows_f32<V, E, U>>();                                                                      \
+    k_rows_f32<V, E, U><<<LA.blocks, LA.threads, LA.smem, s>>>((float*)const_cast<void*>(v), Y, Dup, Ddn,   \
+        dn.blk_off, dn.blk_cnt, P, upd ? (const float*)upd->fo : nullptr, upd ? (float)upd->a : 0.0f,       \
+        upd ? (float)upd->inv : 1.0f)
+#define ROWS32(V, E, P) if (upd) { ROWS32_U(V, E, P, true); } else { ROWS32_U(V, E, P, false); }
 #define BOTH32(M, V, F, P16, P32) if (F) { M(V, uint16_t, P16); } else { M(V, uint32_t, P32); }
     if (va == 4) { BOTH32(ROWS32, 4, dn16, dn.ent16, dn.ent32) }
     else if (va == 2) { BOTH32(ROWS32, 2, dn16, dn.ent16, dn.ent32) }
     else { BOTH32(ROWS32, 1, dn16, dn.ent16, dn.ent32) }
 #undef BOTH32
 #undef ROWS32
+#undef ROWS32_U
     int up_grid = 0;
 #define UP32(V)                                                                                            \
     {                                                                                                      \

@@ -108,23 +108,37 @@ constexpr int kPartStride = 1024;    // stride of the partial arrays of a fused 
 // process-wide count of kernel launches (hubbard_kernel_launches)
 void count_launches(int n);
 
+// A Lanczos vector update deferred into the next H*v (Algorithm 1, the
+// normalisation of the new vector): before v is used, every element becomes
+// v <- (v + a fo) * inv, rounded as launch_axpy_scale (one fused multiply-add,
+// then one multiplication), and is written back to v.  The row phase applies
+// it while staging rows, which saves the separate pass over three vectors.
+struct RowUpdate {
+    const void* fo;
+    double a, inv;
+};
+
 // kernels.cu launchers -------------------------------------------------------
 int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dtype, cudaStream_t s);
 // part != nullptr: also reduce <w, v>, <w, w> and <v, v> into
 // part[kRedSlots-1], part[kRedSlots-2], part[kRedSlots-3] (fused Lanczos
 // reductions); *fused tells whether that happened (the kernel path in use may
 // not support it).
+// upd != nullptr: v is first updated in place as RowUpdate describes.
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta,
                    const void* w_old, int fixed_emax, cudaStream_t s, double* part = nullptr,
-                   bool* fused = nullptr);
+                   bool* fused = nullptr, const RowUpdate* upd = nullptr);
 // hv_phases.cu: two-phase shared-memory H*v; -1 when the staging buffers do not fit.
 // fixed_emax > 0 fixes the fixed-point exponent bound (vectors of norm <= 1:
 // 1023); otherwise it is computed from v and w_old.
 // part != nullptr: the up phase writes per-CTA partials of <w, v>, <w, w> and
 // <v, v> at part[b], part[kPartStride + b], part[2 kPartStride + b];
 // *nparts = their count (<= kPartStride).
+// upd != nullptr: v is first updated in place (fused into the row phase where
+// it stages rows in shared memory); -1 is returned before anything is launched.
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                     void* ybuf, int fixed_emax, cudaStream_t s, double* part = nullptr, int* nparts = nullptr);
+                     void* ybuf, int fixed_emax, cudaStream_t s, double* part = nullptr, int* nparts = nullptr,
+                     const RowUpdate* upd = nullptr);
 // max biased binary64 exponent of |v| folded into *emax (atomicMax; caller zeroes it)
 void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s);
 // binary64 -> (lo, hi) fixed point with the exponent bound *emax (read on the device)

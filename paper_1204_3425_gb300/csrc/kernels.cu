@@ -353,14 +353,14 @@ void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s) 
 }
 
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                   int fixed_emax, cudaStream_t s, double* part, bool* fused) {
+                   int fixed_emax, cudaStream_t s, double* part, bool* fused, const RowUpdate* upd) {
     const DevSpin& up = H->dev[0];
     const DevSpin& dn = H->dev[1];
     const int grid = grid_for(H->Dup, 1, sm_count() * 16);
     if (fused != nullptr) *fused = false;
     if (H->fx_bytes >= (size_t)H->D * 16) {
         int np = 0;
-        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s, part, &np);
+        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s, part, &np, upd);
         if (rc != -1) {
             if (rc == HUB_OK && part != nullptr && np > 0) {
                 k_finish_sum3<<<1, 1024, 0, s>>>(part, np);
@@ -370,6 +370,9 @@ int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double 
             }
             return rc;
         }
+    }
+    if (upd != nullptr) {
+        if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s)) return rc;
     }
     if (dtype == HUB_F32) {
         if (w_old != nullptr || beta != 0.0) return fail(HUB_EINVAL, "f32 fused step not available");

@@ -160,6 +160,39 @@ def test_fused_lanczos_steps_keep_unit_norm(dev, dt, norm_tol, ab_tol):
         beta = b
 
 
+def test_deferred_update_matches_explicit_steps(dev):
+    """lanczos_ground_state completes each f_{j+1} = (w - a_j f_j) / b_{j+1} inside
+    the next step's row phase; driving the same recurrence through
+    hubbard_lanczos_step (which normalises with a pass of its own) must give the
+    same a_j, b_j: bit for bit in binary32 (same kernels, same roundings), to
+    rounding in binary64 (the standalone step takes its fixed-point grid from
+    max|f|, the solver the fixed 2^-47 grid of unit vectors).  Rows of 924
+    elements: 28 full 32-lane groups and a ragged tail."""
+    H, S = _sector("ring12", 6, 6, 1.0, 4.0)
+    rng = np.random.default_rng(21)
+    # 256 entries +-1: |v0| = 16 exactly, so f_0 = v0 / 16 is exact on both routes
+    v0 = np.zeros(S.D)
+    v0[rng.choice(S.D, 256, replace=False)] = rng.choice([-1.0, 1.0], 256)
+    n = 40
+    for tdt in (torch.float32, torch.float64):
+        r = hub.lanczos_ground_state(H, torch.from_numpy(v0).to(dev, tdt), n, 0.0)
+        assert r["iters"] == n
+        f = torch.from_numpy(v0 / 16.0).to(dev, tdt)
+        g = torch.zeros_like(f)
+        a, b, beta = [], [], 0.0
+        for _ in range(n):
+            aj, bj = hub.hubbard_lanczos_step(H, f, g, beta)
+            a.append(aj)
+            b.append(bj)
+            f, g = g, f
+            beta = bj
+        if tdt == torch.float32:
+            assert np.array_equal(r["alpha"], np.array(a)) and np.array_equal(r["beta"], np.array(b))
+        else:
+            np.testing.assert_allclose(r["alpha"], a, rtol=1e-11, atol=1e-12)
+            np.testing.assert_allclose(r["beta"], b, rtol=1e-11)
+
+
 def test_lanczos_breakdown_tiny_sector(dev):
     # one electron on a 4-ring: eigenvalues -2, 0, 0, 2, so the Krylov space
     # of any start vector has dimension 3 and step 3 breaks down (b_4 ~ 0)
