@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "row_blocks.cuh"
 
 namespace hub {
 namespace {
@@ -37,6 +38,7 @@ struct SectorDesc {
     int64_t up_ent, dn_ent;
     int64_t up_st, dn_st;
     int64_t ab;            // offset of its a/b history (2 * max_iters doubles)
+    int64_t dn_blk;        // first group of its down-spin row table in the block pools (-1: none)
     double t, U;
 };
 
@@ -47,6 +49,9 @@ struct BatchParams {
     const int32_t* rp;     // pooled row pointers
     const uint32_t* ent;   // pooled packed hop entries (target << 1) | neg
     const uint32_t* st;    // pooled basis words
+    const int64_t* bo;     // pooled row tables (coloured for 8-byte slots): first entry of each group
+    const int32_t* bc;     //   half-blocks of 4 slots per group
+    const uint16_t* be;    //   entries (15-bit staged slot index, bit 15 = sign -1)
     const double* v0;      // caller start vectors (concatenated)
     double* f;             // Lanczos vector pools (workspace)
     double* g;
@@ -235,20 +240,36 @@ struct SecView {
     const uint32_t *uent, *dent, *ust, *dst;
     int64_t Ddn;
     double U, scale;       // scale = -t * 2^-47
+    // down-spin row table (nullptr: per-lane CSR lists instead); used when the
+    // row is staged with its zero slots
+    const int64_t* dbo = nullptr;
+    const int32_t* dbc = nullptr;
+    const uint16_t* dbe = nullptr;
 };
+
+// A row staged for the coloured down-hop table: Ddn rounded up to 32, then the
+// zero slots its padding entries read (8-byte slots fall in 16 bank groups, so
+// 16 zero slots cover every group).
+constexpr int kRowZeroSlots = 16;
+__host__ __device__ __forceinline__ int64_t row_slots(int64_t Ddn) { return (Ddn + 31) / 32 * 32 + kRowZeroSlots; }
 
 // Row u of q = H f - beta g (Eqs. split1) by one warp, the fixed-point copy in
 // global memory (L2): the row is staged in buf (when given) for the
 // down-hops, up-hops read whole neighbour rows with lanes over columns
 // (coalesced; the row's hop list is held in the lanes, the column loop is
-// warp-uniform).  Adds this lane's <q,f>, <q,q>, <f,f> over the row.
+// warp-uniform).  With V.dbo and a staged row (buf holds row_slots(Ddn)
+// elements) the down-hops walk the coloured row table: the same slot count
+// for all lanes of a group and no shared-memory bank conflicts; otherwise each
+// lane walks its own CSR list.  Adds this lane's <q,f>, <q,q>, <f,f> over the row.
 __device__ __forceinline__ void row_pass(const SecView& V, int64_t u, int2* buf, double beta, double& ap,
                                          double& qq, double& ff) {
     const int lane = threadIdx.x & 31;
     const int64_t Ddn = V.Ddn;
     const int2* xr = V.X + u * Ddn;
+    const bool blocks = buf != nullptr && V.dbo != nullptr;
     if (buf != nullptr) {
         for (int64_t d = lane; d < Ddn; d += 32) buf[d] = __ldcg(xr + d);
+        if (blocks && lane < kRowZeroSlots) buf[(Ddn + 31) / 32 * 32 + lane] = make_int2(0, 0);
         __syncwarp();
         xr = buf;
     }
@@ -275,10 +296,20 @@ __device__ __forceinline__ void row_pass(const SecView& V, int64_t u, int2* buf,
                 if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
             }
         }
-        for (int32_t k = V.drp[dd]; k < V.drp[dd + 1]; ++k) {
-            const uint32_t e = V.dent[k];
-            const int2 x = buf != nullptr ? xr[e >> 1] : __ldcg(xr + (e >> 1));
-            if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+        if (blocks) {
+            // padding slots (and the lanes past Ddn) read a zero slot
+            for_each_hop<uint16_t>(V.dbe + V.dbo[d0 >> 5], V.dbc[d0 >> 5], lane, [&](uint32_t e) {
+                const int s = RowEnt<uint16_t>::sgn(e);
+                const int2 x = buf[RowEnt<uint16_t>::idx(e)];
+                lo += s * x.x;
+                hi += s * x.y;
+            });
+        } else {
+            for (int32_t k = V.drp[dd]; k < V.drp[dd + 1]; ++k) {
+                const uint32_t e = V.dent[k];
+                const int2 x = buf != nullptr ? xr[e >> 1] : __ldcg(xr + (e >> 1));
+                if (e & 1u) { lo -= x.x; hi -= x.y; } else { lo += x.x; hi += x.y; }
+            }
         }
         if (act) {
             const int64_t j = u * Ddn + d;
@@ -388,13 +419,15 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
             const int k = locate(r);
             if (!__ldcg(&P.sst[k].active)) continue;
             const SectorDesc S = P.sec[P.swp[k]];
-            const SecView V{P.xg + S.voff, fp + S.voff, gp + S.voff, P.rp + S.up_rp, P.rp + S.dn_rp,
-                            P.ent + S.up_ent, P.ent + S.dn_ent, P.st + S.up_st, P.st + S.dn_st, S.Ddn, S.U,
-                            -S.t * 0x1p-47};
             // warps of one CTA work on rows of different sectors: each owns a
             // fixed slice of the shared buffer, long rows read from L2 instead
             const int64_t slice = P.smem_elems / nwarps;
             int2* buf = S.Ddn <= slice ? xs + (int64_t)warp * slice : nullptr;
+            const bool blk = S.dn_blk >= 0 && row_slots(S.Ddn) <= slice;
+            const SecView V{P.xg + S.voff, fp + S.voff, gp + S.voff, P.rp + S.up_rp, P.rp + S.dn_rp,
+                            P.ent + S.up_ent, P.ent + S.dn_ent, P.st + S.up_st, P.st + S.dn_st, S.Ddn, S.U,
+                            -S.t * 0x1p-47, blk ? P.bo + S.dn_blk : nullptr, blk ? P.bc + S.dn_blk : nullptr,
+                            P.be};
             double ap = 0.0, qq = 0.0, ff = 0.0;
             row_pass(V, r - P.rowoff[k], buf, __ldcg(&P.sst[k].beta), ap, qq, ff);
             ap = warp_sum(ap);
@@ -526,7 +559,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         const bool in_smem = D <= P.smem_elems;
         // per-warp row buffer for the global-memory path (rows of the fixed-point copy)
         const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
-        const bool rowbuf = !in_smem && Ddn * nwarps <= P.smem_elems;
+        // (row_slots(Ddn) per warp for the coloured down-hop table, else Ddn)
+        const bool blk = S.dn_blk >= 0 && row_slots(Ddn) * nwarps <= P.smem_elems;
+        const int64_t rstride = blk ? row_slots(Ddn) : Ddn;
+        const bool rowbuf = !in_smem && rstride * nwarps <= P.smem_elems;
         int2* X = in_smem ? xs : (P.xg + S.voff);
         double* f = P.f + S.voff;
         double* g = P.g + S.voff;
@@ -596,8 +632,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
                 }
             } else {
                 // global copy (L2): a warp per row (row_pass)
-                const SecView V{X, f, g, urp, drp, uent, dent, ust, dst, Ddn, S.U, scale};
-                int2* buf = rowbuf ? xs + (int64_t)warp * Ddn : nullptr;
+                const SecView V{X, f, g, urp, drp, uent, dent, ust, dst, Ddn, S.U, scale,
+                                blk ? P.bo + S.dn_blk : nullptr, blk ? P.bc + S.dn_blk : nullptr, P.be};
+                int2* buf = rowbuf ? xs + (int64_t)warp * rstride : nullptr;
                 for (int64_t u = warp; u < Dup; u += nwarps) row_pass(V, u, buf, beta, ap, qq, ff);
             }
             double sv[3] = {ap, qq, ff};
@@ -694,6 +731,9 @@ struct hubbard_batch {
     int32_t* d_rp = nullptr;
     uint32_t* d_ent = nullptr;
     uint32_t* d_st = nullptr;
+    int64_t* d_bo = nullptr;                   // row-table pools
+    int32_t* d_bc = nullptr;
+    uint16_t* d_be = nullptr;
     // schedule
     int64_t elems_per_cta = 1 << 14;
     int* d_tasks = nullptr;
@@ -716,10 +756,20 @@ namespace {
 struct Cached {
     int64_t rp_off, ent_off, st_off, D, W;
     double hops;   // mean hops per state
+    int64_t blk;   // first group of the row table in the block pools (-1: none)
+};
+
+// row tables are built for spins whose staged row could fit a warp's slice
+constexpr int64_t kRowTableMaxD = 4064;
+
+struct RowPools {
+    std::vector<int64_t> bo;
+    std::vector<int32_t> bc;
+    std::vector<uint16_t> be;
 };
 
 int batch_upload(hubbard_batch* B, const std::vector<int32_t>& rp, const std::vector<uint32_t>& ent,
-                 const std::vector<uint32_t>& st) {
+                 const std::vector<uint32_t>& st, const RowPools& rows) {
     auto up = [](auto** dst, const auto& v) -> int {
         using T = std::remove_reference_t<decltype(v[0])>;
         const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
@@ -733,6 +783,7 @@ int batch_upload(hubbard_batch* B, const std::vector<int32_t>& rp, const std::ve
     };
     int rc;
     if ((rc = up(&B->d_rp, rp)) || (rc = up(&B->d_ent, ent)) || (rc = up(&B->d_st, st))) return rc;
+    if ((rc = up(&B->d_bo, rows.bo)) || (rc = up(&B->d_bc, rows.bc)) || (rc = up(&B->d_be, rows.be))) return rc;
     return up(&B->d_sec, B->sec);
 }
 
@@ -741,6 +792,9 @@ void batch_free(hubbard_batch* B) {
     cudaFree(B->d_rp);
     cudaFree(B->d_ent);
     cudaFree(B->d_st);
+    cudaFree(B->d_bo);
+    cudaFree(B->d_bc);
+    cudaFree(B->d_be);
     cudaFree(B->d_tasks);
     cudaFree(B->d_swp);
     cudaFree(B->d_rowoff);
@@ -856,6 +910,7 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
     B->n = n_sectors;
     std::vector<int32_t> rp;
     std::vector<uint32_t> ent, st;
+    RowPools rows;
     std::map<std::tuple<int, std::vector<std::pair<int, int>>, int>, Cached> cache;
     auto spin = [&](int ns, const std::vector<std::pair<int, int>>& bl, int N) -> Cached {
         auto key = std::make_tuple(ns, bl, N);
@@ -864,7 +919,20 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
         SpinTables T;
         build_spin_tables(ns, N, bl, T);
         Cached c{(int64_t)rp.size(), (int64_t)ent.size(), (int64_t)st.size(), T.D, T.W,
-                 T.D ? (double)T.tgt.size() / (double)T.D : 0.0};
+                 T.D ? (double)T.tgt.size() / (double)T.D : 0.0, -1};
+        if (T.D <= kRowTableMaxD) {
+            RowBlocks rb;
+            build_row_blocks(T, 8, rb);
+            if (rb.narrow) {
+                const int64_t base = (int64_t)rows.be.size();  // a multiple of 128 entries: 16-byte aligned
+                c.blk = (int64_t)rows.bo.size();
+                for (size_t g = 0; g < rb.boff.size(); ++g) {
+                    rows.bo.push_back(base + rb.boff[g]);
+                    rows.bc.push_back(rb.bcnt[g]);
+                }
+                for (uint32_t e : rb.ent) rows.be.push_back((uint16_t)e);
+            }
+        }
         rp.insert(rp.end(), T.rowptr.begin(), T.rowptr.end());
         for (size_t k = 0; k < T.tgt.size(); ++k) ent.push_back(((uint32_t)T.tgt[k] << 1) | (T.sign[k] < 0 ? 1u : 0u));
         st.insert(st.end(), T.states.begin(), T.states.end());
@@ -913,6 +981,7 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
             s.dn_ent = cd.ent_off;
             s.up_st = cu.st_off;
             s.dn_st = cd.st_off;
+            s.dn_blk = cd.blk;
             s.t = d.t;
             s.U = d.U;
             B->sec.push_back(s);
@@ -925,7 +994,7 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
         delete B;
         return fail(HUB_ENOMEM, "host allocation (batch tables)");
     }
-    int rc = batch_upload(B, rp, ent, st);
+    int rc = batch_upload(B, rp, ent, st, rows);
     if (rc == HUB_OK && batch_grid(B, &B->smem_elems) < 0) rc = fail(HUB_ECUDA, "batch kernel occupancy");
     if (rc != HUB_OK) {
         std::string msg = hubbard_last_error();
@@ -1000,6 +1069,9 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     P.rp = B->d_rp;
     P.ent = B->d_ent;
     P.st = B->d_st;
+    P.bo = B->d_bo;
+    P.bc = B->d_bc;
+    P.be = B->d_be;
     P.v0 = v0_all;
     P.f = (double*)(ws + L.f);
     P.g = (double*)(ws + L.g);

@@ -218,69 +218,18 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
                 ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
     }
     d.sell_entries = total;
-    // SELL-32/8 for the row phase: per group, slots assigned by bank-conflict-free
-    // colouring for the element size the row phase will stage (16 bytes when a
-    // 16-byte-per-state row fits in shared memory, else 8, else 4), in blocks of
-    // 8 slots per lane, contiguous per lane.  Entry = staged slot index, top bit
-    // set for sign -1.  The staged row is followed by 32 zero slots starting at
-    // Dr = D rounded up to 32; a slot a lane does not use points at the zero slot
-    // of a bank group no other lane of its wavefront phase uses (so padding adds
-    // zero without a branch and without a conflict).
+    // SELL-32/8 for the row phase, coloured for the element size the row phase
+    // will stage (16 bytes when a 16-byte-per-state row fits in shared memory,
+    // else 8, else 4)
     const int64_t smem_budget = 220 * 1024;
     const int eb = ((T.D + 64) * 16 <= smem_budget) ? 16 : (((T.D + 64) * 8 <= smem_budget) ? 8 : 4);
-    const int ngroups = 128 / eb;
-    const int planes = std::min(32, ngroups);
-    const int64_t Dr = (T.D + 31) / 32 * 32;
-    const bool narrow = Dr + 32 <= 32767;            // 15-bit index + sign
-    const uint32_t negbit = narrow ? 0x8000u : 0x80000000u;
-    std::vector<int64_t> boff((size_t)groups);
-    std::vector<int32_t> bcnt((size_t)groups);
-    int64_t btotal = 0;
-    std::vector<SlotColouring> colours((size_t)groups);
-    for (int64_t g = 0; g < groups; ++g) {
-        std::vector<std::vector<int32_t>> lt;
-        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r)
-            lt.emplace_back(T.tgt.begin() + T.rowptr[(size_t)r], T.tgt.begin() + T.rowptr[(size_t)r + 1]);
-        colours[(size_t)g] = colour_group(lt, eb);
-        boff[(size_t)g] = btotal;
-        bcnt[(size_t)g] = (colours[(size_t)g].slots + 3) / 4;      // half-blocks of 4 slots
-        btotal += (int64_t)bcnt[(size_t)g] * 32 * 4;
-    }
-    std::vector<uint32_t> bent((size_t)std::max<int64_t>(btotal, 1), (uint32_t)Dr);
-    for (int64_t g = 0; g < groups; ++g) {
-        const SlotColouring& C = colours[(size_t)g];
-        const int nslot = bcnt[(size_t)g] * 4;
-        const int nfull = bcnt[(size_t)g] / 2;                        // blocks of 8 slots, then maybe one of 4
-        auto pos = [&](int l, int s) -> int64_t {
-            if (s < nfull * 8) return boff[(size_t)g] + ((int64_t)(s / 8) * 32 + l) * 8 + s % 8;
-            return boff[(size_t)g] + (int64_t)nfull * 32 * 8 + (int64_t)l * 4 + (s - nfull * 8);
-        };
-        // entry[lane][slot], -1 = padding
-        std::vector<std::vector<int64_t>> grid(32, std::vector<int64_t>((size_t)nslot, -1));
-        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) {
-            const int lane = (int)(r % 32);
-            for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
-                grid[(size_t)lane][(size_t)C.slot_of[(size_t)lane][(size_t)c]] = k;
-        }
-        for (int s = 0; s < nslot; ++s) {
-            for (int p0 = 0; p0 < 32; p0 += planes) {
-                std::vector<char> used((size_t)ngroups, 0);
-                for (int l = p0; l < p0 + planes; ++l) {
-                    const int64_t k = grid[(size_t)l][(size_t)s];
-                    if (k >= 0) used[(size_t)(T.tgt[(size_t)k] % ngroups)] = 1;
-                }
-                int freeg = 0;
-                while (freeg < ngroups && used[(size_t)freeg]) ++freeg;
-                if (freeg == ngroups) freeg = 0;          // cannot happen: a padded lane leaves a group free
-                for (int l = p0; l < p0 + planes; ++l) {
-                    const int64_t k = grid[(size_t)l][(size_t)s];
-                    const uint32_t e = k >= 0 ? ((uint32_t)T.tgt[(size_t)k] | (T.sign[(size_t)k] < 0 ? negbit : 0u))
-                                              : (uint32_t)(Dr + freeg);
-                    bent[(size_t)pos(l, s)] = e;
-                }
-            }
-        }
-    }
+    RowBlocks rb;
+    build_row_blocks(T, eb, rb);
+    const std::vector<int64_t>& boff = rb.boff;
+    const std::vector<int32_t>& bcnt = rb.bcnt;
+    const bool narrow = rb.narrow;
+    std::vector<uint32_t>& bent = rb.ent;
+    if (bent.empty()) bent.push_back(0u);
     // sign-split list: +1 targets first, then -1 targets, each ascending
     std::vector<int32_t> npos((size_t)T.D);
     std::vector<uint32_t> pnl(T.tgt.size());
@@ -405,6 +354,75 @@ int spin_tables(int device, int ns, const std::vector<std::pair<int, int>>& bl, 
     return HUB_OK;
 }
 }  // namespace
+
+// Row-phase table of one spin (SELL-32/8): per group of 32 states, slots
+// assigned by bank-conflict-free colouring for staged elements of eb bytes, in
+// blocks of 8 slots per lane, contiguous per lane.  Entry = staged slot index,
+// top bit set for sign -1.  The staged row is followed by 32 zero slots
+// starting at Dr = D rounded up to 32; a slot a lane does not use points at the
+// zero slot of a bank group no other lane of its wavefront phase uses (so
+// padding adds zero without a branch and without a conflict).  Every group
+// holds a multiple of 128 entries, so each starts 16-byte aligned.
+void build_row_blocks(const SpinTables& T, int eb, RowBlocks& out) {
+    const int ngroups = 128 / eb;
+    const int planes = std::min(32, ngroups);
+    const int64_t Dr = (T.D + 31) / 32 * 32;
+    const bool narrow = Dr + 32 <= 32767;            // 15-bit index + sign
+    out.narrow = narrow;
+    const uint32_t negbit = narrow ? 0x8000u : 0x80000000u;
+    const int64_t groups = (T.D + 31) / 32;
+    std::vector<int64_t>& boff = out.boff;
+    std::vector<int32_t>& bcnt = out.bcnt;
+    boff.assign((size_t)groups, 0);
+    bcnt.assign((size_t)groups, 0);
+    int64_t btotal = 0;
+    std::vector<SlotColouring> colours((size_t)groups);
+    for (int64_t g = 0; g < groups; ++g) {
+        std::vector<std::vector<int32_t>> lt;
+        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r)
+            lt.emplace_back(T.tgt.begin() + T.rowptr[(size_t)r], T.tgt.begin() + T.rowptr[(size_t)r + 1]);
+        colours[(size_t)g] = colour_group(lt, eb);
+        boff[(size_t)g] = btotal;
+        bcnt[(size_t)g] = (colours[(size_t)g].slots + 3) / 4;      // half-blocks of 4 slots
+        btotal += (int64_t)bcnt[(size_t)g] * 32 * 4;
+    }
+    std::vector<uint32_t>& bent = out.ent;
+    bent.assign((size_t)btotal, (uint32_t)Dr);
+    for (int64_t g = 0; g < groups; ++g) {
+        const SlotColouring& C = colours[(size_t)g];
+        const int nslot = bcnt[(size_t)g] * 4;
+        const int nfull = bcnt[(size_t)g] / 2;                        // blocks of 8 slots, then maybe one of 4
+        auto pos = [&](int l, int s) -> int64_t {
+            if (s < nfull * 8) return boff[(size_t)g] + ((int64_t)(s / 8) * 32 + l) * 8 + s % 8;
+            return boff[(size_t)g] + (int64_t)nfull * 32 * 8 + (int64_t)l * 4 + (s - nfull * 8);
+        };
+        // entry[lane][slot], -1 = padding
+        std::vector<std::vector<int64_t>> grid(32, std::vector<int64_t>((size_t)nslot, -1));
+        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) {
+            const int lane = (int)(r % 32);
+            for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
+                grid[(size_t)lane][(size_t)C.slot_of[(size_t)lane][(size_t)c]] = k;
+        }
+        for (int s = 0; s < nslot; ++s) {
+            for (int p0 = 0; p0 < 32; p0 += planes) {
+                std::vector<char> used((size_t)ngroups, 0);
+                for (int l = p0; l < p0 + planes; ++l) {
+                    const int64_t k = grid[(size_t)l][(size_t)s];
+                    if (k >= 0) used[(size_t)(T.tgt[(size_t)k] % ngroups)] = 1;
+                }
+                int freeg = 0;
+                while (freeg < ngroups && used[(size_t)freeg]) ++freeg;
+                if (freeg == ngroups) freeg = 0;          // cannot happen: a padded lane leaves a group free
+                for (int l = p0; l < p0 + planes; ++l) {
+                    const int64_t k = grid[(size_t)l][(size_t)s];
+                    const uint32_t e = k >= 0 ? ((uint32_t)T.tgt[(size_t)k] | (T.sign[(size_t)k] < 0 ? negbit : 0u))
+                                              : (uint32_t)(Dr + freeg);
+                    bent[(size_t)pos(l, s)] = e;
+                }
+            }
+        }
+    }
+}
 
 }  // namespace hub
 

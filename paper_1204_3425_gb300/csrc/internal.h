@@ -36,6 +36,17 @@ struct SpinTables {
 // Builds the basis and hopping table of one spin species.
 void build_spin_tables(int ns, int n, const std::vector<std::pair<int, int>>& bonds, SpinTables& out);
 
+// Row-phase hop table of one spin (the SELL-32/8 layout of DevSpin::blk_off /
+// blk_cnt / ent16 / ent32), its slots coloured for staged elements of eb bytes
+// (4, 8 or 16).  narrow: entries fit 16 bits (15-bit index, sign in bit 15).
+struct RowBlocks {
+    std::vector<int64_t> boff;       // [groups] first entry of each group
+    std::vector<int32_t> bcnt;       // [groups] half-blocks of 4 slots
+    std::vector<uint32_t> ent;       // every group a multiple of 128 entries
+    bool narrow = false;
+};
+void build_row_blocks(const SpinTables& T, int eb, RowBlocks& out);
+
 // Device copy of one spin's tables.
 struct DevSpin {
     uint32_t* states = nullptr;      // [D]
