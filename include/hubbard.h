@@ -113,6 +113,25 @@ int hubbard_export_tables(hubbard_t H, int spin, uint32_t* states, int32_t* rowp
 int hubbard_host_spin_tables(int Ns, const int32_t* bonds, int n_bonds, int N, int64_t* D, int64_t* nnz,
                              uint32_t* states, int32_t* rowptr, int32_t* tgt, int8_t* sign);
 
+/* Host-only copy of the row-phase hop table of one spin (the layout the
+ * down-hop gathers of hubbard_apply and of the batched solver walk; Sec. 4.3
+ * restated for shared-memory staging), for testing its invariants without a
+ * GPU.  States are taken in groups of 32 (group g = states 32g .. 32g+31, one
+ * per lane).  Group g holds bcnt[g] half-blocks of 4 slots per lane starting at
+ * entry boff[g]: bcnt[g] / 2 blocks of 8 slots (slot s < 8 * (bcnt[g] / 2) of
+ * lane l at boff[g] + ((s / 8) * 32 + l) * 8 + s % 8), then, when bcnt[g] is
+ * odd, one block of 4 (slot s of lane l at boff[g] + (bcnt[g] / 2) * 256 +
+ * l * 4 + s - 8 * (bcnt[g] / 2)).  Entry = staged slot index in the low 15 bits
+ * (narrow) or 31 bits, sign -1 in the bit above; the hops of a state are its
+ * entries with index < D, the others point at zero slots (index >= D rounded
+ * up to 32).  Slots are coloured for staged elements of elem_bytes (4, 8 or 16)
+ * bytes: within every wavefront phase (min(32, 128 / elem_bytes) lanes) the
+ * entries of one slot have distinct index mod 128 / elem_bytes (bank group).
+ * Call once with boff/bcnt/ent NULL to get *groups and *entries, then with
+ * host buffers of those sizes.  Same argument rules as hubbard_host_spin_tables. */
+int hubbard_host_row_table(int Ns, const int32_t* bonds, int n_bonds, int N, int elem_bytes, int64_t* groups,
+                           int64_t* entries, int* narrow, int64_t* boff, int32_t* bcnt, uint32_t* ent);
+
 /* ---------------------------------------------------------------------------
  * w = H v  (Sec. 4.3: the fused up-hop, down-hop and interaction kernel,
  * Algorithms 2-4, restated for sm_103a).

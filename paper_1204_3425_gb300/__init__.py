@@ -52,6 +52,8 @@ SIGNATURES = {
     "lanczos_workspace_bytes": (SZ, [P, ctypes.c_int]),
     "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P]),
     "hubbard_host_spin_tables": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]),
+    "hubbard_host_row_table": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P,
+                                              P, P]),
     "hubbard_kernel_launches": (ctypes.c_uint64, []),
     "lanczos_refined_workspace_bytes": (SZ, [P]),
     "hubbard_batch_create": (ctypes.c_int, [P, ctypes.c_int, P]),
@@ -179,6 +181,22 @@ def hubbard_host_spin_tables(ns, bonds, n):
     _check(lib.hubbard_host_spin_tables(int(ns), bp, arr.size // 2, int(n), None, None, states.ctypes.data,
                                         rowptr.ctypes.data, tgt.ctypes.data, sign.ctypes.data))
     return states, rowptr, tgt[:nnz.value], sign[:nnz.value]
+
+
+def hubbard_host_row_table(ns, bonds, n, elem_bytes):
+    """Host-only row-phase hop table of one spin: (boff, bcnt, ent, narrow)."""
+    lib = load_library()
+    arr = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+    bp = arr.ctypes.data if arr.size else None
+    G, E, nar = I64(), I64(), ctypes.c_int()
+    _check(lib.hubbard_host_row_table(int(ns), bp, arr.size // 2, int(n), int(elem_bytes), ctypes.byref(G),
+                                      ctypes.byref(E), ctypes.byref(nar), None, None, None))
+    boff = np.zeros(max(G.value, 1), dtype=np.int64)
+    bcnt = np.zeros(max(G.value, 1), dtype=np.int32)
+    ent = np.zeros(max(E.value, 1), dtype=np.uint32)
+    _check(lib.hubbard_host_row_table(int(ns), bp, arr.size // 2, int(n), int(elem_bytes), None, None, None,
+                                      boff.ctypes.data, bcnt.ctypes.data, ent.ctypes.data))
+    return boff[:G.value], bcnt[:G.value], ent[:E.value], bool(nar.value)
 
 
 def hubbard_apply(H, v, w, stream=None):

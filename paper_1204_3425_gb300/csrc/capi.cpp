@@ -481,6 +481,30 @@ int hubbard_host_spin_tables(int Ns, const int32_t* bonds, int n_bonds, int N, i
     return HUB_OK;
 }
 
+int hubbard_host_row_table(int Ns, const int32_t* bonds, int n_bonds, int N, int elem_bytes, int64_t* groups,
+                           int64_t* entries, int* narrow, int64_t* boff, int32_t* bcnt, uint32_t* ent) {
+    clear_error();
+    if (elem_bytes != 4 && elem_bytes != 8 && elem_bytes != 16) return fail(HUB_EINVAL, "elem_bytes must be 4, 8 or 16");
+    std::vector<std::pair<int, int>> bl;
+    int rc = check_lattice(Ns, bonds, n_bonds, N, bl);
+    if (rc) return rc;
+    SpinTables T;
+    RowBlocks rb;
+    try {
+        build_spin_tables(Ns, N, bl, T);
+        build_row_blocks(T, elem_bytes, rb);
+    } catch (const std::bad_alloc&) {
+        return fail(HUB_ENOMEM, "host allocation (tables)");
+    }
+    if (groups) *groups = (int64_t)rb.boff.size();
+    if (entries) *entries = (int64_t)rb.ent.size();
+    if (narrow) *narrow = rb.narrow ? 1 : 0;
+    if (boff) std::memcpy(boff, rb.boff.data(), rb.boff.size() * sizeof(int64_t));
+    if (bcnt) std::memcpy(bcnt, rb.bcnt.data(), rb.bcnt.size() * sizeof(int32_t));
+    if (ent) std::memcpy(ent, rb.ent.data(), rb.ent.size() * sizeof(uint32_t));
+    return HUB_OK;
+}
+
 int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn, double t, double U,
                           hubbard_t* out) {
     clear_error();
