@@ -68,11 +68,6 @@ void free_spin_dev(DevSpin& d) {
     cudaFree(d.states);
     cudaFree(d.rowptr);
     cudaFree(d.ent);
-    cudaFree(d.ell);
-    cudaFree(d.cnt);
-    cudaFree(d.sell_off);
-    cudaFree(d.sell_cnt);
-    cudaFree(d.sell_ent);
     cudaFree(d.blk_off);
     cudaFree(d.blk_cnt);
     cudaFree(d.ent16);
@@ -191,33 +186,6 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     std::vector<uint32_t> ent(T.tgt.size());
     for (size_t k = 0; k < T.tgt.size(); ++k)
         ent[k] = ((uint32_t)T.tgt[k] << 1) | (T.sign[k] < 0 ? 1u : 0u);
-    std::vector<int32_t> cnt((size_t)T.D);
-    std::vector<uint32_t> ell((size_t)T.D * (size_t)std::max(T.W, 1), 0xFFFFFFFFu);
-    for (int64_t r = 0; r < T.D; ++r) {
-        cnt[(size_t)r] = T.rowptr[(size_t)r + 1] - T.rowptr[(size_t)r];
-        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
-            ell[(size_t)c * (size_t)T.D + (size_t)r] = ent[(size_t)k];
-    }
-    // warp-sliced ELL: group g = states 32g .. 32g+31, slots = max hops in the group
-    const int64_t groups = (T.D + 31) / 32;
-    std::vector<int64_t> soff((size_t)groups);
-    std::vector<int32_t> scnt((size_t)groups);
-    int64_t total = 0;
-    for (int64_t g = 0; g < groups; ++g) {
-        int32_t m = 0;
-        for (int64_t r = 32 * g; r < std::min<int64_t>(T.D, 32 * g + 32); ++r) m = std::max(m, cnt[(size_t)r]);
-        soff[(size_t)g] = total;
-        scnt[(size_t)g] = m;
-        total += (int64_t)m * 32;
-    }
-    std::vector<uint32_t> sent((size_t)std::max<int64_t>(total, 1), 0u);   // padding: target 0, weight 0
-    for (int64_t r = 0; r < T.D; ++r) {
-        const int64_t g = r / 32, lane = r % 32;
-        for (int32_t k = T.rowptr[(size_t)r], c = 0; k < T.rowptr[(size_t)r + 1]; ++k, ++c)
-            sent[(size_t)(soff[(size_t)g] + (int64_t)c * 32 + lane)] =
-                ((uint32_t)T.tgt[(size_t)k] << 2) | (T.sign[(size_t)k] < 0 ? 3u : 1u);
-    }
-    d.sell_entries = total;
     // SELL-32/8 for the row phase, coloured for the element size the row phase
     // will stage (16 bytes when a 16-byte-per-state row fits in shared memory,
     // else 8, else 4)
@@ -254,14 +222,9 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     } else {
         if ((rc = upload(&d.ent32, bent.data(), bent.size()))) return rc;
     }
-    if ((rc = upload(&d.sell_off, soff.data(), soff.size()))) return rc;
-    if ((rc = upload(&d.sell_cnt, scnt.data(), scnt.size()))) return rc;
-    if ((rc = upload(&d.sell_ent, sent.data(), sent.size()))) return rc;
     if ((rc = upload(&d.states, T.states.data(), T.states.size()))) return rc;
     if ((rc = upload(&d.rowptr, T.rowptr.data(), T.rowptr.size()))) return rc;
     if ((rc = upload(&d.ent, ent.data(), ent.size()))) return rc;
-    if ((rc = upload(&d.ell, ell.data(), ell.size()))) return rc;
-    if ((rc = upload(&d.cnt, cnt.data(), cnt.size()))) return rc;
     return HUB_OK;
 }
 

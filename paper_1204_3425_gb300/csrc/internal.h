@@ -52,15 +52,6 @@ struct DevSpin {
     uint32_t* states = nullptr;      // [D]
     int32_t* rowptr = nullptr;       // [D+1]
     uint32_t* ent = nullptr;         // [nnz] packed (target << 1) | (sign < 0)
-    uint32_t* ell = nullptr;         // [W * D] column-major ELL, packed as ent; pad = 0xFFFFFFFF
-    int32_t* cnt = nullptr;          // [D] hops per state
-    // warp-sliced ELL ("SELL-32"): states in groups of 32 (one per lane);
-    // group g holds sell_cnt[g] slots of 32 entries at sell_off[g]; entry =
-    // (target << 2) | code, code 1 = +1, 3 = -1, 0 = padding (weight 0).
-    int64_t* sell_off = nullptr;     // [groups]
-    int32_t* sell_cnt = nullptr;     // [groups]
-    uint32_t* sell_ent = nullptr;    // [sum cnt * 32]
-    int64_t sell_entries = 0;
     // the row-phase table in blocks of 8 slots per lane ("SELL-32/8"): group g
     // starts at blk_off[g] (in entries) and has blk_cnt[g] half-blocks of 4
     // slots: blk_cnt[g] / 2 blocks of 8 (block b of lane l holds slots
