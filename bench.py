@@ -294,6 +294,10 @@ def run_ours(args):
     line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sq4x4_n8_8_U8_f64":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if "batch" in line:
+            line["batch"]["cpu_baseline"] = solves_cpu_baseline("batch", args.batch_sectors, args.cpu_seconds / 2)
+        if "serve" in line:
+            line["serve"]["cpu_baseline"] = solves_cpu_baseline("serve", args.serve, args.cpu_seconds / 2)
     H.close()
     if rank == 0:
         print(json.dumps(line))
@@ -462,6 +466,31 @@ def cpu_baseline(budget_s=15.0):
             "sample": f"{len(times)} Kronecker-sum H*v calls on the 4x4 (8,8) sector (plain C, OpenMP, "
                       f"{prev} threads), median {per:.3f} s each; table build {build_s:.1f} s not timed",
             "value_1_thread": nbytes / per1 / 1e9, "hv_s_1_thread": per1, "hv_s": per}
+
+
+def solves_cpu_baseline(kind, count, budget_s):
+    """The oracle's matrix-free Lanczos (plain-C Kronecker-sum H*v, OpenMP) over the
+    same request list, one request after another in list order, until budget_s of
+    solving is spent (the request running at the deadline finishes); table builds
+    are not timed, as the GPU figures exclude sector creation."""
+    from oracle.kron import KronHamiltonian, lanczos_matrix_free, set_threads
+    from workload import batch_sectors, lattice_by_name, serve_requests, start_vector
+    reqs = batch_sectors(count, seed=1234) if kind == "batch" else serve_requests(count, rate=500.0, seed=1234)
+    cores = set_threads(0)
+    solve_s, n, elems, iters = 0.0, 0, 0, 0
+    while n < len(reqs) and (n == 0 or solve_s < budget_s):
+        r = reqs[n]
+        ns, bonds = lattice_by_name(r["lattice"])
+        K = KronHamiltonian(ns, bonds, r["nup"], r["ndn"], r["t"], r["U"])
+        v0 = start_vector(K.D, seed=r["seed"])
+        t0 = time.perf_counter()
+        res = lanczos_matrix_free(K, v0, min(K.D, 1000), tol=1e-10, inplace=True)
+        solve_s += time.perf_counter() - t0
+        n, elems, iters = n + 1, elems + K.D, iters + res["iters"]
+    return {"value": n / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {n} of the {len(reqs)} {kind} requests in list order ({elems} elements, "
+                      f"{iters} Lanczos steps to rho < 1e-10), one after another; {solve_s:.1f} s of solving "
+                      f"on {cores} OpenMP threads"}
 
 
 def run_reference(args):
