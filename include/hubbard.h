@@ -247,6 +247,9 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
  * Breakdown (beta_{m+1} <= 1e-13 * max(1, max|a|, max b)) counts as
  * converged.  Returns HUB_ENOTCONV (with the best energy in *out) when
  * max_iters is reached with tol > 0 and rho >= tol.  Synchronises `stream`.
+ * Each new vector f_{j+1} = (g - a_j f_j) / b_{j+1} is completed by the next
+ * step's H*v while it stages its rows (same roundings as the separate update
+ * of hubbard_lanczos_step), so the workspace holds no finished vector on return.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double energy;
