@@ -7,9 +7,12 @@
 //  * sectors above a size threshold advance in lock step, one Lanczos step per
 //    grid-synchronous sweep whose phases spread the rows of every active
 //    sector over all warps (sweep_solve);
-//  * the rest are tasks of one CTA each, walked from a static per-CTA list
-//    (largest work first); a task that fits keeps the fixed-point copy of its
-//    Lanczos vector in shared memory.
+//  * the rest are tasks of one CTA each, claimed by the CTAs from a global
+//    counter (largest work first); a task that fits keeps the fixed-point copy
+//    of its Lanczos vector in shared memory.
+// Rows staged in shared memory take their down-hops from the coloured row
+// table of the single-sector kernels (row_blocks.cuh), built here for 8-byte
+// slots.
 // Grid barriers are bounded (a timeout sets an error word; later waits fail
 // fast).  Every reduction is summed in a fixed order, so the result of a
 // sector does not depend on which other sectors share the launch.
