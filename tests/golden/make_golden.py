@@ -6,6 +6,7 @@ inputs from `workload`; nothing is taken from the CUDA path.
     python tests/golden/make_golden.py ring8     # ring 8, (4,4), U=4: dense + Lanczos a/b
     python tests/golden/make_golden.py sq4x4     # 4x4, (8,8), U=8: matrix-free Lanczos
     python tests/golden/make_golden.py ring18 --U 4
+    python tests/golden/make_golden.py ring18-bethe --U 2   # exact solution of the ring
 """
 import argparse
 import datetime
@@ -21,6 +22,7 @@ sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 import numpy as np  # noqa: E402
 
 from oracle.basis import Sector  # noqa: E402
+from oracle.bethe import lieb_wu_ground_energy  # noqa: E402
 from oracle.kron import KronHamiltonian, lanczos_matrix_free  # noqa: E402
 from oracle.lanczos import ground_energy_dense, lanczos_plain  # noqa: E402
 from workload import lattice_by_name, start_vector  # noqa: E402
@@ -74,9 +76,18 @@ def _matrix_free(name, nup, ndn, U, tol, max_iter, fname):
         seconds=time.time() - t0, meta=_meta(" ".join(sys.argv))))
 
 
+def ring18_bethe(U):
+    ns, _ = lattice_by_name("ring18")
+    e = lieb_wu_ground_energy(ns, 9, 9, 1.0, U)
+    _write(f"ring18_n9_9_U{U:g}.json", dict(
+        lattice="ring18", ns=ns, nup=9, ndn=9, t=1.0, U=U, dim=48620 * 48620, e0=e,
+        method="Lieb-Wu Bethe-ansatz equations (oracle/bethe.py), residual <= 1e-11",
+        meta=_meta(" ".join(sys.argv))))
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("which", choices=["ring8", "sq4x4", "ring18"])
+    ap.add_argument("which", choices=["ring8", "sq4x4", "ring18", "ring18-bethe"])
     ap.add_argument("--U", type=float, default=None)
     a = ap.parse_args()
     if a.which == "ring8":
@@ -84,9 +95,11 @@ def main():
     elif a.which == "sq4x4":
         U = 8.0 if a.U is None else a.U
         _matrix_free("sq4x4", 8, 8, U, 1e-12, 600, f"sq4x4_n8_8_U{U:g}.json")
-    else:
+    elif a.which == "ring18":
         U = 4.0 if a.U is None else a.U
         _matrix_free("ring18", 9, 9, U, 1e-11, 600, f"ring18_n9_9_U{U:g}.json")
+    else:
+        ring18_bethe(2.0 if a.U is None else a.U)
 
 
 if __name__ == "__main__":

@@ -5,7 +5,9 @@
 * the binary32 + binary64-refined ground state against the binary64 Lanczos
   on the same GPU and seed (1e-9 relative), and against the oracle's stored
   energy when tests/golden/ring18_n9_9_U4.json exists;
-* at U = 8, the refined ground state against the oracle (ring18_n9_9_U8.json).
+* at U = 8, the refined ground state against the oracle (ring18_n9_9_U8.json);
+* at U = 2, the refined ground state against the exact solution of the ring
+  (Lieb-Wu Bethe ansatz, ring18_n9_9_U2.json).
 """
 import json
 import os
@@ -82,16 +84,18 @@ def test_ring18_refined_vs_f64(ring18):
         assert abs(r64["energy"] - e) <= 1e-9 * abs(e)
 
 
-def test_ring18_u8_refined_vs_oracle(ring18):
-    """U = 8 (stronger coupling, 258 oracle iterations): binary32 Lanczos + binary64
-    refinement against the oracle's matrix-free Lanczos energy."""
+@pytest.mark.parametrize("U", [8.0, 2.0])
+def test_ring18_refined_vs_stored_energy(ring18, U):
+    """U = 8 (stronger coupling, 258 oracle iterations; the oracle's matrix-free
+    Lanczos energy) and U = 2 (the Bethe-ansatz energy): binary32 Lanczos +
+    binary64 refinement."""
     _, _, vd = ring18
-    path = os.path.join(GOLD, "ring18_n9_9_U8.json")
+    path = os.path.join(GOLD, f"ring18_n9_9_U{U:g}.json")
     if not os.path.exists(path):
-        pytest.skip("no U=8 golden value")
+        pytest.skip(f"no U={U:g} stored value")
     e = json.load(open(path))["e0"]
     ns, bonds = lattice_by_name("ring18")
-    H8 = hub.hubbard_sector_create(ns, bonds, 9, 9, 1.0, 8.0)
+    H8 = hub.hubbard_sector_create(ns, bonds, 9, 9, 1.0, U)
     try:
         r = hub.lanczos_ground_state_refined(H8, vd, 1000, 1e-10)
         assert r["status"] == hub.HUB_OK, r

@@ -10,6 +10,7 @@ import scipy.sparse as sp
 
 from oracle import closed_forms as cf
 from oracle.basis import Sector, sector_dim, spin_states
+from oracle.bethe import lieb_wu_ground_energy
 from oracle.kron import KronHamiltonian
 from oracle.lanczos import ground_energy_dense, lanczos_full, lanczos_plain
 from workload import dimer, ring, square, start_vector, splitmix64
@@ -230,6 +231,34 @@ def test_golden_ring8_consistent():
     g = json.load(open(os.path.join(GOLD, "ring8_n4_4_U4.json")))
     assert g["e0_dense"] == pytest.approx(-4.603526299989137, abs=1e-12)
     assert g["lanczos_energy"] == pytest.approx(g["e0_dense"], rel=1e-12)
+
+
+# ---- Sec. 1: the exact solution of the ring (Lieb-Wu Bethe ansatz) ----------
+BETHE_SMALL = [(4, 1, 1, 1.0, 4.0), (4, 2, 2, 1.0, 4.0), (6, 3, 3, 1.0, 4.0), (6, 3, 2, 1.0, 5.0),
+               (7, 3, 3, 1.0, 2.0), (8, 3, 3, 1.0, 6.0), (6, 1, 1, 1.0, 1.0), (8, 4, 4, 1.0, 4.0),
+               (8, 4, 4, 0.7, 3.0), (10, 3, 3, 1.0, 4.0), (10, 5, 5, 1.0, 8.0), (9, 4, 3, 1.0, 2.5)]
+
+
+@pytest.mark.parametrize("L,nup,ndn,t,U", BETHE_SMALL)
+def test_bethe_ansatz_matches_diagonalisation(L, nup, ndn, t, U):
+    """The Lieb-Wu equations against diagonalisation of the explicit H."""
+    assert lieb_wu_ground_energy(L, nup, ndn, t, U) == pytest.approx(e0(L, ring(L), nup, ndn, t, U),
+                                                                      rel=1e-11, abs=1e-11)
+
+
+def test_bethe_ansatz_open_shell_is_outside_its_class():
+    # two electrons of each spin on 6 sites: the consecutive-quantum-number
+    # states miss the ground state (so the pins above are not vacuous)
+    assert lieb_wu_ground_energy(6, 2, 2, 1.0, 3.0) > e0(6, ring(6), 2, 2, 1.0, 3.0) + 0.1
+
+
+@pytest.mark.parametrize("U", [4.0, 8.0])
+def test_ring18_stored_energies_match_bethe_ansatz(U):
+    """The stored 18-site energies (the oracle's matrix-free Lanczos on D = 2.4e9)
+    against the exact solution."""
+    import json
+    g = json.load(open(os.path.join(GOLD, f"ring18_n9_9_U{U:g}.json")))
+    assert g["e0"] == pytest.approx(lieb_wu_ground_energy(18, 9, 9, 1.0, U), rel=1e-12)
 
 
 # ---- seeded inputs ----------------------------------------------------------
