@@ -79,11 +79,13 @@ def _solve(L, N, M, u, I, J):
 
 def lieb_wu_ground_energy(L, n_up, n_dn, t=1.0, U=0.0, max_residual=1e-11):
     """Lowest energy over the consecutive-quantum-number states of the ring with
-    L sites, n_up + n_dn electrons; U > 0.  Raises ValueError when no candidate
-    solves the equations to max_residual."""
+    L sites, n_up + n_dn <= L electrons; U > 0.  Raises ValueError when no
+    candidate solves the equations to max_residual."""
     if not U > 0.0 or not t > 0.0:
         raise ValueError("the logarithmic equations need U > 0 and t > 0")
     N, M = n_up + n_dn, min(n_up, n_dn)
+    if N > L:
+        raise ValueError("more electrons than sites: use particle-hole symmetry first")
     if N == 0:
         return 0.0
     u = U / (4.0 * t)

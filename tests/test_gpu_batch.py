@@ -145,13 +145,27 @@ def test_batch_full_config(dev):
     for i in rng.choice(small, 40, replace=False):
         e = _oracle(specs[i])
         assert abs(res[i]["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (i, specs[i][2:], res[i], e)
-    # the largest sectors against the single-sector GPU path
+    # the largest sectors (853 776 elements) against the oracle's matrix-free
+    # Lanczos and against the single-sector GPU path
+    from oracle.kron import KronHamiltonian, lanczos_matrix_free
     big = sorted(range(len(specs)), key=lambda i: -math.comb(specs[i][0], specs[i][2]) * math.comb(specs[i][0], specs[i][3]))[:3]
     for i in big:
         ns, bonds, nup, ndn, t, U = specs[i]
+        K = KronHamiltonian(ns, bonds, nup, ndn, t, U)
+        eo = lanczos_matrix_free(K, start_vector(K.D, seed=reqs[i]["seed"]), MAXIT, tol=1e-11)["energy"]
+        assert abs(res[i]["energy"] - eo) <= 1e-9 * max(1.0, abs(eo)), (i, specs[i][2:], res[i], eo)
         H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
         r1 = hub.lanczos_ground_state(H, torch.from_numpy(start_vector(H.D, seed=reqs[i]["seed"])).to(dev), MAXIT, TOL)
         assert abs(r1["energy"] - res[i]["energy"]) <= 1e-9 * max(1.0, abs(r1["energy"]))
+        H.close()
+    # every ring sector of a closed-shell filling against the exact solution (Bethe ansatz)
+    from oracle.bethe import lieb_wu_ground_energy
+    rings = [i for i, r in enumerate(reqs) if r["lattice"].startswith("ring") and r["nup"] == r["ndn"]
+             and (r["nup"] % 2 == 1 or 2 * r["nup"] == r["ns"]) and 2 * r["nup"] <= r["ns"] and r["U"] > 0.05]
+    for i in rings[:60]:
+        ns, bonds, nup, ndn, t, U = specs[i]
+        eb = lieb_wu_ground_energy(ns, nup, ndn, t, U)
+        assert abs(res[i]["energy"] - eb) <= 1e-9 * max(1.0, abs(eb)), (i, reqs[i], res[i], eb)
 
 
 def test_bounded_wait_times_out_and_context_survives(dev):
