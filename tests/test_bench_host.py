@@ -55,3 +55,12 @@ def test_reference_arm_other_ranks_do_nothing(capsys, monkeypatch):
         steps, warmup = 1, 0
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+@pytest.mark.parametrize("kind,count", [("batch", 2048), ("serve", 400)])
+def test_solves_cpu_baseline_reports_its_sample(kind, count):
+    """The batch and serving CPU baselines solve a prefix of the same request
+    list with the oracle and say how much they solved."""
+    r = bench.solves_cpu_baseline(kind, count, 0.05)
+    assert r["kind"] == "oracle" and r["unit"] == "solves/s" and r["value"] > 0 and r["cores"] >= 1
+    assert f"of the {count} {kind} requests in list order" in r["sample"]
