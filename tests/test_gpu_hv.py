@@ -1,8 +1,10 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances:
   * tables: bit-exact;
-  * binary64 H*v: max-abs error <= 1e-12 * |v|_2 * max(1, |t|);
+  * binary64 H*v: max-abs error <= 1e-12 * |v|_2 * max(1, |t|) (the hop sums are
+    exact on a grid of 2^-48 max|v|, so the error is at most (W_up + W_dn + 1)
+    grid steps times |t| plus one rounding of the result, far below this);
   * binary32 H*v: max-abs error <= 4e-7 * (W_up + W_dn + 1) * max(|t|, |U| Ns, 1) * max|v|;
   * ground-state energy: relative error <= 1e-9.
 """
