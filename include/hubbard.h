@@ -147,8 +147,10 @@ int hubbard_host_row_table(int Ns, const int32_t* bonds, int n_bonds, int N, int
  * ------------------------------------------------------------------------- */
 int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 
-/* Same as hubbard_apply, reference kernel: one thread per element, native
- * arithmetic of `dtype` (binary64 DADD/DFMA for HUB_F64), no workspace.
+/* Same as hubbard_apply, reference kernel: one thread per element and native
+ * arithmetic of `dtype` (binary64 DADD/DFMA for HUB_F64), the paper's own
+ * kernel organisation (Sec. 4.3, Algorithms 2-4: each thread gathers its
+ * element's up- and down-hops and adds the interaction), no workspace.
  * Kept as the parity anchor for the fast path. */
 int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 
@@ -164,7 +166,8 @@ int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void
  * fixed order (binary32) or exactly (binary64 fixed point). */
 int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols);
 
-/* Autotuner for the schedule above: times three hubbard_apply calls (after a
+/* Autotuner for the schedule above (the paper tunes elements per thread by
+ * hand, Sec. 4.3): times three hubbard_apply calls (after a
  * warm one) for every vec_rows x vec_cols in {1, 2 (, 4 for binary32)} and
  * ctas_rows in {1, 2} on the caller's v, w (device, dtype, as hubbard_apply;
  * w is overwritten), keeps the fastest on the handle and writes it to
