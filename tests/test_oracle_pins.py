@@ -246,6 +246,15 @@ def test_bethe_ansatz_matches_diagonalisation(L, nup, ndn, t, U):
                                                                       rel=1e-11, abs=1e-11)
 
 
+@pytest.mark.parametrize("L,n", [(8, 3), (8, 4), (9, 4), (12, 5), (18, 9), (18, 8)])
+def test_bethe_ansatz_polarised_is_free_fermions(L, n):
+    """One spin species only (M = 0): the equations decouple to k = 2 pi I / L and
+    the energy is that of free fermions on the ring, for any U."""
+    ef = cf.free_energy(L, ring(L), n, 0, 1.0)
+    for U in (0.5, 7.0):
+        assert lieb_wu_ground_energy(L, n, 0, 1.0, U) == pytest.approx(ef, rel=1e-13, abs=1e-13)
+
+
 def test_bethe_ansatz_open_shell_is_outside_its_class():
     # two electrons of each spin on 6 sites: the consecutive-quantum-number
     # states miss the ground state (so the pins above are not vacuous)
