@@ -255,6 +255,24 @@ def test_bethe_ansatz_polarised_is_free_fermions(L, n):
         assert lieb_wu_ground_energy(L, n, 0, 1.0, U) == pytest.approx(ef, rel=1e-13, abs=1e-13)
 
 
+def test_planted_bethe_parity_error_is_caught(monkeypatch):
+    """A plausible mistake in the Bethe-ansatz oracle (the spin quantum numbers'
+    parity rule inverted) fails the dense-diagonalisation pin."""
+    import oracle.bethe as ob
+    real = ob._consecutive
+
+    def flipped(n, half):
+        # ring 8, N = 8, M = 4: the sets of size M are the spin quantum numbers J
+        return real(n, (not half) if n == 4 else half)
+
+    monkeypatch.setattr(ob, "_consecutive", flipped)
+    try:
+        e_wrong = ob.lieb_wu_ground_energy(8, 4, 4, 1.0, 4.0)
+    except ValueError:
+        return                                           # no root at all: caught as well
+    assert abs(e_wrong - e0(8, ring(8), 4, 4, 1.0, 4.0)) > 1e-3
+
+
 def test_bethe_ansatz_open_shell_is_outside_its_class():
     # two electrons of each spin on 6 sites: the consecutive-quantum-number
     # states miss the ground state (so the pins above are not vacuous)
