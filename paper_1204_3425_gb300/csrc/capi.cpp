@@ -725,9 +725,11 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
 // <g, g> (near breakdown), or the kernel path cannot fuse, g - a_j f is formed
 // and its norm taken explicitly.  *pending (may be null when normalise) tells
 // how g is left:
-//   true : g = H f - beta_j g; finish with launch_axpy_scale(-a_j, 1/beta_{j+1})
+//   true : g = H f - beta_j g; finish with launch_axpy_scale(-a_j, 1/beta_{j+1}),
+//          or pass that update as `upd` to the next step, whose row phase applies it
 //   false: g = H f - beta_j g - a_j f; finish with launch_scale(1/beta_{j+1})
-// Both finishes round as axpy then scale, so either leaves the same f_{j+1}.
+// Every finish rounds as axpy then scale, so each leaves the same f_{j+1}.
+// upd (may be null): the previous step's pending update, applied to f first.
 static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
                              double* alpha, double* beta_next, bool normalise, int fixed_emax,
                              bool* pending = nullptr, const RowUpdate* upd = nullptr) {
