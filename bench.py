@@ -294,10 +294,10 @@ def run_ours(args):
     line.update(extra)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and args.workload == "sq4x4_n8_8_U8_f64":
         line["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
-        if "batch" in line:
-            line["batch"]["cpu_baseline"] = solves_cpu_baseline("batch", args.batch_sectors, args.cpu_seconds / 2)
-        if "serve" in line:
-            line["serve"]["cpu_baseline"] = solves_cpu_baseline("serve", args.serve, args.cpu_seconds / 2)
+        attach_solve_baselines(line, args.batch_sectors, args.serve, args.cpu_seconds / 2)
+    for key in ("batch", "serve"):
+        if key in line:
+            line[key].pop("_energies", None)
     H.close()
     if rank == 0:
         print(json.dumps(line))
@@ -417,7 +417,8 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune
     ok = sum(1 for r in res if r["status"] == 0)
     return dict(sectors=count, ms=ms, solves_per_s=ok / (ms * 1e-3), converged=ok, elems_per_cta=chosen,
                 autotune_s=tune_s, create_s=create_s, iters_total=sum(r["iters"] for r in res),
-                launches_per_batch=1, timed="CUDA graph replay", tol="rho < 1e-10 max(1,|theta|)")
+                launches_per_batch=1, timed="CUDA graph replay", tol="rho < 1e-10 max(1,|theta|)",
+                _energies=[r["energy"] if r["status"] == 0 else None for r in res])
 
 
 def bench_serve(n):
@@ -430,6 +431,7 @@ def bench_serve(n):
     srv.stop()
     st["converged"] = sum(1 for r in reqs if r.result and r.result["status"] == 0)
     st["rate_req_per_s"] = 500.0
+    st["_energies"] = [r.result["energy"] if r.result and r.result["status"] == 0 else None for r in reqs]
     return st
 
 
@@ -483,7 +485,7 @@ def solves_cpu_baseline(kind, count, budget_s):
     from workload import batch_sectors, lattice_by_name, serve_requests, start_vector
     reqs = batch_sectors(count, seed=1234) if kind == "batch" else serve_requests(count, rate=500.0, seed=1234)
     cores = set_threads(0)
-    solve_s, n, elems, iters = 0.0, 0, 0, 0
+    solve_s, n, elems, iters, energies = 0.0, 0, 0, 0, []
     while n < len(reqs) and (n == 0 or solve_s < budget_s):
         r = reqs[n]
         ns, bonds = lattice_by_name(r["lattice"])
@@ -493,10 +495,31 @@ def solves_cpu_baseline(kind, count, budget_s):
         res = lanczos_matrix_free(K, v0, min(K.D, 1000), tol=1e-10, inplace=True)
         solve_s += time.perf_counter() - t0
         n, elems, iters = n + 1, elems + K.D, iters + res["iters"]
+        energies.append(res["energy"])
     return {"value": n / solve_s, "unit": "solves/s", "cores": cores, "kind": "oracle",
             "sample": f"the first {n} of the {len(reqs)} {kind} requests in list order ({elems} elements, "
                       f"{iters} Lanczos steps to rho < 1e-10), one after another; {solve_s:.1f} s of solving "
-                      f"on {cores} OpenMP threads"}
+                      f"on {cores} OpenMP threads", "_energies": energies}
+
+
+def attach_solve_baselines(line, batch_count, serve_count, budget_s):
+    """The batch and serving CPU baselines, each with the agreement of the
+    oracle's energies and the GPU's on the requests the oracle solved."""
+    for key, count in (("batch", batch_count), ("serve", serve_count)):
+        if key in line:
+            cb = solves_cpu_baseline(key, count, budget_s)
+            cb["max_rel_diff_vs_gpu"], cb["compared"] = agreement(line[key].get("_energies", []),
+                                                                  cb.pop("_energies"))
+            line[key]["cpu_baseline"] = cb
+
+
+def agreement(gpu, oracle):
+    """Largest |E_gpu - E_oracle| / max(1, |E_oracle|) over the requests both
+    solved (lists in request order), and how many were compared."""
+    pairs = [(g, o) for g, o in zip(gpu, oracle) if g is not None and o is not None]
+    if not pairs:
+        return None, 0
+    return max(abs(g - o) / max(1.0, abs(o)) for g, o in pairs), len(pairs)
 
 
 def run_reference(args):

@@ -64,3 +64,21 @@ def test_solves_cpu_baseline_reports_its_sample(kind, count):
     r = bench.solves_cpu_baseline(kind, count, 0.05)
     assert r["kind"] == "oracle" and r["unit"] == "solves/s" and r["value"] > 0 and r["cores"] >= 1
     assert f"of the {count} {kind} requests in list order" in r["sample"]
+    assert len(r["_energies"]) >= 1 and all(isinstance(e, float) for e in r["_energies"])
+
+
+def test_agreement_of_gpu_and_oracle_energies():
+    d, n = bench.agreement([-1.0, None, 2.0, 5.0], [-1.0 - 2e-12, -3.0, 2.0 + 4e-12])
+    assert n == 2 and d == pytest.approx(2e-12, rel=1e-3)
+    assert bench.agreement([None], [1.0]) == (None, 0)
+
+
+def test_attach_solve_baselines(monkeypatch):
+    def fake(kind, count, budget):
+        return {"value": 1.0, "unit": "solves/s", "_energies": [-2.0, -3.0 + 3e-12]}
+    monkeypatch.setattr(bench, "solves_cpu_baseline", fake)
+    line = {"batch": {"_energies": [-2.0, -3.0, -4.0]}}
+    bench.attach_solve_baselines(line, 2048, 400, 1.0)
+    cb = line["batch"]["cpu_baseline"]
+    assert "_energies" not in cb and cb["compared"] == 2 and cb["max_rel_diff_vs_gpu"] == pytest.approx(1e-12)
+    assert "serve" not in line
