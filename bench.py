@@ -57,11 +57,30 @@ def workload_config(name):
     return ns, bonds, nup, ndn, U, dt, cfg
 
 
-# DRAM bytes per hubbard_apply from the ncu capture summarised in
-# profiles/hv_f64_sq4x4_n6_6_phases_ncu.md (small case scaled by D to the bench
-# sector); must be set back to None whenever the H*v kernels change.
-TRAFFIC = {"sq4x4_n8_8_U8_f64": 9.16e9}
+# DRAM bytes per hubbard_apply from one ncu metrics capture (dram__bytes_read.sum
+# + dram__bytes_write.sum over the apply's kernels, a smaller sector scaled by D
+# to the bench sector), each with the SHA-256 prefix of the H*v kernel sources it
+# was taken on: a figure is reported only while those sources are unchanged.
+TRAFFIC = {"sq4x4_n8_8_U8_f64": (9.16e9, "cf9e9bfd24c3fbfa")}
+KERNEL_SOURCES = ("paper_1204_3425_gb300/csrc/hv_phases.cu", "paper_1204_3425_gb300/csrc/row_blocks.cuh")
 NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal per GPU (vendor figure)
+
+
+def kernel_sources_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per apply if captured on the current kernel sources, else None."""
+    t = TRAFFIC.get(workload)
+    if t is None or t[1] != kernel_sources_hash():
+        return None
+    return t[0]
 
 
 def peaks():
@@ -266,24 +285,35 @@ def run_ours(args):
     if args.serve and rank == 0:
         extra["serve"] = bench_serve(args.serve)
 
+    if args.workload == "sq4x4_n8_8_U8_f64":
+        extra["hv_sq4x4_f32"] = bench_hv_f32(hub, torch, H, v_host, args.steps, args.warmup)
+    H.close()
+    del v, w, v_pin
+    torch.cuda.empty_cache()
+    if args.ring18 and args.workload == "sq4x4_n8_8_U8_f64":
+        extra["config3_ring18"] = bench_ring18(hub, torch, dev, args.ring18_U,
+                                               cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
     peak, src = peaks()
     avg_kernel_ms = float(np.mean(per))
     achieved = nbytes / (avg_kernel_ms * 1e-3) / 1e9
+    traffic = measured_traffic(args.workload)
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dts,
         "arith": ("exact int32-pair fixed-point hop sums, binary64 storage and rounding" if dts == "f64"
                   else "binary32"),
         "data": "synthetic (seeded SplitMix64 start vector)",
-        "config": dict(cfg, step="one H*v (hubbard_apply)", parallelism="replicas" if ws > 1 else "single",
-                       schedule=dict(zip(("vec_rows", "vec_cols", "ctas_rows", "ctas_cols"), schedule))),
+        "config": dict(cfg, step="one H*v (hubbard_apply)"),
+        "parallelism": "replicas" if ws > 1 else "single",
+        "schedule": dict(zip(("vec_rows", "vec_cols", "ctas_rows", "ctas_cols"), schedule)),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": TRAFFIC.get(args.workload), "peak_source": src,
+                     "traffic": traffic, "peak_source": src,
                      "algorithmic_bytes_per_launch": nbytes,
                      "frac_of_nominal_7900": achieved / NOMINAL_HBM_GBS,
-                     "dram_gbs_from_traffic": (TRAFFIC[args.workload] / (avg_kernel_ms * 1e-3) / 1e9
-                                               if TRAFFIC.get(args.workload) else None),
-                     "amplification": (TRAFFIC[args.workload] / nbytes if TRAFFIC.get(args.workload) else None),
+                     "dram_gbs_from_traffic": (traffic / (avg_kernel_ms * 1e-3) / 1e9 if traffic else None),
+                     "dram_frac_from_traffic": (traffic / (avg_kernel_ms * 1e-3) / 1e9 / peak if traffic else None),
+                     "amplification": (traffic / nbytes if traffic else None),
+                     "kernel_sources_sha": kernel_sources_hash(),
                      "kernel": "hubbard_apply (row phase + up phase kernels)"},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * esize, "d2h_bytes_per_step": D * esize,
                 "ms_per_step": e2e_ms, "pipelined": "3 streams: upload i+1 | H*v i | download i-1"},
@@ -298,7 +328,6 @@ def run_ours(args):
     for key in ("batch", "serve"):
         if key in line:
             line[key].pop("_energies", None)
-    H.close()
     if rank == 0:
         print(json.dumps(line))
     if ws > 1:
@@ -345,6 +374,133 @@ def e2e_pipelined(hub, torch, H, v_pin, D, tdt, dev, k):
     t1.record(sc)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1) / k
+
+
+def time_apply(hub, torch, H, v, w, steps, warmup):
+    """Mean CUDA-event time (ms) of `steps` hubbard_apply calls after `warmup` ones."""
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        hub.hubbard_apply(H, v, w)
+    torch.cuda.synchronize()
+    per = []
+    for _ in range(steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hub.hubbard_apply(H, v, w)
+        e1.record(stream)
+        per.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in per]))
+
+
+def tables_bytes(hub, H):
+    """Per-spin tables read once per H*v: packed targets + sign mask + state word."""
+    return sum(int(hub.load_library().hubbard_table_nnz(H.handle, s)) * 4 + (H.Dup if s == 0 else H.Ddn) * 12
+               for s in (0, 1))
+
+
+def hv_line(ms, D, tables, s):
+    peak, src = peaks()
+    nbytes = hv_bytes(D, tables, s)
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return dict(ms=ms, gbs=gbs, algorithmic_bytes=nbytes, roofline={"bound": "hbm", "achieved": gbs, "peak": peak,
+                "unit": "GB/s", "frac": gbs / peak, "traffic": None, "peak_source": src})
+
+
+def bench_hv_f32(hub, torch, H, v_host, steps, warmup):
+    """The same sector's H*v with binary32 vectors (the refined path's hot loop)."""
+    v = v_host.to(torch.float32).cuda()
+    w = torch.empty_like(v)
+    ms = time_apply(hub, torch, H, v, w, max(steps, 5), warmup)
+    out = hv_line(ms, H.D, tables_bytes(hub, H), 4)
+    out["dtype"] = "f32"
+    del v, w
+    return out
+
+
+def bench_ring18(hub, torch, dev, U, cpu=True):
+    """Config 3: the 18-site ring, N = (9, 9), D = 2.36e9, t = 1, U: binary32 and
+    binary64 H*v, then one plain binary64 ground-state solve and one binary32 +
+    binary64-refined solve from the same seeded start vector, each checked
+    against the stored oracle energy; one solve per path keeps the run short."""
+    from workload import ring
+    name = f"ring18_n9_9_U{int(U)}"
+    e_ref = json.load(open(os.path.join(ROOT, "tests", "golden", name + ".json")))["e0"]
+    bonds = ring(18)
+    out = {"workload": name, "dim": 48620 ** 2, "t": 1.0, "U": U, "seed": 1234, "solves_per_path": 1,
+           "oracle_energy": f"tests/golden/{name}.json"}
+    H = hub.hubbard_sector_create(18, bonds, 9, 9, 1.0, U)
+    D = H.D
+    tb = tables_bytes(hub, H)
+    ws_bytes = hub.lanczos_workspace_bytes(H, hub.HUB_F64)
+    v = torch.empty(D, dtype=torch.float64, device=dev)
+    hub.hubbard_fill_start_vector(v, 1234)          # the seeded recipe, generated on the device
+    w = torch.empty_like(v)
+    out["hv_f64"] = hv_line(time_apply(hub, torch, H, v, w, 5, 2), D, tb, 8)
+    del w
+    v32 = v.to(torch.float32)
+    w32 = torch.empty_like(v32)
+    out["hv_f32"] = hv_line(time_apply(hub, torch, H, v32, w32, 5, 2), D, tb, 4)
+    del v32, w32
+    H.close()
+    torch.cuda.empty_cache()
+    # plain binary64 solve (create + Lanczos to rho < 1e-10 + destroy)
+    ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hs = hub.hubbard_sector_create(18, bonds, 9, 9, 1.0, U)
+    r = hub.lanczos_ground_state(Hs, v, 1000, 1e-10, workspace=ws)
+    Hs.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rel = abs(r["energy"] - e_ref) / abs(e_ref)
+    out["solve_f64"] = dict(s=dt, solves_per_s=(1.0 / dt) if rel <= 1e-9 else 0.0, iters=r["iters"],
+                            energy=r["energy"], rel_err_vs_oracle=rel, err_bound=r["err_bound"],
+                            ms_per_iteration=1e3 * dt / max(1, r["iters"]))
+    del ws
+    torch.cuda.empty_cache()
+    # binary32 + binary64 refinement; spare workspace stores binary32 Lanczos vectors
+    free, _ = torch.cuda.mem_get_info()
+    slot = (D * 4 + 255) // 256 * 256
+    store = int(max(0, min(128, (free - 40 * D - (8 << 30)) // slot)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Hs = hub.hubbard_sector_create(18, bonds, 9, 9, 1.0, U)
+    rr = hub.lanczos_ground_state_refined(Hs, v, 1000, 1e-10, store_vectors=store)
+    Hs.close()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rel = abs(rr["energy"] - e_ref) / abs(e_ref)
+    out["solve_refined"] = dict(s=dt, solves_per_s=(1.0 / dt) if rel <= 1e-9 else 0.0,
+                                iters_f32_f64=(rr["iters_f32"], rr["iters_f64"]), energy=rr["energy"],
+                                rel_err_vs_oracle=rel, error_bound=rr["error_bound"], stored_vectors=store,
+                                replayed=rr["replayed"])
+    out["refined_over_f64_solves"] = (out["solve_refined"]["solves_per_s"] / out["solve_f64"]["solves_per_s"]
+                                      if out["solve_f64"]["solves_per_s"] else None)
+    del v
+    torch.cuda.empty_cache()
+    if cpu:
+        out["cpu_baseline"] = ring18_cpu_baseline(U)
+    return out
+
+
+def ring18_cpu_baseline(U):
+    """The oracle's Kronecker-sum Lanczos iteration on the 18-site ring, host cores
+    (two iterations after one warm-up step: 38 GB of host memory)."""
+    from oracle.kron import KronHamiltonian, lanczos_matrix_free, set_threads
+    from workload import ring, start_vector
+    cores = set_threads(0)
+    t0 = time.perf_counter()
+    K = KronHamiltonian(18, ring(18), 9, 9, 1.0, U)
+    build_s = time.perf_counter() - t0
+    x = start_vector(K.D, seed=1234)
+    stamps = []
+    lanczos_matrix_free(K, x, 3, on_step=lambda j, e, r: stamps.append(time.perf_counter()), inplace=True)
+    it_s = float(np.median(np.diff(stamps)))
+    del x, K
+    return {"value": it_s, "unit": "s per Lanczos iteration", "cores": cores, "kind": "oracle",
+            "sample": f"3 matrix-free Lanczos steps on the ring-18 (9,9) sector (plain C Kronecker-sum H*v, "
+                      f"OpenMP, {cores} threads), median of the last two; table build {build_s:.1f} s not timed"}
 
 
 def bench_refined(hub, torch, dev, bonds, golden, n):
@@ -514,12 +670,13 @@ def attach_solve_baselines(line, batch_count, serve_count, budget_s):
 
 
 def agreement(gpu, oracle):
-    """Largest |E_gpu - E_oracle| / max(1, |E_oracle|) over the requests both
-    solved (lists in request order), and how many were compared."""
+    """Largest relative difference |E_gpu - E_oracle| / |E_oracle| over the
+    requests both solved (lists in request order; pairs with E_oracle = 0 are
+    compared absolutely), and how many were compared."""
     pairs = [(g, o) for g, o in zip(gpu, oracle) if g is not None and o is not None]
     if not pairs:
         return None, 0
-    return max(abs(g - o) / max(1.0, abs(o)) for g, o in pairs), len(pairs)
+    return max(abs(g - o) / abs(o) if o != 0.0 else abs(g - o) for g, o in pairs), len(pairs)
 
 
 def run_reference(args):
@@ -571,6 +728,8 @@ def main():
     ap.add_argument("--batch-sectors", type=int, default=2048,
                     help="sectors in the batched solve (smaller: the profiling case)")
     ap.add_argument("--serve", type=int, default=400, help="requests in the serving trace (0: skip)")
+    ap.add_argument("--ring18", type=int, default=1, help="also time config 3, the 18-site ring (0: skip)")
+    ap.add_argument("--ring18-U", type=float, default=4.0, choices=[2.0, 4.0, 8.0])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

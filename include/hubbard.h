@@ -196,6 +196,9 @@ int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, vo
  *   - Every call, from any thread or stream, shares the one array and leaves
  *     its contents behind; calls whose GPU work overlaps (concurrent streams
  *     or threads) race on it and must be serialised by the caller.
+ *   - Sectors with more than 127 hops per state (W_up + W_dn > 127) take the
+ *     native binary64 kernel of hubbard_apply_reference, which needs no
+ *     scratch; every other sector takes the fixed-point kernels.
  * Same accuracy and argument rules as hubbard_apply with HUB_F64.
  * Asynchronous on `stream`.
  * ------------------------------------------------------------------------- */
@@ -243,10 +246,23 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
  *              max_iters steps (or to breakdown)
  *   workspace  device buffer of at least lanczos_workspace_bytes(H, dtype)
  *              bytes, caller-owned, 256-byte aligned
+ *   psi_out    optional binary64 device vector of D elements (16-byte
+ *              aligned, not overlapping the workspace) receiving the
+ *              normalised Ritz vector psi = sum_j s_j f_j of the lowest Ritz
+ *              value.  The Lanczos vectors are not stored: a second pass
+ *              replays the same recurrence with the recorded a_j, b_j (the
+ *              kernels are deterministic, so the replayed f_j are the ones of
+ *              the first pass) and accumulates psi in binary64, which doubles
+ *              the H*v count.  NULL skips it.
  *   alpha_out, beta_out  optional host arrays of max_iters doubles receiving
  *              a_1..a_m and b_2..b_{m+1}
- *   out        host result: energy (lowest Ritz value), residual rho, iters,
- *              status, breakdown flag
+ *   out        host result: energy (lowest Ritz value), residual rho,
+ *              err_bound, iters, status, breakdown flag
+ * err_bound is the a-posteriori bound min(rho, rho^2 / gap) on |energy - E0|,
+ * gap = (theta_2 - rho_2) - energy from the second distinct Ritz pair of T_m
+ * (theta_2, residual estimate rho_2); when T_m resolves no positive gap it is
+ * rho.  The quadratic form assumes no eigenvalue of H other than E0 lies below
+ * theta_2 - rho_2.
  * Breakdown (beta_{m+1} <= 1e-13 * max(1, max|a|, max b)) counts as
  * converged.  Returns HUB_ENOTCONV (with the best energy in *out) when
  * max_iters is reached with tol > 0 and rho >= tol.  Synchronises `stream`.
@@ -257,6 +273,7 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
 typedef struct {
     double energy;
     double residual;
+    double err_bound;
     int32_t iters;
     int32_t status;
     int32_t breakdown;
@@ -266,7 +283,7 @@ typedef struct {
 size_t lanczos_workspace_bytes(hubbard_t H, int dtype);
 
 int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype,
-                         void* workspace, size_t ws_bytes, void* stream,
+                         void* workspace, size_t ws_bytes, void* psi_out, void* stream,
                          double* alpha_out, double* beta_out, lanczos_result* out);
 
 /* Number of kernels this library has launched in this process (all threads,
@@ -284,8 +301,8 @@ uint64_t hubbard_kernel_launches(void);
  *      (bit-identical f_j, so psi is the same however many were stored);
  *   3. binary64 Rayleigh quotient theta = <psi|H|psi> and residual
  *      |H psi - theta psi| with the binary64 H*v;
- *   4. if residual^2 / gap > tol max(1,|theta|): a short binary64 Lanczos
- *      run started from psi (at most 60 steps).
+ *   4. if the error bound below exceeds tol max(1,|theta|): a short binary64
+ *      Lanczos run started from psi (at most 60 steps).
  *   v0          binary64 device start vector (normalised inside)
  *   workspace   >= lanczos_refined_workspace_bytes(H) bytes (40 D), 256-aligned;
  *               every further 4 D bytes (rounded up to 256) stores one more
@@ -293,10 +310,17 @@ uint64_t hubbard_kernel_launches(void);
  *   psi_out     optional binary64 device vector receiving the normalised psi
  *               of step 2
  *   out         energy (binary64 Rayleigh quotient or polished Ritz value),
- *               residual, error_bound = residual^2 / gap (a-posteriori bound on
- *               |energy - E0| when the gap estimate holds), binary32 energy,
- *               gap estimate, iteration counts, status
- * Returns HUB_ENOTCONV when the bound stays above tol.  Synchronises stream.
+ *               residual (|H psi - theta psi| in binary64, or the polish's
+ *               Ritz residual estimate), error_bound, binary32 energy, gap,
+ *               iteration counts, status
+ * gap is a lower estimate of lambda_2 - E0 from the binary32 run:
+ * (theta_2 - rho_2) - theta with theta_2 its second distinct Ritz value and
+ * rho_2 that Ritz pair's residual estimate (a Ritz value alone only bounds
+ * lambda_2 from above).  error_bound = min(residual, residual^2 / gap), or the
+ * residual when gap <= 0; the quadratic form assumes no eigenvalue other than
+ * E0 lies below theta_2 - rho_2.  The polish runs until error_bound <= tol *
+ * max(1, |energy|) (at most 60 binary64 steps); status is HUB_OK exactly when
+ * that holds.  Returns HUB_ENOTCONV otherwise.  Synchronises stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double energy;
@@ -361,7 +385,9 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
                               size_t ws_bytes, void* stream);
 
 /* Copies the per-sector results (host array of n_sectors); synchronises
- * `stream`.  HUB_ETIMEOUT if a grid barrier gave up. */
+ * `stream`.  err_bound is computed here on the host from each sector's a/b
+ * history, as lanczos_ground_state defines it.  HUB_ETIMEOUT if a grid
+ * barrier gave up. */
 int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
                           lanczos_result* results);
 

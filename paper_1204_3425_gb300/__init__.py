@@ -26,8 +26,9 @@ class HubError(RuntimeError):
 
 
 class LanczosResult(ctypes.Structure):
-    _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("iters", ctypes.c_int32),
-                ("status", ctypes.c_int32), ("breakdown", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("err_bound", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("breakdown", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 _lib = None
@@ -50,7 +51,7 @@ SIGNATURES = {
     "hubbard_fill_start_vector": (ctypes.c_int, [P, I64, ctypes.c_uint64, I64, ctypes.c_int, P]),
     "hubbard_lanczos_step": (ctypes.c_int, [P, P, P, D, ctypes.c_int, P, P, P]),
     "lanczos_workspace_bytes": (SZ, [P, ctypes.c_int]),
-    "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P]),
+    "lanczos_ground_state": (ctypes.c_int, [P, P, ctypes.c_int, D, ctypes.c_int, P, SZ, P, P, P, P, P]),
     "hubbard_host_spin_tables": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]),
     "hubbard_host_row_table": (ctypes.c_int, [ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P,
                                               P, P]),
@@ -99,6 +100,17 @@ def _dtype_code(t):
     if t.dtype == torch.float32:
         return HUB_F32
     raise TypeError(f"unsupported dtype {t.dtype}")
+
+
+def _vec_pair(H, v, w, dtypes=None):
+    """Checks that v and w are vectors of H.D elements of one supported dtype
+    (the C entry points read and write exactly H.D elements of it)."""
+    import torch
+    allowed = dtypes if dtypes is not None else (torch.float64, torch.float32)
+    if v.dtype not in allowed or w.dtype != v.dtype:
+        raise TypeError(f"v and w must share one dtype of {allowed}, got {v.dtype} and {w.dtype}")
+    if v.numel() != H.D or w.numel() != H.D:
+        raise ValueError(f"v and w must hold D = {H.D} elements, got {v.numel()} and {w.numel()}")
 
 
 def _ptr(t):
@@ -200,17 +212,20 @@ def hubbard_host_row_table(ns, bonds, n, elem_bytes):
 
 
 def hubbard_apply(H, v, w, stream=None):
+    _vec_pair(H, v, w)
     _check(load_library().hubbard_apply(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
     return w
 
 
 def hubbard_apply_reference(H, v, w, stream=None):
+    _vec_pair(H, v, w)
     _check(load_library().hubbard_apply_reference(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
     return w
 
 
 def hubbard_autotune_schedule(H, v, w, stream=None):
     """Times the H*v schedules on (v, w) and keeps the fastest; returns it as a tuple."""
+    _vec_pair(H, v, w)
     out = (ctypes.c_int * 4)()
     _check(load_library().hubbard_autotune_schedule(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream), out))
     return tuple(out)
@@ -233,6 +248,8 @@ def hubbard_apply_noalloc(H, v, w, stream=None):
     shared by all calls: sectors above HUBBARD_NOALLOC_MAX_ELEMS are rejected,
     and calls whose GPU work overlaps race on the array.
     """
+    import torch
+    _vec_pair(H, v, w, (torch.float64,))
     _check(load_library().hubbard_apply_noalloc(H.handle, _ptr(v), _ptr(w), _stream(stream)))
     return w
 
@@ -273,11 +290,17 @@ def lanczos_workspace_bytes(H, dtype=HUB_F64):
     return int(load_library().lanczos_workspace_bytes(H.handle, dtype))
 
 
-def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None, raise_on_notconv=False):
-    """Returns dict(energy, residual, iters, status, breakdown, alpha, beta)."""
+def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None, raise_on_notconv=False,
+                         psi_out=None):
+    """Returns dict(energy, residual, err_bound, iters, status, breakdown, alpha, beta).
+    psi_out: optional float64 device tensor of D elements receiving the Ritz vector."""
     import torch
     lib = load_library()
     dt = _dtype_code(v0)
+    if v0.numel() != H.D:
+        raise ValueError(f"v0 must hold D = {H.D} elements, got {v0.numel()}")
+    if psi_out is not None and (psi_out.dtype != torch.float64 or psi_out.numel() != H.D):
+        raise ValueError("psi_out must be a float64 tensor of D elements")
     need = lanczos_workspace_bytes(H, dt)
     if workspace is None:
         workspace = torch.empty(need, dtype=torch.uint8, device=v0.device)
@@ -285,12 +308,13 @@ def lanczos_ground_state(H, v0, max_iters, tol=0.0, workspace=None, stream=None,
     b = np.zeros(max_iters)
     res = LanczosResult()
     rc = lib.lanczos_ground_state(H.handle, _ptr(v0), int(max_iters), float(tol), dt, _ptr(workspace),
-                                  workspace.numel() * workspace.element_size(), _stream(stream),
+                                  workspace.numel() * workspace.element_size(),
+                                  _ptr(psi_out) if psi_out is not None else None, _stream(stream),
                                   a.ctypes.data, b.ctypes.data, ctypes.byref(res))
     if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
         _check(rc)
     m = res.iters
-    return dict(energy=res.energy, residual=res.residual, iters=m, status=res.status,
+    return dict(energy=res.energy, residual=res.residual, err_bound=res.err_bound, iters=m, status=res.status,
                 breakdown=bool(res.breakdown), alpha=a[:m], beta=b[:m])
 
 
@@ -371,7 +395,7 @@ class Batch:
         res = (LanczosResult * self.n)()
         _check(load_library().hubbard_batch_results(self.handle, _ptr(workspace), int(max_iters), _stream(stream),
                                                     res))
-        return [dict(energy=r.energy, residual=r.residual, iters=r.iters, status=r.status,
+        return [dict(energy=r.energy, residual=r.residual, err_bound=r.err_bound, iters=r.iters, status=r.status,
                      breakdown=bool(r.breakdown)) for r in res]
 
     def autotune(self, v0_all, max_iters, tol, workspace, stream=None):

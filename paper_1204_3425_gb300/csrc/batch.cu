@@ -490,6 +490,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
                         lanczos_result res;
                         res.energy = th;
                         res.residual = rho;
+                        res.err_bound = 0.0;             // set on the host (hubbard_batch_results)
                         res.iters = m;
                         res.breakdown = st.broke;
                         res.status = conv ? HUB_OK : HUB_ENOTCONV;
@@ -702,6 +703,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             lanczos_result r;
             r.energy = theta;
             r.residual = rho;
+            r.err_bound = 0.0;                           // set on the host (hubbard_batch_results)
             r.iters = m;
             r.breakdown = broke;
             r.status = conv ? HUB_OK : HUB_ENOTCONV;
@@ -1111,8 +1113,29 @@ int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iter
     HUB_CUDA(cudaMemcpyAsync(results, (const char*)workspace + L.res, (size_t)B->n * sizeof(lanczos_result),
                              cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaMemcpyAsync(&err, (const char*)workspace + L.err, 4, cudaMemcpyDeviceToHost, s));
+    // a/b histories, for the a-posteriori error bound of every sector
+    std::vector<double> ab;
+    try {
+        ab.resize((size_t)B->n * 2 * (size_t)max_iters);
+    } catch (const std::bad_alloc&) {
+        return fail(HUB_ENOMEM, "host allocation (batch a/b histories)");
+    }
+    HUB_CUDA(cudaMemcpyAsync(ab.data(), (const char*)workspace + L.ab, ab.size() * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaStreamSynchronize(s));
     if (err != 0) return fail(err, "batch: a grid barrier timed out");
+    for (int i = 0; i < B->n; ++i) {
+        lanczos_result& r = results[i];
+        const int m = r.iters;
+        if (m < 1 || m > max_iters) {
+            r.err_bound = INFINITY;
+            continue;
+        }
+        const double* A = ab.data() + (size_t)i * 2 * max_iters;
+        const double* Bv = A + max_iters;
+        const double gap = tridiag_gap_lower(A, Bv, m, Bv[m - 1], r.energy);
+        r.err_bound = energy_error_bound(r.residual, gap);
+    }
     return HUB_OK;
 }
 

@@ -885,8 +885,51 @@ struct ScratchGuard {
     }
 };
 
+// psi <- (init ? 0 : psi) + s f for a Lanczos vector f of dtype
+static int psi_accumulate(const void* f, int dtype, double* psi, int64_t n, double sj, bool init, cudaStream_t s) {
+    if (dtype == HUB_F64) return launch_psi_accumulate_f64((const double*)f, psi, n, sj, init, s);
+    return launch_psi_accumulate((const float*)f, psi, n, sj, init, s);
+}
+
+// Ritz vector psi = sum_j s_j f_j (binary64, accumulated in j order) of a
+// finished lanczos_core run, by replaying its recurrence: f_0 = v0 / |v0| as
+// in the run, then g <- H f_j - b_j g with the recorded b_j, and f_{j+1} =
+// (g - a_j f_j) / b_{j+1} completed inside the next H*v (the run's own
+// kernels with the same operands, hence the same f_j bit for bit).  f, g:
+// two vectors of dtype; psi is normalised on return.
+static int replay_ritz_vector(hubbard_t H, const void* v0, int v0_dtype, int dtype, const LanczosRun& R,
+                              const std::vector<double>& sv, void* f, void* g, double* psi, cudaStream_t s) {
+    int rc;
+    const int m = (int)R.a.size();
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0)))
+        return rc;
+    if (v0_dtype == dtype) rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / std::sqrt(n0), s);
+    else rc = launch_f64_to_f32_scaled((const double*)v0, (float*)f, H->D, 1.0 / std::sqrt(n0), s);
+    if (rc) return rc;
+    if (cudaMemsetAsync(g, 0, (size_t)H->D * elem_size(dtype), s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    if ((rc = psi_accumulate(f, dtype, psi, H->D, sv[0], true, s))) return rc;
+    RowUpdate ru{};
+    bool have = false;
+    for (int j = 0; j + 1 < m; ++j) {
+        const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
+        if ((rc = launch_hv_fast(H, f, g, dtype, bj, g, 1023, s, nullptr, nullptr, have ? &ru : nullptr))) return rc;
+        if (have && (rc = psi_accumulate(f, dtype, psi, H->D, sv[(size_t)j], false, s))) return rc;
+        ru = RowUpdate{f, -R.a[(size_t)j], 1.0 / R.b[(size_t)j]};
+        have = true;
+        std::swap(f, g);
+    }
+    if (have) {
+        if ((rc = launch_axpy_scale(ru.a, ru.inv, ru.fo, f, H->D, dtype, s))) return rc;
+        if ((rc = psi_accumulate(f, dtype, psi, H->D, sv[(size_t)m - 1], false, s))) return rc;
+    }
+    double pn = 0.0;
+    if ((rc = launch_dot(H, psi, psi, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pn))) return rc;
+    return launch_scale(1.0 / std::sqrt(pn), psi, H->D, HUB_F64, s);
+}
+
 int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol, int dtype, void* workspace,
-                         size_t ws_bytes, void* stream, double* alpha_out, double* beta_out,
+                         size_t ws_bytes, void* psi_out, void* stream, double* alpha_out, double* beta_out,
                          lanczos_result* out) {
     clear_error();
     int rc;
@@ -901,6 +944,12 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     if (ws_bytes < lanczos_workspace_bytes(H, dtype)) return fail(HUB_ENOMEM, "workspace too small");
     if (dtype == HUB_F64 && !fixed_point_ok(H))
         return fail(HUB_EINVAL, "lanczos: more than 127 hops per state is not supported");
+    if (psi_out != nullptr) {
+        if (!aligned16(psi_out)) return fail(HUB_EINVAL, "psi_out not 16-byte aligned");
+        const char* p = (const char*)psi_out;
+        const char* w0 = (const char*)workspace;
+        if (p < w0 + ws_bytes && w0 < p + (size_t)H->D * 8) return fail(HUB_EINVAL, "psi_out overlaps the workspace");
+    }
     cudaStream_t s = (cudaStream_t)stream;
     const size_t vec = align_up((size_t)H->D * elem_size(dtype), 256);
     char* ws = (char*)workspace;
@@ -910,8 +959,17 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     const int m = (int)R.a.size();
     if (alpha_out) std::memcpy(alpha_out, R.a.data(), m * sizeof(double));
     if (beta_out) std::memcpy(beta_out, R.b.data(), m * sizeof(double));
+    const double gap = tridiag_gap_lower(R.a.data(), R.b.data(), m, R.b.back(), R.theta);
+    if (psi_out != nullptr) {
+        std::vector<double> sv((size_t)m);
+        double th = 0.0;
+        tridiag_lowest_vector(R.a.data(), R.b.data(), m, &th, sv.data());
+        if ((rc = replay_ritz_vector(H, v0, dtype, dtype, R, sv, ws, ws + vec, (double*)psi_out, s))) return rc;
+        if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+    }
     out->energy = R.theta;
     out->residual = R.rho;
+    out->err_bound = energy_error_bound(R.rho, gap);
     out->iters = m;
     out->breakdown = R.broke ? 1 : 0;
     out->status = R.converged ? HUB_OK : HUB_ENOTCONV;
@@ -964,15 +1022,9 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
     std::vector<double> sv((size_t)m);
     double theta32 = 0.0;
     tridiag_lowest_vector(R.a.data(), R.b.data(), m, &theta32, sv.data());
-    // gap to the next distinct Ritz value (skipping converged copies of the lowest)
-    double gap = 0.0;
-    for (int k = 1; k < std::min(m, 8); ++k) {
-        const double tk = tridiag_kth(R.a.data(), R.b.data(), m, k);
-        if (tk - theta32 > 1e-5 * std::max(1.0, std::fabs(theta32))) {
-            gap = tk - theta32;
-            break;
-        }
-    }
+    // lower estimate of lambda_2 - E0: the second distinct Ritz value minus its
+    // Ritz residual (a Ritz value alone bounds lambda_2 only from above)
+    const double gap = tridiag_gap_lower(R.a.data(), R.b.data(), m, R.b.back(), theta32);
     out->energy_f32 = theta32;
     out->iters_f32 = m;
     out->gap = gap;
@@ -1041,7 +1093,7 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         return rc;
     out->energy = th;
     out->residual = std::sqrt(std::max(r2, 0.0));
-    out->error_bound = gap > 0.0 ? r2 / gap : INFINITY;
+    out->error_bound = energy_error_bound(out->residual, gap);
     out->iters_f64 = 0;
 
     // 4. short binary64 Lanczos polish from psi when the bound misses tol * |theta|
@@ -1055,12 +1107,14 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
             return fail(HUB_ENOMEM, "workspace too small for the binary64 polish");
         ScratchGuard g2(H, pscr, D * 16);
         LanczosRun P;
-        // stop as soon as rho^2 / gap meets the requested bound
-        const double rho_target = std::sqrt(tol * std::max(1.0, std::fabs(th)) * std::max(gap, 1e-300));
-        if ((rc = lanczos_core(H, psi, HUB_F64, 60, gap > 0.0 ? rho_target : 1e-13, HUB_F64, pf, pg, s, P))) return rc;
+        // stop as soon as the bound meets tol: rho^2 / gap when a gap is
+        // resolved, else rho itself
+        const double want = tol * std::max(1.0, std::fabs(th));
+        const double rho_target = gap > 0.0 ? std::sqrt(want * gap) : want;
+        if ((rc = lanczos_core(H, psi, HUB_F64, 60, rho_target, HUB_F64, pf, pg, s, P))) return rc;
         out->energy = P.theta;
         out->residual = P.rho;
-        out->error_bound = gap > 0.0 ? P.rho * P.rho / gap : INFINITY;
+        out->error_bound = energy_error_bound(P.rho, gap);
         out->iters_f64 = (int)P.a.size();
     }
     out->status = (out->error_bound <= tol * std::max(1.0, std::fabs(out->energy))) ? HUB_OK : HUB_ENOTCONV;

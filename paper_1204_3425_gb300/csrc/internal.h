@@ -1,5 +1,6 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
+#include <algorithm>
 #include <cstdint>
 #include <cstddef>
 #include <memory>
@@ -160,6 +161,7 @@ int launch_copy_normalise(const void* x, void* y, int64_t n, int dtype, double i
 int launch_f64_to_f32_scaled(const double* x, float* y, int64_t n, double a, cudaStream_t s);
 int launch_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype, cudaStream_t s);
 int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s);
+int launch_psi_accumulate_f64(const double* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s);
 // psi = sum_{j<m} s_j f_j, f_j = base + j * stride (binary32), s on the device;
 // bit-identical to m successive launch_psi_accumulate calls
 int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_dev, double* psi, int64_t n,
@@ -173,5 +175,17 @@ void tridiag_lowest(const double* a, const double* b, int m, double* theta, doub
 void tridiag_lowest_vector(const double* a, const double* b, int m, double* theta, double* s);
 // k-th smallest eigenvalue (k = 0 is the lowest)
 double tridiag_kth(const double* a, const double* b, int m, int k);
+// Lower estimate of the gap lambda_2 - theta from the Lanczos tridiagonal
+// T_m (b_next = b_{m+1}): (theta_2 - rho_2) - theta, with theta_2 the lowest
+// Ritz value above theta that is not a copy of it and rho_2 = b_{m+1} |s_m|
+// its residual estimate.  Valid when no eigenvalue of H other than the one
+// near theta lies below theta_2 - rho_2.  <= 0 when T_m resolves no gap.
+double tridiag_gap_lower(const double* a, const double* b, int m, double b_next, double theta);
+// a-posteriori bound on |theta - E0| from a residual norm rho and a gap lower
+// estimate: min(rho, rho^2 / gap) when gap > 0 (Temple-type), else rho
+inline double energy_error_bound(double rho, double gap) {
+    if (gap > 0.0) return std::min(rho, rho * rho / gap);
+    return rho;
+}
 
 }  // namespace hub

@@ -113,6 +113,20 @@ __global__ void k_to_fixed(const double* __restrict__ v, int2* __restrict__ X, i
         X[i] = to_fixed(v[i], emax);
 }
 
+// (-t * S) * 2^-k: the product -t * S is rounded once in the normal range and
+// the power of two is applied to its exponent field; only a result that is
+// itself subnormal is rounded a second time (by ldexp).  Scaling -t by 2^-k
+// first would round -t to a few bits whenever 2^-k is below the normal range
+// (inputs below about 2^-975).
+__device__ __forceinline__ double scaled_hop_sum(long long S, double mt, int k) {
+    if (S == 0) return 0.0;
+    const double p = mt * (double)S;
+    const long long bits = __double_as_longlong(p);
+    const int be = (int)((bits >> 52) & 0x7FF) - k;
+    if (be <= 0 || be >= 2047) return ldexp(p, -k);
+    return __longlong_as_double(bits - ((long long)k << 52));
+}
+
 // w = -t * S * 2^-k + U * n_d * v  [ - beta * w_old ]
 __global__ void k_hv_fixed(const int2* __restrict__ X, const double* __restrict__ v, double* w,
                            const double* w_old, double beta, int64_t Dup, int64_t Ddn,
@@ -121,7 +135,7 @@ __global__ void k_hv_fixed(const int2* __restrict__ X, const double* __restrict_
                            const uint32_t* __restrict__ su, const uint32_t* __restrict__ sd,
                            double mt, double U, const int* __restrict__ emax_p) {
     const int emax = max(*emax_p, 1);
-    const double scale = ldexp(mt, -(1070 - emax));   // -t * 2^-k
+    const int kg = 1070 - emax;                       // grid 2^-kg
     for (int64_t u = blockIdx.x; u < Dup; u += gridDim.x) {
         const int32_t ub = up_ptr[u], ue = up_ptr[u + 1];
         const uint32_t su_u = su[u];
@@ -142,7 +156,7 @@ __global__ void k_hv_fixed(const int2* __restrict__ X, const double* __restrict_
             const long long S = ((long long)hi << 24) + (long long)lo;
             const int64_t J = u * Ddn + d;
             const int nd = __popc(su_u & sd[d]);
-            double r = fma(U * (double)nd, v[J], scale * (double)S);
+            double r = fma(U * (double)nd, v[J], scaled_hop_sum(S, mt, kg));
             if (w_old != nullptr) r = fma(-beta, w_old[J], r);
             w[J] = r;
         }
@@ -264,6 +278,12 @@ __global__ void k_f64_to_f32_scaled(const double* __restrict__ x, float* __restr
 __global__ void k_psi_acc(const float* __restrict__ f, double* __restrict__ psi, int64_t n, double s, int init) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         psi[i] = init ? s * (double)f[i] : fma(s, (double)f[i], psi[i]);
+}
+
+// psi <- (init ? 0 : psi) + s * f  (binary64 f)
+__global__ void k_psi_acc_f64(const double* __restrict__ f, double* __restrict__ psi, int64_t n, double s, int init) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        psi[i] = init ? s * f[i] : fma(s, f[i], psi[i]);
 }
 
 // psi = sum_j s_j f_j over m stored binary32 vectors f_j = base + j * stride,
@@ -485,6 +505,14 @@ int launch_psi_accumulate(const float* f, double* psi, int64_t n, double sj, boo
     return HUB_OK;
 }
 
+int launch_psi_accumulate_f64(const double* f, double* psi, int64_t n, double sj, bool init, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_psi_acc_f64<<<g, kThreads, 0, s>>>(f, psi, n, sj, init ? 1 : 0);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
 int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_dev, double* psi, int64_t n,
                      cudaStream_t s) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
@@ -564,8 +592,9 @@ extern "C" int hubbard_apply_noalloc(hubbard_t H, const void* v, void* w, void* 
     if (a < b + bytes && b < a + bytes) return fail(HUB_EINVAL, "v and w overlap");
     if (H->D > (int64_t)HUBBARD_NOALLOC_MAX_ELEMS)
         return fail(HUB_EINVAL, "sector dimension exceeds HUBBARD_NOALLOC_MAX_ELEMS (2^21) of the no-allocation path");
-    if (H->host[0].W + H->host[1].W > 127)
-        return fail(HUB_EINVAL, "more than 127 hops per state: not supported by the no-allocation path");
+    // more than 127 hops per state overflow the two int32 fixed-point
+    // accumulators: the native binary64 kernel needs no scratch at all
+    if (H->host[0].W + H->host[1].W > 127) return launch_hv_reference(H, v, w, HUB_F64, (cudaStream_t)stream);
     int2* fixed = nullptr;
     int* emax = nullptr;
     int rc = noalloc_addresses(dev, &fixed, &emax);

@@ -66,7 +66,38 @@ void tridiag_solve(const double* a, const double* b, int m, double x, std::vecto
     }
 }
 
+// Inverse iteration for the eigenvector of T at eigenvalue x (normalised,
+// written to y[0..m)).
+void inverse_iteration(const double* a, const double* b, int m, double x, std::vector<double>& y) {
+    const double shift = x - 1e-14 * std::max(1.0, std::fabs(x));
+    y.assign(m, 1.0 / std::sqrt((double)m));
+    for (int it = 0; it < 4; ++it) {
+        tridiag_solve(a, b, m, shift, y);
+        double nrm = 0.0;
+        for (double v : y) nrm += v * v;
+        nrm = std::sqrt(nrm);
+        if (!(nrm > 0.0) || !std::isfinite(nrm)) break;
+        for (double& v : y) v /= nrm;
+    }
+}
+
 }  // namespace
+
+double tridiag_gap_lower(const double* a, const double* b, int m, double b_next, double theta) {
+    // the next Ritz value above theta that is not a copy of it (plain Lanczos
+    // repeats a converged Ritz value), and the residual estimate of its Ritz
+    // pair: an eigenvalue of H lies within rho_k of theta_k
+    const double copy_tol = 1e-8 * std::max(1.0, std::fabs(theta));
+    std::vector<double> y;
+    for (int k = 1; k < std::min(m, 16); ++k) {
+        const double tk = tridiag_kth(a, b, m, k);
+        if (tk - theta <= copy_tol) continue;
+        inverse_iteration(a, b, m, tk, y);
+        const double rho_k = std::fabs(b_next) * std::fabs(y[m - 1]);
+        return (tk - rho_k) - theta;
+    }
+    return 0.0;
+}
 
 double tridiag_kth(const double* a, const double* b, int m, int k) {
     // k-th smallest eigenvalue (k = 0 lowest) by bisection on the Sturm count

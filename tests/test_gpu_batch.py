@@ -80,6 +80,8 @@ def test_batch_matches_oracle(dev):
         assert r["status"] == hub.HUB_OK, (spec[2:], r)
         e = _oracle(spec)
         assert abs(r["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (spec[2:], r, e)
+        # the per-sector a-posteriori bound covers the actual error
+        assert abs(r["energy"] - e) <= r["err_bound"] + 1e-12 * max(1.0, abs(e)), (spec[2:], r, e)
 
 
 def test_batch_alone_equals_in_mix_and_single_path(dev):

@@ -245,6 +245,30 @@ def test_config2_sampled_rows(dev, sq4x4):
     del fd, w, w2
 
 
+def test_config2_whole_vector_vs_oracle(dev, sq4x4):
+    """Every one of the 1.66e8 elements of one H*v on the 4x4 (8,8) sector
+    against the oracle's Kronecker-sum H*v (plain C, Eq. H-Kroneckersum):
+    binary64 within 1e-12 |v|_2, binary32 within its stated bound."""
+    from oracle.kron import KronHamiltonian
+    H, S, v0 = sq4x4
+    K = KronHamiltonian(S.ns, S.bonds, S.nup, S.ndn, S.t, S.U)
+    f = v0 / np.linalg.norm(v0)
+    ref = K.hv(f)
+    fd = torch.from_numpy(f).to(dev)
+    w = torch.empty_like(fd)
+    hub.hubbard_apply(H, fd, w)
+    assert np.abs(w.cpu().numpy() - ref).max() <= 1e-12
+    del fd, w
+    f32 = f.astype(np.float32)
+    ref32 = K.hv(f32.astype(np.float64))
+    fd = torch.from_numpy(f32).to(dev)
+    w = torch.empty_like(fd)
+    hub.hubbard_apply(H, fd, w)
+    tol = 4e-7 * (H.Wup + H.Wdn + 1) * max(1.0, abs(S.U) * S.ns) * np.abs(f32).max()
+    assert np.abs(w.cpu().numpy().astype(np.float64) - ref32).max() <= tol
+    del fd, w
+
+
 def test_config2_ground_state(dev, sq4x4):
     H, S, v0 = sq4x4
     g = json.load(open(os.path.join(GOLD, "sq4x4_n8_8_U8.json")))
@@ -342,7 +366,7 @@ def test_shared_tables_between_handles(dev):
 
 
 @pytest.mark.parametrize("scale", [2.0 ** 900, 2.0 ** -900, 1e-310, 3.7e12])
-@pytest.mark.parametrize("case", [("sq3x3", 4, 5, 1.0, 6.0), ("ring6", 3, 3, 0.75, 2.5)])
+@pytest.mark.parametrize("case", [("sq3x3", 4, 5, 1.0, 6.0), ("ring6", 3, 3, 0.75, 2.5), ("ring8", 4, 3, 1.3, 7.0)])
 def test_hv_f64_extreme_scales(dev, case, scale):
     """The fixed-point grid follows max|v| wherever it lies in the binary64
     range (huge, tiny, subnormal inputs), both in the standalone H*v and in a

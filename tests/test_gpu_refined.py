@@ -101,3 +101,81 @@ def test_refined_stored_vectors_equal_replay(dev):
     for r, p in ((r1, p1), (r2, p2)):
         assert torch.equal(p, p0)
         assert {k: v for k, v in r.items() if k != "replayed"} == {k: v for k, v in r0.items() if k != "replayed"}
+
+
+def _two_lowest(S):
+    """E0 and lambda_2 of the sector (dense or ARPACK on the explicit H)."""
+    if S.D <= 2000:
+        w = np.linalg.eigvalsh(S.dense())
+        return float(w[0]), float(w[1])
+    from scipy.sparse.linalg import eigsh
+    w = np.sort(eigsh(S.explicit(), k=2, which="SA", tol=1e-14, v0=start_vector(S.D, seed=9))[0])
+    return float(w[0]), float(w[1])
+
+
+@pytest.mark.parametrize("case", CASES[:4])
+@pytest.mark.parametrize("iters_f32", [12, 1000])
+def test_refined_gap_is_lower_estimate_and_bound_covers_error(dev, case, iters_f32):
+    """The gap the refined solver reports is a lower estimate of lambda_2 - E0
+    (the binary32 run's second Ritz value minus its residual), also when that
+    run is cut short after 12 steps and lambda_2 is far from converged; the
+    error bound then covers the actual error of the binary64 energy."""
+    name, nup, ndn, t, U = case
+    ns, bonds = lattice_by_name(name)
+    S = Sector(ns, bonds, nup, ndn, t, U)
+    e0, e1 = _two_lowest(S)
+    H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+    v0 = torch.from_numpy(start_vector(S.D, seed=1234)).to(dev)
+    r = hub.lanczos_ground_state_refined(H, v0, iters_f32, 1e-10)
+    assert r["gap"] <= (e1 - e0) + 1e-9 * max(1.0, abs(e0)), (r, e1 - e0)
+    err = abs(r["energy"] - e0)
+    assert err <= r["error_bound"] + 1e-12 * max(1.0, abs(e0)), (r, e0)
+    if r["status"] == hub.HUB_OK:
+        assert err <= 1e-9 * max(1.0, abs(e0))
+
+
+@pytest.mark.parametrize("case", CASES[:3] + [("ring6", 3, 3, 1.0, 0.0)])
+@pytest.mark.parametrize("dt", ["f64", "f32"])
+def test_plain_solver_psi_out_and_err_bound(dev, case, dt):
+    """lanczos_ground_state with psi_out: the replayed Ritz vector is a unit
+    vector whose binary64 Rayleigh quotient (the oracle's explicit H) is the
+    returned energy and whose residual is small; err_bound covers the error."""
+    name, nup, ndn, t, U = case
+    ns, bonds = lattice_by_name(name)
+    S = Sector(ns, bonds, nup, ndn, t, U)
+    e0, _ = _two_lowest(S)
+    H = hub.hubbard_sector_create(ns, bonds, nup, ndn, t, U)
+    tdt = torch.float64 if dt == "f64" else torch.float32
+    v0 = torch.from_numpy(start_vector(S.D, seed=1234)).to(dev, tdt)
+    psi = torch.full((S.D,), float("nan"), dtype=torch.float64, device=dev)
+    tol = 1e-10 if dt == "f64" else 1e-5
+    r = hub.lanczos_ground_state(H, v0, 1000, tol, psi_out=psi)
+    assert r["status"] == hub.HUB_OK
+    p = psi.cpu().numpy()
+    assert abs(np.linalg.norm(p) - 1.0) < 1e-12
+    Hp = S.explicit() @ p
+    th = float(p @ Hp)
+    res = float(np.linalg.norm(Hp - th * p))
+    if dt == "f64":
+        assert abs(r["energy"] - e0) <= 1e-9 * max(1.0, abs(e0))
+        assert abs(th - e0) <= 1e-9 * max(1.0, abs(e0))
+        assert res <= 1e-6
+    else:
+        assert abs(th - e0) <= 1e-6 * max(1.0, abs(e0))
+        assert res <= 1e-2
+    assert abs(r["energy"] - e0) <= r["err_bound"] + 1e-12 * max(1.0, abs(e0))
+
+
+@pytest.mark.parametrize("iters", [20, 40])
+def test_plain_solver_err_bound_when_stopped_early(dev, iters):
+    """A run stopped before convergence reports a bound that still covers its
+    (large) error: the second Ritz pair then resolves little of the gap."""
+    ns, bonds = lattice_by_name("ring10")
+    S = Sector(ns, bonds, 5, 5, 1.0, 3.0)
+    e0, e1 = _two_lowest(S)
+    H = hub.hubbard_sector_create(ns, bonds, 5, 5, 1.0, 3.0)
+    v0 = torch.from_numpy(start_vector(S.D, seed=1234)).to(dev)
+    r = hub.lanczos_ground_state(H, v0, iters, 0.0)
+    err = abs(r["energy"] - e0)
+    assert err > 1e-9 * abs(e0)                        # genuinely unconverged
+    assert err <= r["err_bound"]

@@ -325,3 +325,16 @@ def test_planted_transposed_rank_is_caught(monkeypatch):
 def test_planted_dropped_interaction_is_caught(monkeypatch):
     monkeypatch.setattr(Sector, "diagonal", lambda self: np.zeros(self.D))
     assert abs(e0(2, dimer(), 1, 1, 1.0, 4.0) - cf.dimer_energy(1.0, 4.0)) > 0.1
+
+
+@pytest.mark.parametrize("name,nup,ndn,U", [("ring6", 3, 3, 4.0), ("sq3x3", 2, 3, 6.5), ("ring7", 3, 2, 2.0)])
+def test_energy_routes_agree(name, nup, ndn, U):
+    """The three routes of oracle.energies (dense, eigsh on the explicit H,
+    matrix-free Kronecker-sum Lanczos) give the same E0 where all apply."""
+    from oracle.energies import ground_energy
+    from workload import lattice_by_name
+    ns, bonds = lattice_by_name(name)
+    es = {r: ground_energy(ns, bonds, nup, ndn, 1.0, U, route=r)[0] for r in ("dense", "eigsh", "lanczos")}
+    ref = es["dense"]
+    for r, e in es.items():
+        assert abs(e - ref) <= 1e-11 * max(1.0, abs(ref)), (r, e, ref)
