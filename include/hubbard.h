@@ -261,8 +261,10 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
  * err_bound is the a-posteriori bound min(rho, rho^2 / gap) on |energy - E0|,
  * gap = (theta_2 - rho_2) - energy from the second distinct Ritz pair of T_m
  * (theta_2, residual estimate rho_2); when T_m resolves no positive gap it is
- * rho.  The quadratic form assumes no eigenvalue of H other than E0 lies below
- * theta_2 - rho_2.
+ * rho.  The quadratic form assumes no eigenvalue of H other than E0 (counted
+ * once if degenerate) lies below theta_2 - rho_2.  A rounding floor
+ * (W_up + W_dn + 1) u max(1, max|a_j|, max b_j) is added, u = 2^-47 for
+ * HUB_F64 (the fixed-point grid of unit vectors) and 2^-24 for HUB_F32.
  * Breakdown (beta_{m+1} <= 1e-13 * max(1, max|a|, max b)) counts as
  * converged.  Returns HUB_ENOTCONV (with the best energy in *out) when
  * max_iters is reached with tol > 0 and rho >= tol.  Synchronises `stream`.
@@ -317,7 +319,8 @@ uint64_t hubbard_kernel_launches(void);
  * (theta_2 - rho_2) - theta with theta_2 its second distinct Ritz value and
  * rho_2 that Ritz pair's residual estimate (a Ritz value alone only bounds
  * lambda_2 from above).  error_bound = min(residual, residual^2 / gap), or the
- * residual when gap <= 0; the quadratic form assumes no eigenvalue other than
+ * residual when gap <= 0, plus the binary64 rounding floor of
+ * lanczos_ground_state; the quadratic form assumes no eigenvalue other than
  * E0 lies below theta_2 - rho_2.  The polish runs until error_bound <= tol *
  * max(1, |energy|) (at most 60 binary64 steps); status is HUB_OK exactly when
  * that holds.  Returns HUB_ENOTCONV otherwise.  Synchronises stream.

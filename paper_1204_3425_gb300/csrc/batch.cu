@@ -732,6 +732,7 @@ struct hubbard_batch {
     std::vector<int64_t> voff;                 // n + 1 vector offsets
     int64_t total = 0;                         // sum of D
     std::vector<double> cost;                  // per-sector work estimate
+    std::vector<int> hops1;                    // per-sector W_up + W_dn + 1 (error-bound floor)
     hub::SectorDesc* d_sec = nullptr;
     int32_t* d_rp = nullptr;
     uint32_t* d_ent = nullptr;
@@ -991,6 +992,7 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
             s.U = d.U;
             B->sec.push_back(s);
             B->cost.push_back((double)s.D * (cu.hops + cd.hops + 8.0));
+            B->hops1.push_back(cu.W + cd.W + 1);
             B->rows_all += s.Dup;
             B->total += (s.D + 1) / 2 * 2;           // keep every sector 16-byte aligned
             B->voff[(size_t)i + 1] = B->total;
@@ -1134,7 +1136,8 @@ int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iter
         const double* A = ab.data() + (size_t)i * 2 * max_iters;
         const double* Bv = A + max_iters;
         const double gap = tridiag_gap_lower(A, Bv, m, Bv[m - 1], r.energy);
-        r.err_bound = energy_error_bound(r.residual, gap);
+        r.err_bound = energy_error_bound(r.residual, gap) +
+                      rounding_floor(B->hops1[(size_t)i], HUB_F64, tridiag_scale(A, Bv, m));
     }
     return HUB_OK;
 }

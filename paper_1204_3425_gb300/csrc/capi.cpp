@@ -182,6 +182,21 @@ static SlotColouring colour_group(const std::vector<std::vector<int32_t>>& lane_
     return R;
 }
 
+// sign-split list: per row the +1 targets first, then the -1 targets, each
+// ascending; npos[r] = number of +1 targets of row r
+void sign_split_list(const SpinTables& T, std::vector<int32_t>& npos, std::vector<uint32_t>& pnl) {
+    npos.assign((size_t)T.D, 0);
+    pnl.assign(T.tgt.size(), 0u);
+    for (int64_t r = 0; r < T.D; ++r) {
+        int32_t o = T.rowptr[(size_t)r], np = 0;
+        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
+            if (T.sign[(size_t)k] > 0) { pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k]; ++np; }
+        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
+            if (T.sign[(size_t)k] < 0) pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k];
+        npos[(size_t)r] = np;
+    }
+}
+
 int upload_spin(const SpinTables& T, DevSpin& d) {
     std::vector<uint32_t> ent(T.tgt.size());
     for (size_t k = 0; k < T.tgt.size(); ++k)
@@ -198,17 +213,9 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
     const bool narrow = rb.narrow;
     std::vector<uint32_t>& bent = rb.ent;
     if (bent.empty()) bent.push_back(0u);
-    // sign-split list: +1 targets first, then -1 targets, each ascending
-    std::vector<int32_t> npos((size_t)T.D);
-    std::vector<uint32_t> pnl(T.tgt.size());
-    for (int64_t r = 0; r < T.D; ++r) {
-        int32_t o = T.rowptr[(size_t)r], np = 0;
-        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
-            if (T.sign[(size_t)k] > 0) { pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k]; ++np; }
-        for (int32_t k = T.rowptr[(size_t)r]; k < T.rowptr[(size_t)r + 1]; ++k)
-            if (T.sign[(size_t)k] < 0) pnl[(size_t)o++] = (uint32_t)T.tgt[(size_t)k];
-        npos[(size_t)r] = np;
-    }
+    std::vector<int32_t> npos;
+    std::vector<uint32_t> pnl;
+    sign_split_list(T, npos, pnl);
     int rc;
     if ((rc = upload(&d.pn_ptr, T.rowptr.data(), T.rowptr.size()))) return rc;
     if ((rc = upload(&d.pn_npos, npos.data(), npos.size()))) return rc;
@@ -509,6 +516,7 @@ int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, in
         cudaError_t e = cudaMalloc((void**)&H->red, kRedSlots * sizeof(double));
         if (e == cudaSuccess) e = cudaMalloc((void**)&H->status, 4 * sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(H->status, 0, 4 * sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(H->red, 0, kRedSlots * sizeof(double));
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
     }
     if (rc != HUB_OK) {
@@ -969,7 +977,8 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     }
     out->energy = R.theta;
     out->residual = R.rho;
-    out->err_bound = energy_error_bound(R.rho, gap);
+    out->err_bound = energy_error_bound(R.rho, gap) +
+                     rounding_floor(H->host[0].W + H->host[1].W + 1, dtype, tridiag_scale(R.a.data(), R.b.data(), m));
     out->iters = m;
     out->breakdown = R.broke ? 1 : 0;
     out->status = R.converged ? HUB_OK : HUB_ENOTCONV;
@@ -1093,7 +1102,9 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         return rc;
     out->energy = th;
     out->residual = std::sqrt(std::max(r2, 0.0));
-    out->error_bound = energy_error_bound(out->residual, gap);
+    const double floor64 = rounding_floor(H->host[0].W + H->host[1].W + 1, HUB_F64,
+                                          std::max(1.0, std::fabs(th) + out->residual));
+    out->error_bound = energy_error_bound(out->residual, gap) + floor64;
     out->iters_f64 = 0;
 
     // 4. short binary64 Lanczos polish from psi when the bound misses tol * |theta|
@@ -1114,7 +1125,9 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         if ((rc = lanczos_core(H, psi, HUB_F64, 60, rho_target, HUB_F64, pf, pg, s, P))) return rc;
         out->energy = P.theta;
         out->residual = P.rho;
-        out->error_bound = energy_error_bound(P.rho, gap);
+        out->error_bound = energy_error_bound(P.rho, gap) +
+                           rounding_floor(H->host[0].W + H->host[1].W + 1, HUB_F64,
+                                          tridiag_scale(P.a.data(), P.b.data(), (int)P.a.size()));
         out->iters_f64 = (int)P.a.size();
     }
     out->status = (out->error_bound <= tol * std::max(1.0, std::fabs(out->energy))) ? HUB_OK : HUB_ENOTCONV;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstddef>
 #include <memory>
@@ -186,6 +187,19 @@ double tridiag_gap_lower(const double* a, const double* b, int m, double b_next,
 inline double energy_error_bound(double rho, double gap) {
     if (gap > 0.0) return std::min(rho, rho * rho / gap);
     return rho;
+}
+// floor of the computed energy's rounding error: hops of one H*v element
+// (hops_plus_one = W_up + W_dn + 1, or any upper bound of it) times the unit
+// of the H*v arithmetic (2^-47: the binary64 path rounds unit vectors to that
+// fixed-point grid; 2^-24: binary32) times scale = max(1, max|a_j|, max b_j)
+// (a bound on |H| restricted to the Krylov space)
+inline double rounding_floor(int hops_plus_one, int dtype, double scale) {
+    return (double)hops_plus_one * (dtype == HUB_F64 ? 0x1p-47 : 0x1p-24) * scale;
+}
+inline double tridiag_scale(const double* a, const double* b, int m) {
+    double s = 1.0;
+    for (int i = 0; i < m; ++i) s = std::max(s, std::max(std::fabs(a[i]), std::fabs(b[i])));
+    return s;
 }
 
 }  // namespace hub
