@@ -160,16 +160,19 @@ int hubbard_apply_reference(hubbard_t H, const void* v, void* w, int dtype, void
  * vec_cols: columns per lane in the up phase (each 0 = automatic, else 1, 2
  * or 4; binary64 uses at most 2, and a width the row length does not divide
  * is narrowed); ctas_rows: row-phase CTAs per SM (0 = automatic, 1 or 2);
- * ctas_cols: accepted (0, 1 or 2) and reserved.  A choice whose buffers do
- * not fit in shared memory falls back to the largest one that does.
+ * ctas_cols: binary64 up phase of a standalone H*v (0 = automatic; 1 = 4 CTAs
+ * per SM, epilogue operands loaded after the hop sum; 2 = 3 CTAs per SM, the
+ * own element and row-phase sum requested before it).  A choice whose buffers
+ * do not fit in shared memory falls back to the largest one that does.
  * Results do not depend on the schedule: every output sums its hops in one
  * fixed order (binary32) or exactly (binary64 fixed point). */
 int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols);
 
 /* Autotuner for the schedule above (the paper tunes elements per thread by
  * hand, Sec. 4.3): times three hubbard_apply calls (after a
- * warm one) for every vec_rows x vec_cols in {1, 2 (, 4 for binary32)} and
- * ctas_rows in {1, 2} on the caller's v, w (device, dtype, as hubbard_apply;
+ * warm one) for every vec_rows x vec_cols in {1, 2 (, 4 for binary32)},
+ * ctas_rows in {1, 2} and (binary64) ctas_cols in {1, 2} on the caller's v, w
+ * (device, dtype, as hubbard_apply;
  * w is overwritten), keeps the fastest on the handle and writes it to
  * chosen[4] = {vec_rows, vec_cols, ctas_rows, ctas_cols} (nullable).
  * Synchronises `stream`.  On error the previous schedule is kept. */

@@ -616,11 +616,12 @@ int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, vo
     int pick[4] = {0, 0, 0, 0};
     for (int vr = 1; vr <= vmax && rc == HUB_OK; vr *= 2)
         for (int vc = 1; vc <= vmax && rc == HUB_OK; vc *= 2)
-            for (int cr = 1; cr <= 2 && rc == HUB_OK; ++cr) {
+            for (int cr = 1; cr <= 2 && rc == HUB_OK; ++cr)
+            for (int cc = 1; cc <= (dtype == HUB_F64 ? 2 : 1) && rc == HUB_OK; ++cc) {
                 H->vec_rows = vr;
                 H->vec_cols = vc;
                 H->ctas_rows = cr;
-                H->ctas_cols = 0;
+                H->ctas_cols = dtype == HUB_F64 ? cc : 0;
                 if ((rc = hubbard_apply(H, v, w, dtype, stream))) break;    // warm (allocates scratch)
                 cudaEventRecord(e0, s);
                 for (int k = 0; k < 3 && rc == HUB_OK; ++k) rc = hubbard_apply(H, v, w, dtype, stream);
@@ -637,7 +638,7 @@ int hubbard_autotune_schedule(hubbard_t H, const void* v, void* w, int dtype, vo
                     pick[0] = vr;
                     pick[1] = vc;
                     pick[2] = cr;
-                    pick[3] = 0;
+                    pick[3] = H->ctas_cols;
                 }
             }
     cudaEventDestroy(e0);

@@ -243,8 +243,10 @@ struct FFAcc {
 // chunk, which keeps that chunk of X resident in L2 while all rows are
 // combined, and consecutive rows share part of their neighbours (L1 reuse).
 // RED: also accumulate <W, fv>, <W, W> and <fv, fv> into part (block_sum3_store).
-template <int VPL, bool FAST>
-__global__ void __launch_bounds__(256, 4) k_up_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
+// PRE: the epilogue's own element and Y are requested before the gathers (their
+// HBM latency then overlaps the hop sum); CT: CTAs per SM the launch bounds keep
+template <int VPL, bool FAST, bool PRE = false, int CT = 4>
+__global__ void __launch_bounds__(256, CT) k_up_f64x(const int2* __restrict__ X, const long long* __restrict__ Y,
                                                      double* w, const double* w_old, int64_t Dup, int64_t Ddn,
                                                      const int32_t* __restrict__ ptr,
                                                      const int32_t* __restrict__ npos,
@@ -281,6 +283,13 @@ __global__ void __launch_bounds__(256, 4) k_up_f64x(const int2* __restrict__ X, 
         const int64_t uend = min(rb * kUpRows + kUpRows, Dup);
         for (int64_t u = rb * kUpRows + warp; u < uend; u += nw) {
             const int32_t kb = ptr[u];
+            [[maybe_unused]] int4 t4p;
+            [[maybe_unused]] longlong2 y2p;
+            if constexpr (PRE && VPL == 2) {
+                const int64_t J = u * Ddn + c;
+                t4p = __ldg(reinterpret_cast<const int4*>(X + J));
+                y2p = __ldcs(reinterpret_cast<const longlong2*>(Y + J));
+            }
             IV P{}, N{};
             uniform_hops<IV>(list, kb, ptr[u + 1] - kb, npos[u], lane, P, N,
                 [&](uint32_t t) { return __ldg(reinterpret_cast<const IV*>(reinterpret_cast<const int2*>(base) + (int64_t)t * Ddn)); },
@@ -293,10 +302,17 @@ __global__ void __launch_bounds__(256, 4) k_up_f64x(const int2* __restrict__ X, 
                 long long yv[VPL];
                 if constexpr (VPL == 2) {
                     lo[0] = P.x - N.x; hi[0] = P.y - N.y; lo[1] = P.z - N.z; hi[1] = P.w - N.w;
-                    const int4 t4 = __ldg(reinterpret_cast<const int4*>(X + J));
+                    int4 t4;
+                    longlong2 y2;
+                    if constexpr (PRE) {
+                        t4 = t4p;
+                        y2 = y2p;
+                    } else {
+                        t4 = __ldg(reinterpret_cast<const int4*>(X + J));
+                        y2 = __ldcs(reinterpret_cast<const longlong2*>(Y + J));
+                    }
                     xo[0] = make_int2(t4.x, t4.y);
                     xo[1] = make_int2(t4.z, t4.w);
-                    const longlong2 y2 = __ldcs(reinterpret_cast<const longlong2*>(Y + J));
                     yv[0] = y2.x;
                     yv[1] = y2.y;
                 } else {
@@ -779,11 +795,20 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
 #undef ROWS64_U
         const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
         const int up_grid = sms() * (part != nullptr ? 3 : 4);
+        // standalone up phase: request the epilogue's own element and Y before
+        // the gathers (at 3 CTAs/SM for the registers) where that measured
+        // faster -- the 128-bit epilogue and rows staged from global memory --
+        // unless the schedule fixes it (ctas_cols 1: no, 2: yes)
+        const bool pre = H->ctas_cols == 2 || (H->ctas_cols == 0 && (!ep.fast || va == 0));
 #define UP64(K, V, F)                                                                                       \
     K<V, F><<<up_grid, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,             \
         up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax
+#define UP64P(V, F, CT)                                                                                     \
+    k_up_f64x<V, F, true, CT><<<sms() * CT, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn,  \
+        up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax)
 #define UP64_R(V, F)                                                                                        \
     if (part != nullptr) { UP64(k_up_step_f64x, V, F), (const double*)v, part); }                          \
+    else if (V == 2 && pre) { UP64P(V, F, 3); }                                                            \
     else { UP64(k_up_f64x, V, F)); }
         if (vpl == 2) {
             if (ep.fast) { UP64_R(2, true) } else { UP64_R(2, false) }
@@ -791,6 +816,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             if (ep.fast) { UP64_R(1, true) } else { UP64_R(1, false) }
         }
 #undef UP64_R
+#undef UP64P
 #undef UP64
         if (part != nullptr && nparts != nullptr) *nparts = up_grid;
         HUB_CUDA(cudaGetLastError());

@@ -314,7 +314,8 @@ def test_argument_errors(dev):
 @pytest.mark.parametrize("dt", ["f64", "f32"])
 def test_schedules_bit_identical_and_autotune(dev, dt):
     """Every H*v schedule (rows per block, row CTAs per SM, up-phase columns per
-    lane) gives the same bits; the autotuner keeps one of them."""
+    lane, binary64 up-phase variant) gives the same bits; the autotuner keeps
+    one of them."""
     tdt = torch.float64 if dt == "f64" else torch.float32
     ns, bonds = lattice_by_name("sq4x3")
     H = hub.hubbard_sector_create(ns, bonds, 6, 5, 1.0, 4.0)
@@ -327,13 +328,14 @@ def test_schedules_bit_identical_and_autotune(dev, dt):
             if vr > vmax or vc > vmax:
                 continue
             for cr in (1, 2):
-                hub.hubbard_set_schedule(H, vr, vc, cr, 0)
-                hub.hubbard_apply(H, v, w)
-                if ref is None:
-                    ref = w.clone()
-                assert torch.equal(w, ref), (vr, vc, cr)
+                for cc in ((0, 1, 2) if dt == "f64" else (0,)):
+                    hub.hubbard_set_schedule(H, vr, vc, cr, cc)
+                    hub.hubbard_apply(H, v, w)
+                    if ref is None:
+                        ref = w.clone()
+                    assert torch.equal(w, ref), (vr, vc, cr, cc)
     chosen = hub.hubbard_autotune_schedule(H, v, w)
-    assert chosen[0] in (1, 2, 4) and chosen[1] in (1, 2, 4) and chosen[2] in (1, 2)
+    assert chosen[0] in (1, 2, 4) and chosen[1] in (1, 2, 4) and chosen[2] in (1, 2) and chosen[3] in (0, 1, 2)
     hub.hubbard_apply(H, v, w)
     assert torch.equal(w, ref)
 
