@@ -88,8 +88,11 @@ void free_dev(hubbard_sector* H) {
     H->fx_bytes = 0;
     cudaFree(H->red);
     cudaFree(H->status);
+    cudaFree(H->lz);
     H->red = nullptr;
     H->status = nullptr;
+    H->lz = nullptr;
+    H->lz_cap = 0;
 }
 
 // Slot assignment for the row-phase gathers of one group of 32 states.
@@ -816,9 +819,186 @@ struct LanczosRun {
 
 // store (optional): f_j is also copied to store + j * store_stride bytes for
 // j < store_cap (the Ritz vector is then one pass over the stored vectors).
+static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype,
+                             void* f, void* g, cudaStream_t s, LanczosRun& R, double rel_tol, char* store,
+                             size_t store_stride, int store_cap);
+
+// The handle's device-resident Lanczos control block and a/b history for
+// cap steps (grown on demand; freed with the handle).
+static int ensure_lz(hubbard_sector* H, int cap) {
+    if (H->lz != nullptr && H->lz_cap >= cap) return HUB_OK;
+    cudaFree(H->lz);
+    H->lz = nullptr;
+    H->lz_cap = 0;
+    const size_t bytes = 256 + 2 * (size_t)cap * sizeof(double);
+    cudaError_t e = cudaMalloc(&H->lz, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(Lanczos control)");
+    H->lz_cap = cap;
+    return HUB_OK;
+}
+
+// Records step m-1 (a_m, b_{m+1} appended to R) and applies the run's stop
+// tests in the order of Algorithm 1's loop; returns true when the run ends.
+static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol, double rel_tol) {
+    R.a.push_back(aj);
+    double s_last = 1.0;
+    tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
+    R.rho = bn * std::fabs(s_last);
+    double scale = 1.0;
+    for (double x : R.a) scale = std::max(scale, std::fabs(x));
+    for (double x : R.b) scale = std::max(scale, x);
+    R.b.push_back(bn);
+    if (bn <= 1e-13 * scale) {
+        R.broke = true;
+        R.converged = true;
+        return true;
+    }
+    if ((tol > 0.0 && R.rho < tol) || (rel_tol > 0.0 && R.rho < rel_tol * std::max(1.0, std::fabs(R.theta)))) {
+        R.converged = true;
+        return true;
+    }
+    return false;
+}
+
+// Algorithm 1 in the two-vector form on caller buffers f, g (D elements of
+// dtype each; the handle's H*v scratch must already point at 16 D bytes).
+// f receives v0 / |v0| (v0 of dtype v0_dtype; binary64 -> binary32 allowed).
+// store (optional): f_j is also copied to store + j * store_stride bytes for
+// j < store_cap (the Ritz vector is then one pass over the stored vectors).
+//
+// Device-resident: every step's scalars (beta_j for the H*v, the deferred
+// update's coefficients, a_j and b_{j+1}) are formed and consumed on the
+// device (k_lz_finish, k_lz_finish2), so steps are enqueued in chunks with no
+// host round trip inside a chunk; after each chunk the recorded a_j, b_{j+1}
+// come back and the host runs the tridiagonal stop test on every step of it,
+// in order.  A chunk can run a few steps past the one that stops the run:
+// those steps only overwrite f, g (and stored vectors past it), never the
+// recorded values of the steps before.  The kernels and roundings are those of
+// the host-driven step, so the a_j, b_{j+1} are the same bit for bit.
+// Chunks are longer for small sectors (where a round trip costs more than a
+// step); sectors of more than 2.7e6 elements (one step per chunk) and those
+// whose H*v kernels do not fuse the reductions take the host-driven loop.
 static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype, void* f,
                         void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0, char* store = nullptr,
                         size_t store_stride = 0, int store_cap = 0) {
+    // steps per chunk: about 4e6 / D (a round trip is worth a few steps of a small sector)
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(4e6 / (double)H->D)));
+    // one step per round trip gains nothing over the host-driven loop, whose
+    // explicit branch costs no launches when unused (same results either way)
+    if (chunk == 1 || !hv_phases_fuse(H, dtype) || H->fx_bytes < (size_t)H->D * 16)
+        return lanczos_core_host(H, v0, v0_dtype, max_iters, tol, dtype, f, g, s, R, rel_tol, store, store_stride,
+                                 store_cap);
+    int rc;
+    const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
+    if ((rc = ensure_lz(H, m_cap))) return rc;
+    LzDev* dv = reinterpret_cast<LzDev*>(H->lz);
+    double* ha = reinterpret_cast<double*>((char*)H->lz + 256);
+    double* hb = ha + H->lz_cap;
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+    n0 = std::sqrt(n0);
+    if (!(n0 > 0.0) || !std::isfinite(n0)) return fail(HUB_EINVAL, "start vector has zero or non-finite norm");
+    if (v0_dtype == dtype) rc = launch_copy_normalise(v0, f, H->D, dtype, 1.0 / n0, s);
+    else rc = launch_f64_to_f32_scaled((const double*)v0, (float*)f, H->D, 1.0 / n0, s);
+    if (rc) return rc;
+    const size_t vbytes = (size_t)H->D * elem_size(dtype);
+    if (store_cap > 0 && cudaMemcpyAsync(store, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(HUB_ECUDA, "store f_0");
+    if (cudaMemsetAsync(g, 0, vbytes, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    const LzDev init{0.0, 0.0, 1.0, 0.0, 0, 1, {0, 0}};
+    if (cudaMemcpyAsync(dv, &init, sizeof(init), cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return fail(HUB_ECUDA, "Lanczos control upload");
+    std::vector<double> ab(2 * (size_t)chunk);
+    // one Lanczos step: g <- H f_j - b_j g with f_j completed from the previous
+    // step inside the row phase, then the explicit branch (a no-op when fused)
+    auto step = [&](void* fj, void* gj, bool first, uint64_t& launches, cudaStream_t st) -> int {
+        const uint64_t c0 = hubbard_kernel_launches();
+        RowUpdate upd{gj, 0.0, 1.0, dv};
+        bool fused = false;
+        int r = launch_hv_fast(H, fj, gj, dtype, 0.0, gj, 1023, st, H->red, &fused, first ? nullptr : &upd, dv, ha, hb);
+        if (r == HUB_OK && !fused) r = fail(HUB_ECUDA, "device-resident Lanczos: fused reductions unavailable");
+        if (r == HUB_OK) r = launch_lz_explicit(dv, fj, gj, H->D, dtype, H->red, hb, st);
+        launches = hubbard_kernel_launches() - c0;
+        return r;
+    };
+    // Small sectors are bound by kernel launches: with no vectors to store, the
+    // steps of either parity (f, g or g, f) are the same launches every time, so
+    // each is captured once as a CUDA graph (after one step run directly, which
+    // also settles every kernel attribute) and replayed on the caller's stream.
+    // Capture runs on a private stream (the legacy default stream cannot be
+    // captured); nothing executes during capture.
+    bool graphs = chunk > 1 && store_cap == 0 && m_cap > 4 && hv_phases_capturable(H, dtype);
+    cudaGraphExec_t gx[2] = {nullptr, nullptr};
+    uint64_t glaunch[2] = {0, 0};
+    cudaStream_t cap = nullptr;
+    if (graphs && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        graphs = false;
+    }
+    struct GraphGuard {
+        cudaGraphExec_t* g;
+        cudaStream_t cap;
+        ~GraphGuard() {
+            for (int i = 0; i < 2; ++i)
+                if (g[i]) cudaGraphExecDestroy(g[i]);
+            if (cap) cudaStreamDestroy(cap);
+        }
+    } gguard{gx, cap};
+    int j = 0;
+    bool done = false;
+    while (!done && j < m_cap) {
+        const int j0 = j;
+        const int j1 = std::min(m_cap, j0 + chunk);
+        for (; j < j1; ++j) {
+            const int par = j & 1;
+            if (graphs && j >= 1 && gx[par] == nullptr) {
+                cudaGraph_t gr = nullptr;
+                const cudaError_t e0 = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+                if (e0 != cudaSuccess) return cuda_fail(e0, "Lanczos step capture");
+                uint64_t n = 0;
+                const int r = step(f, g, false, n, cap);
+                const cudaError_t e = cudaStreamEndCapture(cap, &gr);
+                if (r != HUB_OK) {
+                    if (gr) cudaGraphDestroy(gr);
+                    return r;
+                }
+                if (e != cudaSuccess) return cuda_fail(e, "Lanczos step capture");
+                const cudaError_t e2 = cudaGraphInstantiate(&gx[par], gr, 0);
+                cudaGraphDestroy(gr);
+                if (e2 != cudaSuccess) return cuda_fail(e2, "Lanczos step graph");
+                glaunch[par] = n;
+                count_launches(-(int)n);              // captured, not run: counted at each replay
+            }
+            if (graphs && j >= 1) {
+                if (cudaGraphLaunch(gx[par], s) != cudaSuccess) return fail(HUB_ECUDA, "Lanczos step graph launch");
+                count_launches((int)glaunch[par]);
+            } else {
+                uint64_t n = 0;
+                if ((rc = step(f, g, j == 0, n, s))) return rc;
+            }
+            // f holds the final f_j from here on
+            if (j >= 1 && j < store_cap &&
+                cudaMemcpyAsync(store + (size_t)j * store_stride, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail(HUB_ECUDA, "store f_j");
+            std::swap(f, g);
+        }
+        // the recorded a_j, b_{j+1} of the chunk, then the stop tests step by step
+        if (cudaMemcpyAsync(ab.data(), ha + j0, (size_t)(j1 - j0) * sizeof(double), cudaMemcpyDeviceToHost, s) !=
+                cudaSuccess ||
+            cudaMemcpyAsync(ab.data() + chunk, hb + j0, (size_t)(j1 - j0) * sizeof(double), cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess)
+            return fail(HUB_ECUDA, "Lanczos history download");
+        if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+        for (int q = 0; q < j1 - j0 && !done; ++q) done = lanczos_record_step(R, ab[(size_t)q], ab[(size_t)chunk + q], tol, rel_tol);
+    }
+    if (tol <= 0.0 && rel_tol <= 0.0) R.converged = true;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+    return HUB_OK;
+}
+
+static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype,
+                             void* f, void* g, cudaStream_t s, LanczosRun& R, double rel_tol, char* store,
+                             size_t store_stride, int store_cap) {
     int rc;
     double n0 = 0.0;
     if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
@@ -848,23 +1028,7 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
         if (j >= 1 && j < store_cap &&
             cudaMemcpyAsync(store + (size_t)j * store_stride, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return fail(HUB_ECUDA, "store f_j");
-        R.a.push_back(aj);
-        double s_last = 1.0;
-        tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
-        R.rho = bn * std::fabs(s_last);
-        double scale = 1.0;
-        for (double x : R.a) scale = std::max(scale, std::fabs(x));
-        for (double x : R.b) scale = std::max(scale, x);
-        R.b.push_back(bn);
-        if (bn <= 1e-13 * scale) {
-            R.broke = true;
-            R.converged = true;
-            break;
-        }
-        if ((tol > 0.0 && R.rho < tol) || (rel_tol > 0.0 && R.rho < rel_tol * std::max(1.0, std::fabs(R.theta)))) {
-            R.converged = true;
-            break;
-        }
+        if (lanczos_record_step(R, aj, bn, tol, rel_tol)) break;
         if (pending) {
             upd = RowUpdate{f, -aj, 1.0 / bn};
             have_upd = true;

@@ -162,10 +162,14 @@ __device__ __forceinline__ void block_sum3_store(double a, double b, double c, d
 }
 
 
-// m such that max(|t|, |U| Ns, |beta|) * 2^m <= 2^61
-inline EpiParams make_epilogue(double t, double U, int ns, double beta) {
+// m such that M * 2^m <= 2^61, M = max(|t|, |U| Ns, |beta|, 2 (W |t| + |U| Ns)):
+// the last term bounds every Lanczos beta (beta_{j+1} <= |H| <= W |t| + |U| Ns
+// by Gershgorin, W = W_up + W_dn), so m does not depend on beta and a device-
+// resident step can form round(-beta 2^m) itself with the host's m
+inline EpiParams make_epilogue(double t, double U, int ns, double beta, int W) {
     EpiParams p{};
-    double M = std::max(std::fabs(t), std::max(std::fabs(U) * ns, std::fabs(beta)));
+    const double gersh = 2.0 * ((double)W * std::fabs(t) + std::fabs(U) * ns);
+    double M = std::max(std::max(std::fabs(t), std::fabs(U) * ns), std::max(std::fabs(beta), gersh));
     int m = 0;
     if (M > 0) {
         int ex = 0;

@@ -59,8 +59,15 @@ __global__ void __launch_bounds__(1024, 1) k_rows_f64x(std::conditional_t<UPD, d
                                                      const int32_t* __restrict__ bcnt,
                                                      const EntT* __restrict__ ent,
                                                      const int* __restrict__ emax_p, int fixed_emax,
-                                                     const double* __restrict__ fo, double ua, double uinv) {
+                                                     const double* __restrict__ fo, double ua, double uinv,
+                                                     const LzDev* __restrict__ dv) {
     using S = typename FxVec<VEC>::T;
+    if constexpr (UPD) {
+        if (dv != nullptr) {                              // device-resident step: the update's scalars
+            ua = dv->ua;
+            uinv = dv->uinv;
+        }
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* X = reinterpret_cast<S*>(smem_raw);
     const int emax = fixed_emax > 0 ? fixed_emax : max(*emax_p, 1);
@@ -363,12 +370,18 @@ __global__ void __launch_bounds__(256, 3) k_up_step_f64x(const int2* __restrict_
                                                      const uint32_t* __restrict__ su,
                                                      const uint32_t* __restrict__ sd, EpiParams ep,
                                                      const int* __restrict__ emax_p, int fixed_emax,
-                                                     const double* __restrict__ fv, double* part) {
+                                                     const double* __restrict__ fv, double* part,
+                                                     const LzDev* __restrict__ dv) {
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     using IV = typename FxVec<VPL>::T;
     __shared__ long long Bs[33];
     for (int i = threadIdx.x; i < 33; i += blockDim.x) Bs[i] = i < ep.nB ? ep.B[i] : 0;
     __syncthreads();
+    if (dv != nullptr) {                                  // device-resident step: beta_j on the device
+        const double b = dv->beta;
+        ep.mbeta = -b;
+        ep.Bbeta = llround(ldexp(-b, ep.m));
+    }
     const int emax = fixed_emax > 0 ? fixed_emax : max(*emax_p, 1);
     const int k = 1070 - emax;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -507,8 +520,9 @@ __global__ void __launch_bounds__(256, up32_ctas<VPL, RED>()) k_up_f32(const flo
                                                     const uint32_t* __restrict__ list,
                                                     const uint32_t* __restrict__ su,
                                                     const uint32_t* __restrict__ sd, float mt, float U, float mbeta,
-                                                    double* part) {
+                                                    double* part, const LzDev* __restrict__ dv) {
     FFAcc s1, s2, s3;
+    if (dv != nullptr) mbeta = (float)-dv->beta;          // device-resident step: beta_j on the device
     using V = typename F32Vec<VPL>::T;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     constexpr int CC = 32 * VPL;
@@ -580,8 +594,15 @@ __global__ void __launch_bounds__(1024, 1) k_rows_f32(std::conditional_t<UPD, fl
                                                     int64_t Ddn, const int64_t* __restrict__ boff,
                                                     const int32_t* __restrict__ bcnt,
                                                     const EntT* __restrict__ ent,
-                                                    const float* __restrict__ fo, float ua, float uinv) {
+                                                    const float* __restrict__ fo, float ua, float uinv,
+                                                    const LzDev* __restrict__ dv) {
     using S = typename F32Vec<VEC>::T;
+    if constexpr (UPD) {
+        if (dv != nullptr) {
+            ua = (float)dv->ua;
+            uinv = (float)dv->uinv;
+        }
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S* X = reinterpret_cast<S*>(smem_raw);
     float* Xf = reinterpret_cast<float*>(smem_raw);
@@ -716,6 +737,9 @@ void allow_smem() {
     (void)once;
 }
 
+// a grid of at most `full` CTAs and no more than the work items
+int grid_cap(int full, int64_t items) { return (int)std::max<int64_t>(1, std::min<int64_t>(full, items)); }
+
 // requested vec (0 = largest that fits), capped to what fits
 int choose_vec(int req, int64_t len, int elem_bytes, int vmax, int reserve) {
     const int fit = pick_vec(len, elem_bytes, vmax, reserve);
@@ -727,9 +751,20 @@ int choose_vec(int req, int64_t len, int elem_bytes, int vmax, int reserve) {
 
 // Returns HUB_OK and launches, or returns -1 when the staging buffers do not fit
 // (the caller then uses the single-pass gather kernel).
+bool hv_phases_fuse(const hubbard_sector* H, int dtype) {
+    if (sms() * 5 > kPartStride) return false;
+    return dtype == HUB_F64 || choose_vec(H->vec_rows, H->Ddn, 4, 4, 0) != 0;
+}
+
+bool hv_phases_capturable(const hubbard_sector* H, int dtype) {
+    // the binary64 path for rows longer than shared memory uploads its fixed
+    // exponent word from host memory on each call
+    return hv_phases_fuse(H, dtype) && (dtype == HUB_F32 || choose_vec(H->vec_rows, H->Ddn, 8, 2, 0) != 0);
+}
+
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
                      void* ybuf, int fixed_emax, cudaStream_t s, double* part, int* nparts,
-                     const RowUpdate* upd) {
+                     const RowUpdate* upd, const LzDev* dv) {
     if (nparts != nullptr) *nparts = 0;
     if (sms() * 5 > kPartStride) part = nullptr;        // partial arrays too short: no fused reduction
     const DevSpin& up = H->dev[0];
@@ -747,7 +782,8 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
         // the deferred update goes into the row phase when it stages rows in
         // shared memory with a fixed exponent bound; otherwise it is one pass first
         if (upd != nullptr && (va == 0 || fixed_emax <= 0)) {
-            if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s)) return rc;
+            if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s, upd->dv))
+                return rc;
             upd = nullptr;
         }
         if (fixed_emax <= 0) {
@@ -755,11 +791,10 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             launch_max_exponent((const double*)v, H->D, emax, s);
             if (w_old != nullptr) launch_max_exponent((const double*)w_old, H->D, emax, s);
         }
-        const Launch LA = shape((size_t)staged_slots(Ddn) * 8 * std::max(va, 1), H->ctas_rows);
+        Launch LA = shape((size_t)staged_slots(Ddn) * 8 * std::max(va, 1), H->ctas_rows);
+        LA.blocks = grid_cap(LA.blocks, (Dup + std::max(va, 1) - 1) / std::max(va, 1));   // no idle CTAs
         long long* Y = (long long*)ybuf;
         int2* Xg = (int2*)((char*)ybuf + (size_t)H->D * 8);
-        // columns per lane in the up phase: 2 when Ddn is even (16-byte loads)
-        const int vpl = ((Ddn & 1) == 0 && H->vec_cols != 1) ? 2 : 1;
         int extra = 0;
         if (va == 0) {
             // rows longer than shared memory: fixed-point copy first, then gathers through L1/L2
@@ -772,9 +807,11 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
             }
             launch_to_fixed((const double*)v, H->D, Xg, em, s);
             if (dn16) {
-                k_rows_global_f64x<uint16_t><<<sms() * 4, 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, dn.ent16);
+                k_rows_global_f64x<uint16_t><<<grid_cap(sms() * 4, Dup), 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off,
+                                                                                         dn.blk_cnt, dn.ent16);
             } else {
-                k_rows_global_f64x<uint32_t><<<sms() * 4, 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off, dn.blk_cnt, dn.ent32);
+                k_rows_global_f64x<uint32_t><<<grid_cap(sms() * 4, Dup), 512, 0, s>>>(Xg, Y, Dup, Ddn, dn.blk_off,
+                                                                                         dn.blk_cnt, dn.ent32);
             }
             extra = 2;
         } else {
@@ -782,7 +819,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     allow_smem<k_rows_f64x<V, E, U>>();                                                                      \
     k_rows_f64x<V, E, U><<<LA.blocks, LA.threads, LA.smem, s>>>((double*)const_cast<void*>(v), Y, Xg, Dup,   \
         Ddn, dn.blk_off, dn.blk_cnt, P, emax, fixed_emax, upd ? (const double*)upd->fo : nullptr,            \
-        upd ? upd->a : 0.0, upd ? upd->inv : 1.0)
+        upd ? upd->a : 0.0, upd ? upd->inv : 1.0, upd ? upd->dv : nullptr)
 #define ROWS64(V, E, P) if (upd) { ROWS64_U(V, E, P, true); } else { ROWS64_U(V, E, P, false); }
         if (va == 2) {
             if (dn16) { ROWS64(2, uint16_t, dn.ent16); } else { ROWS64(2, uint32_t, dn.ent32); }
@@ -793,8 +830,11 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
         }
 #undef ROWS64
 #undef ROWS64_U
-        const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0);
-        const int up_grid = sms() * (part != nullptr ? 3 : 4);
+        const EpiParams ep = make_epilogue(H->t, H->U, H->ns, w_old ? beta : 0.0, H->host[0].W + H->host[1].W);
+        // columns per lane in the up phase: 2 when Ddn is even (16-byte loads)
+        const int vpl = ((Ddn & 1) == 0 && H->vec_cols != 1) ? 2 : 1;
+        const int64_t up_items = ((Ddn + 32 * vpl - 1) / (32 * vpl)) * ((Dup + kUpRows - 1) / kUpRows);
+        const int up_grid = grid_cap(sms() * (part != nullptr ? 3 : 4), up_items);
         // standalone up phase: request the epilogue's own element and Y before
         // the gathers (at 3 CTAs/SM for the registers) where that measured
         // faster -- the 128-bit epilogue and rows staged from global memory --
@@ -804,10 +844,11 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     K<V, F><<<up_grid, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn, up.pn_ptr,             \
         up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax
 #define UP64P(V, F, CT)                                                                                     \
-    k_up_f64x<V, F, true, CT><<<sms() * CT, 256, 0, s>>>(Xg, Y, (double*)w, (const double*)w_old, Dup, Ddn,  \
+    k_up_f64x<V, F, true, CT><<<grid_cap(sms() * CT, up_items), 256, 0, s>>>(Xg, Y, (double*)w,               \
+        (const double*)w_old, Dup, Ddn,                                                                    \
         up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, ep, emax, fixed_emax)
 #define UP64_R(V, F)                                                                                        \
-    if (part != nullptr) { UP64(k_up_step_f64x, V, F), (const double*)v, part); }                          \
+    if (part != nullptr) { UP64(k_up_step_f64x, V, F), (const double*)v, part, dv); }                      \
     else if (V == 2 && pre) { UP64P(V, F, 3); }                                                            \
     else { UP64(k_up_f64x, V, F)); }
         if (vpl == 2) {
@@ -826,7 +867,8 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     // binary32
     const int va = choose_vec(H->vec_rows, Ddn, 4, 4, 0);
     if (va == 0) return -1;
-    const Launch LA = shape((size_t)staged_slots(Ddn) * 4 * va, H->ctas_rows);
+    Launch LA = shape((size_t)staged_slots(Ddn) * 4 * va, H->ctas_rows);
+    LA.blocks = grid_cap(LA.blocks, (Dup + va - 1) / va);
     float* Y = (float*)ybuf;
     // columns per lane in the up phase: the widest aligned vector load, capped by vec_cols
     int vpl = (Ddn & 3) == 0 ? 4 : ((Ddn & 1) == 0 ? 2 : 1);
@@ -835,7 +877,7 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     allow_smem<k_rows_f32<V, E, U>>();                                                                      \
     k_rows_f32<V, E, U><<<LA.blocks, LA.threads, LA.smem, s>>>((float*)const_cast<void*>(v), Y, Dup, Ddn,   \
         dn.blk_off, dn.blk_cnt, P, upd ? (const float*)upd->fo : nullptr, upd ? (float)upd->a : 0.0f,       \
-        upd ? (float)upd->inv : 1.0f)
+        upd ? (float)upd->inv : 1.0f, upd ? upd->dv : nullptr)
 #define ROWS32(V, E, P) if (upd) { ROWS32_U(V, E, P, true); } else { ROWS32_U(V, E, P, false); }
 #define BOTH32(M, V, F, P16, P32) if (F) { M(V, uint16_t, P16); } else { M(V, uint32_t, P32); }
     if (va == 4) { BOTH32(ROWS32, 4, dn16, dn.ent16, dn.ent32) }
@@ -847,15 +889,16 @@ int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, doubl
     int up_grid = 0;
 #define UP32(V)                                                                                            \
     {                                                                                                      \
-        up_grid = sms() * (part != nullptr ? up32_ctas<V, true>() : up32_ctas<V, false>());               \
+        up_grid = grid_cap(sms() * (part != nullptr ? up32_ctas<V, true>() : up32_ctas<V, false>()),      \
+                           ((Ddn + 32 * V - 1) / (32 * V)) * ((Dup + kUpRows - 1) / kUpRows));             \
         if (part != nullptr)                                                                               \
             k_up_f32<V, true><<<up_grid, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old,  \
                 Dup, Ddn, up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t,           \
-                (float)H->U, (float)-beta, part);                                                          \
+                (float)H->U, (float)-beta, part, dv);                                                      \
         else                                                                                               \
             k_up_f32<V, false><<<up_grid, 256, 0, s>>>((const float*)v, Y, (float*)w, (const float*)w_old, \
                 Dup, Ddn, up.pn_ptr, up.pn_npos, up.pn_list, up.states, dn.states, (float)-H->t,           \
-                (float)H->U, (float)-beta, part);                                                          \
+                (float)H->U, (float)-beta, part, nullptr);                                                 \
     }
     if (vpl == 4) { UP32(4) } else if (vpl == 2) { UP32(2) } else { UP32(1) }
 #undef UP32

@@ -102,6 +102,9 @@ struct hubbard_sector {
     // small device scratch for reductions: partial sums, status words
     double* red = nullptr;           // [kRedSlots]
     int* status = nullptr;           // [4]
+    // device-resident Lanczos control (LzDev) and a/b history for lz_cap steps
+    void* lz = nullptr;
+    int lz_cap = 0;
 };
 
 namespace hub {
@@ -112,14 +115,28 @@ constexpr int kPartStride = 1024;    // stride of the partial arrays of a fused 
 // process-wide count of kernel launches (hubbard_kernel_launches)
 void count_launches(int n);
 
+// Device-resident control of a Lanczos run (Algorithm 1 steps enqueued without
+// a host round trip): the scalars the next step's kernels read, written by the
+// one-CTA kernels that close each step (k_lz_finish, k_lz_finish2).
+struct LzDev {
+    double beta;      // b_j: coefficient of w_old (= f_{j-1}) in the next H*v
+    double ua, uinv;  // the next row phase's deferred update f <- (f + ua fo) * uinv
+    double a;         // a_j of the step in progress
+    int j;            // steps closed so far (index of the step in progress)
+    int fused;        // the step in progress took beta^2 from the fused sums
+    int pad[2];
+};
+
 // A Lanczos vector update deferred into the next H*v (Algorithm 1, the
 // normalisation of the new vector): before v is used, every element becomes
 // v <- (v + a fo) * inv, rounded as launch_axpy_scale (one fused multiply-add,
 // then one multiplication), and is written back to v.  The row phase applies
 // it while staging rows, which saves the separate pass over three vectors.
+// dv != nullptr: a and inv are read on the device from dv->ua, dv->uinv.
 struct RowUpdate {
     const void* fo;
     double a, inv;
+    const LzDev* dv = nullptr;
 };
 
 // kernels.cu launchers -------------------------------------------------------
@@ -129,9 +146,13 @@ int launch_hv_reference(const hubbard_sector* H, const void* v, void* w, int dty
 // reductions); *fused tells whether that happened (the kernel path in use may
 // not support it).
 // upd != nullptr: v is first updated in place as RowUpdate describes.
+// dv != nullptr (device-resident step): beta is read on the device from
+// dv->beta, and the fused sums are closed by k_lz_finish into dv and the
+// history arrays ha, hb (requires part).
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta,
                    const void* w_old, int fixed_emax, cudaStream_t s, double* part = nullptr,
-                   bool* fused = nullptr, const RowUpdate* upd = nullptr);
+                   bool* fused = nullptr, const RowUpdate* upd = nullptr, LzDev* dv = nullptr,
+                   double* ha = nullptr, double* hb = nullptr);
 // hv_phases.cu: two-phase shared-memory H*v; -1 when the staging buffers do not fit.
 // fixed_emax > 0 fixes the fixed-point exponent bound (vectors of norm <= 1:
 // 1023); otherwise it is computed from v and w_old.
@@ -142,7 +163,12 @@ int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double 
 // it stages rows in shared memory); -1 is returned before anything is launched.
 int launch_hv_phases(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
                      void* ybuf, int fixed_emax, cudaStream_t s, double* part = nullptr, int* nparts = nullptr,
-                     const RowUpdate* upd = nullptr);
+                     const RowUpdate* upd = nullptr, const LzDev* dv = nullptr);
+// whether launch_hv_phases fuses the Lanczos reductions for this sector and dtype
+bool hv_phases_fuse(const hubbard_sector* H, int dtype);
+// whether a fused launch_hv_phases call with a fixed exponent bound enqueues
+// only kernels (no host-memory copies), so a CUDA graph can capture it
+bool hv_phases_capturable(const hubbard_sector* H, int dtype);
 // max biased binary64 exponent of |v| folded into *emax (atomicMax; caller zeroes it)
 void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s);
 // binary64 -> (lo, hi) fixed point with the exponent bound *emax (read on the device)
@@ -153,7 +179,16 @@ int reduce_partials_host(double* partials, cudaStream_t s, double* out);
 // the three sums of a fused reduction: out[k] = part[kRedSlots-1-k]
 int reduce_partials3_host(double* partials, cudaStream_t s, double out[3]);
 // y <- (y + a x) * inv, rounded as launch_axpy_nrm2 followed by launch_scale
-int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s);
+// (dv != nullptr: a and inv read on the device from dv->ua, dv->uinv)
+int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s,
+                      const LzDev* dv = nullptr);
+// the explicit branch of a device-resident step: when dv->fused is 0,
+// y <- y - dv->a x with partial sums of y^2 in partials, then k_lz_finish2
+// sums them and closes the step (no-ops when the step was closed fused)
+int launch_lz_explicit(LzDev* dv, const void* x, void* y, int64_t n, int dtype, double* partials, double* hb,
+                       cudaStream_t s);
+// k_lz_finish: the fused sums of an up phase (np per-CTA partials) closed into dv, ha, hb
+int launch_lz_finish(double* part, int np, LzDev* dv, double* ha, double* hb, cudaStream_t s);
 int launch_axpy(double a, const void* x, void* y, int64_t n, int dtype, cudaStream_t s);
 int launch_axpy_nrm2(double a, const void* x, void* y, int64_t n, int dtype, double* partials,
                      cudaStream_t s);

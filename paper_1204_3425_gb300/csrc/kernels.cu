@@ -253,14 +253,103 @@ __global__ void k_scale(T a, T* __restrict__ y, int64_t n) {
 }
 
 // y <- (y + a x) * inv with the roundings of k_axpy_nrm2 then k_scale
+// (dv: a, inv from the device-resident step control)
 __global__ void k_axpy_scale_f64(double a, double inv, const double* __restrict__ x, double* __restrict__ y,
-                                 int64_t n) {
+                                 int64_t n, const LzDev* __restrict__ dv) {
+    if (dv != nullptr) {
+        a = dv->ua;
+        inv = dv->uinv;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = fma(a, x[i], y[i]) * inv;
 }
-__global__ void k_axpy_scale_f32(float a, float inv, const float* __restrict__ x, float* __restrict__ y, int64_t n) {
+__global__ void k_axpy_scale_f32(float a, float inv, const float* __restrict__ x, float* __restrict__ y, int64_t n,
+                                 const LzDev* __restrict__ dv) {
+    if (dv != nullptr) {
+        a = (float)dv->ua;
+        inv = (float)dv->uinv;
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = fmaf(a, x[i], y[i]) * inv;
+}
+
+// Device-resident Lanczos step control (Algorithm 1): the step in progress is
+// closed with beta_{j+1}; the next step's H*v then reads beta = beta_{j+1} and
+// completes f_{j+1} = (g + ua f_j) * uinv while staging its rows: ua = -a_j
+// when g still holds H f_j - beta_j f_{j-1} (fused sums), 0 when the explicit
+// branch already subtracted a_j f_j.  The roundings are those of the host-driven
+// step (sqrt and the division are correctly rounded on both sides).
+__device__ __forceinline__ void lz_close_step(LzDev* dv, double* hb, double bn, bool fused) {
+    const int j = dv->j;
+    hb[j] = bn;
+    dv->ua = fused ? -dv->a : 0.0;
+    dv->uinv = 1.0 / bn;
+    dv->beta = bn;
+    dv->j = j + 1;
+}
+
+// the three fused sums in the order of k_finish_sum3, then a_j and, unless the
+// difference <w,w> - 2a^2 + a^2 <f,f> cancels more than six digits, beta_{j+1}
+__global__ void k_lz_finish(double* partials, int nb, LzDev* dv, double* ha, double* hb) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        a += partials[i];
+        b += partials[kPartStride + i];
+        c += partials[2 * kPartStride + i];
+    }
+    a = block_sum(a);
+    b = block_sum(b);
+    c = block_sum(c);
+    if (threadIdx.x == 0) {
+        partials[kRedSlots - 1] = a;
+        partials[kRedSlots - 2] = b;
+        partials[kRedSlots - 3] = c;
+        const double b2 = b - 2.0 * a * a + a * a * c;
+        const int fused = b2 > 1e-6 * b;
+        dv->a = a;
+        dv->fused = fused;
+        ha[dv->j] = a;
+        if (fused) lz_close_step(dv, hb, sqrt(fmax(b2, 0.0)), true);
+    }
+}
+
+// explicit branch: y <- y - a x and partial sums of y^2, as k_axpy_nrm2_*
+__global__ void k_lz_axpy_nrm2_f64(const LzDev* __restrict__ dv, const double* __restrict__ x, double* __restrict__ y,
+                                   int64_t n, double* partials) {
+    if (dv->fused) return;
+    const double a = -dv->a;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double r = fma(a, x[i], y[i]);
+        y[i] = r;
+        s = fma(r, r, s);
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+__global__ void k_lz_axpy_nrm2_f32(const LzDev* __restrict__ dv, const float* __restrict__ x, float* __restrict__ y,
+                                   int64_t n, double* partials) {
+    if (dv->fused) return;
+    const float a = (float)(-dv->a);
+    FF acc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float r = fmaf(a, x[i], y[i]);
+        y[i] = r;
+        acc.add_product(r, r);
+    }
+    const double s = block_sum(acc.value());
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+// sums the explicit branch's partials in the order of k_finish_sum, closes the step
+__global__ void k_lz_finish2(double* partials, int nb, LzDev* dv, double* hb) {
+    if (dv->fused) return;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) s += partials[i];
+    s = block_sum(s);
+    if (threadIdx.x == 0) {
+        partials[kRedSlots - 1] = s;
+        lz_close_step(dv, hb, sqrt(fmax(s, 0.0)), false);
+    }
 }
 
 template <typename T>
@@ -373,26 +462,35 @@ void launch_max_exponent(const double* v, int64_t n, int* emax, cudaStream_t s) 
 }
 
 int launch_hv_fast(hubbard_sector* H, const void* v, void* w, int dtype, double beta, const void* w_old,
-                   int fixed_emax, cudaStream_t s, double* part, bool* fused, const RowUpdate* upd) {
+                   int fixed_emax, cudaStream_t s, double* part, bool* fused, const RowUpdate* upd, LzDev* dv,
+                   double* ha, double* hb) {
     const DevSpin& up = H->dev[0];
     const DevSpin& dn = H->dev[1];
     const int grid = grid_for(H->Dup, 1, sm_count() * 16);
     if (fused != nullptr) *fused = false;
     if (H->fx_bytes >= (size_t)H->D * 16) {
         int np = 0;
-        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s, part, &np, upd);
+        int rc = launch_hv_phases(H, v, w, dtype, beta, w_old, H->fx_scratch, fixed_emax, s, part, &np, upd, dv);
         if (rc != -1) {
             if (rc == HUB_OK && part != nullptr && np > 0) {
-                k_finish_sum3<<<1, 1024, 0, s>>>(part, np);
-                HUB_CUDA(cudaGetLastError());
-                count_launches(1);
+                if (dv != nullptr) {
+                    if ((rc = launch_lz_finish(part, np, dv, ha, hb, s))) return rc;
+                } else {
+                    k_finish_sum3<<<1, 1024, 0, s>>>(part, np);
+                    HUB_CUDA(cudaGetLastError());
+                    count_launches(1);
+                }
                 if (fused != nullptr) *fused = true;
+            } else if (rc == HUB_OK && dv != nullptr) {
+                return fail(HUB_EINVAL, "device-resident Lanczos step without fused reductions");
             }
             return rc;
         }
     }
+    if (dv != nullptr) return fail(HUB_EINVAL, "device-resident Lanczos step without fused reductions");
     if (upd != nullptr) {
-        if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s)) return rc;
+        if (int rc = launch_axpy_scale(upd->a, upd->inv, upd->fo, const_cast<void*>(v), H->D, dtype, s, upd->dv))
+            return rc;
     }
     if (dtype == HUB_F32) {
         if (w_old != nullptr || beta != 0.0) return fail(HUB_EINVAL, "f32 fused step not available");
@@ -463,10 +561,29 @@ int reduce_partials3_host(double* partials, cudaStream_t s, double out[3]) {
     return HUB_OK;
 }
 
-int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s) {
+int launch_axpy_scale(double a, double inv, const void* x, void* y, int64_t n, int dtype, cudaStream_t s,
+                      const LzDev* dv) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
-    if (dtype == HUB_F64) k_axpy_scale_f64<<<g, kThreads, 0, s>>>(a, inv, (const double*)x, (double*)y, n);
-    else k_axpy_scale_f32<<<g, kThreads, 0, s>>>((float)a, (float)inv, (const float*)x, (float*)y, n);
+    if (dtype == HUB_F64) k_axpy_scale_f64<<<g, kThreads, 0, s>>>(a, inv, (const double*)x, (double*)y, n, dv);
+    else k_axpy_scale_f32<<<g, kThreads, 0, s>>>((float)a, (float)inv, (const float*)x, (float*)y, n, dv);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_lz_explicit(LzDev* dv, const void* x, void* y, int64_t n, int dtype, double* partials, double* hb,
+                       cudaStream_t s) {
+    const int g = red_grid(n);
+    if (dtype == HUB_F64) k_lz_axpy_nrm2_f64<<<g, kThreads, 0, s>>>(dv, (const double*)x, (double*)y, n, partials);
+    else k_lz_axpy_nrm2_f32<<<g, kThreads, 0, s>>>(dv, (const float*)x, (float*)y, n, partials);
+    k_lz_finish2<<<1, 1024, 0, s>>>(partials, g, dv, hb);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(2);
+    return HUB_OK;
+}
+
+int launch_lz_finish(double* part, int np, LzDev* dv, double* ha, double* hb, cudaStream_t s) {
+    k_lz_finish<<<1, 1024, 0, s>>>(part, np, dv, ha, hb);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;
