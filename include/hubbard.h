@@ -52,7 +52,8 @@ typedef enum {
     HUB_ECUDA = 3,     /* a CUDA runtime call failed                               */
     HUB_ENOTCONV = 4,  /* Lanczos hit max_iters before the residual test passed    */
     HUB_ETIMEOUT = 5,  /* a bounded device wait gave up                            */
-    HUB_EDEVICE = 6    /* a kernel reported an error through its status word       */
+    HUB_EDEVICE = 6,   /* a kernel reported an error through its status word       */
+    HUB_EPENDING = 7   /* hubbard_server_poll: the request has not finished yet    */
 } hub_status;
 
 typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
@@ -67,7 +68,7 @@ typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
  * copies them to the current device and returns an opaque handle.  The
  * tables of one spin depend only on (device, Ns, bonds, N): handles with the
  * same ones share a single read-only device copy (also between the two spins
- * when Nup = Ndn), and the library keeps the 64 most recently built table
+ * when Nup = Ndn), and the library keeps the 256 most recently built table
  * sets after their last handle is gone, so re-creating a sector skips the
  * build.  Each handle has its own t, U, schedule and scratch.
  *   Ns      number of sites, 1..32
@@ -307,7 +308,7 @@ uint64_t hubbard_kernel_launches(void);
  *   3. binary64 Rayleigh quotient theta = <psi|H|psi> and residual
  *      |H psi - theta psi| with the binary64 H*v;
  *   4. if the error bound below exceeds tol max(1,|theta|): a short binary64
- *      Lanczos run started from psi (at most 60 steps).
+ *      Lanczos run started from psi (at most 150 steps).
  *   v0          binary64 device start vector (normalised inside)
  *   workspace   >= lanczos_refined_workspace_bytes(H) bytes (40 D), 256-aligned;
  *               every further 4 D bytes (rounded up to 256) stores one more
@@ -324,9 +325,11 @@ uint64_t hubbard_kernel_launches(void);
  * lambda_2 from above).  error_bound = min(residual, residual^2 / gap), or the
  * residual when gap <= 0, plus the binary64 rounding floor of
  * lanczos_ground_state; the quadratic form assumes no eigenvalue other than
- * E0 lies below theta_2 - rho_2.  The polish runs until error_bound <= tol *
- * max(1, |energy|) (at most 60 binary64 steps); status is HUB_OK exactly when
- * that holds.  Returns HUB_ENOTCONV otherwise.  Synchronises stream.
+ * E0 lies below theta_2 - rho_2.  After a polish, gap is the larger of that
+ * estimate and the same estimate from the polish's own tridiagonal matrix.  The
+ * polish runs until error_bound <= tol * max(1, |energy|) (at most 150
+ * binary64 steps); status is HUB_OK exactly when that holds.  Returns
+ * HUB_ENOTCONV otherwise.  Synchronises stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double energy;
@@ -410,6 +413,93 @@ int hubbard_selftest_wait_timeout(void* stream);
  * (written to *chosen).  Synchronises `stream`. */
 int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
                            size_t ws_bytes, void* stream, int64_t* chosen);
+
+/* ---------------------------------------------------------------------------
+ * Continuous-batching ground-state server (the paper notes that a small
+ * sector alone leaves the GPU idle, Sec. 5; this serves many requests at once).
+ * Requests are queued by hubbard_server_submit and taken by worker lanes (host
+ * threads, each with its own non-blocking stream) as soon as a lane is free and
+ * the request's device-memory footprint fits what remains of the budget, first
+ * come first served within each queue:
+ *   D <= small_max_dim                : the small queue; a small lane takes every
+ *       small request waiting (up to batch_max, within the budget) into one
+ *       launch of the batched solver, each sector a one-CTA task (the launch
+ *       occupies one CTA per sector, the rest of the GPU stays with the other
+ *       lanes); tol is relative, rho < tol max(1, |theta|);
+ *   small_max_dim < D <= mid_max_dim  : a big lane, binary64 Lanczos
+ *       (lanczos_ground_state, absolute rho < tol);
+ *   D > mid_max_dim                   : a big lane, binary32 Lanczos with
+ *       binary64 refinement (lanczos_ground_state_refined, tol relative on the
+ *       error bound), keeping up to store_vectors binary32 Lanczos vectors
+ *       within half of the spare budget.
+ * Requests that arrive while others run are admitted as lanes and memory free
+ * up, and their work overlaps on the device.  Handles, batches and buffers of
+ * a lane are allocated on its stream, so finishing a request never waits for
+ * the whole device.  A request whose solve fails carries that status; the
+ * others are unaffected.  Start vectors: hubbard_fill_start_vector(seed).
+ *
+ * host_solver (testing without a GPU): when non-NULL, lanes call it instead
+ * of any CUDA work, with the request, its path (0 batch, 1 binary64,
+ * 2 refined) and a result to fill; its return value is the request's status.
+ * It is called from the lane threads, concurrently.
+ * ------------------------------------------------------------------------- */
+typedef struct hubbard_server* hubbard_server_t;
+
+typedef struct {
+    int32_t ns, nup, ndn, n_bonds;
+    const int32_t* bonds;      /* host, 2 * n_bonds; copied by submit */
+    double t, U;
+    uint64_t seed;             /* start vector (hubbard_fill_start_vector) */
+} hubbard_request;
+
+typedef int (*hubbard_host_solver)(void* ctx, uint64_t ticket, const hubbard_request* req, int path,
+                                   lanczos_result* out);
+
+typedef struct {
+    double hbm_budget;         /* bytes of device memory for requests (<= 0: 80 % of the free memory) */
+    int32_t small_lanes;       /* concurrent micro-batches */
+    int32_t big_lanes;         /* concurrent single-sector solves */
+    int64_t small_max_dim;
+    int64_t mid_max_dim;
+    int32_t max_iters;         /* <= 0: 1000 */
+    int32_t batch_max;         /* requests per micro-batch (<= 0: 1024) */
+    int32_t store_vectors;     /* binary32 Lanczos vectors kept per refined request (>= 0) */
+    int32_t reserved;
+    double tol;                /* <= 0: 1e-10 */
+    hubbard_host_solver host_solver;
+    void* host_ctx;
+} hubbard_server_opts;
+
+typedef struct {
+    lanczos_result result;     /* energy, residual, err_bound, iters, status, breakdown */
+    int32_t path;              /* 0 batch, 1 binary64, 2 refined */
+    int32_t reserved;
+    double t_submit, t_admit, t_done;   /* seconds since the server was created */
+} hubbard_served;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t verified;          /* completed with status HUB_OK and err_bound <= 1e-9 max(1, |energy|) */
+    int64_t running, queued, max_backlog;
+    int64_t batches, batched_requests, binary64_solves, refined_solves;
+    double budget_bytes, peak_bytes, free_bytes;
+} hubbard_server_stats;
+
+/* Starts the lanes.  HUB_EINVAL for no lane, negative thresholds or, with a
+ * host solver, no budget; HUB_ECUDA without a device. */
+int hubbard_server_create(const hubbard_server_opts* opts, hubbard_server_t* out);
+/* Queues one request (non-blocking); *ticket identifies it.  HUB_ENOMEM when
+ * its footprint exceeds the whole budget, HUB_EINVAL for a bad sector. */
+int hubbard_server_submit(hubbard_server_t S, const hubbard_request* req, uint64_t* ticket);
+/* HUB_OK with *out filled once the request has finished (its own status in
+ * out->result.status), HUB_EPENDING before (out holds its times so far). */
+int hubbard_server_poll(hubbard_server_t S, uint64_t ticket, hubbard_served* out);
+/* Blocks until the request finishes or timeout_s passes (HUB_ETIMEOUT). */
+int hubbard_server_wait(hubbard_server_t S, uint64_t ticket, double timeout_s, hubbard_served* out);
+int hubbard_server_stats_get(hubbard_server_t S, hubbard_server_stats* out);
+/* Stops taking work, lets running requests finish, joins the lanes; queued
+ * requests are dropped. */
+void hubbard_server_destroy(hubbard_server_t S);
 
 /* Message for the last failing call on this thread ("" if none). */
 const char* hubbard_last_error(void);

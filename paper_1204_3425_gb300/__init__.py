@@ -13,10 +13,10 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libhubbard.so")
 
-HUB_OK, HUB_EINVAL, HUB_ENOMEM, HUB_ECUDA, HUB_ENOTCONV, HUB_ETIMEOUT, HUB_EDEVICE = range(7)
+HUB_OK, HUB_EINVAL, HUB_ENOMEM, HUB_ECUDA, HUB_ENOTCONV, HUB_ETIMEOUT, HUB_EDEVICE, HUB_EPENDING = range(8)
 HUB_F64, HUB_F32 = 0, 1
 STATUS_NAMES = {0: "HUB_OK", 1: "HUB_EINVAL", 2: "HUB_ENOMEM", 3: "HUB_ECUDA", 4: "HUB_ENOTCONV",
-                5: "HUB_ETIMEOUT", 6: "HUB_EDEVICE"}
+                5: "HUB_ETIMEOUT", 6: "HUB_EDEVICE", 7: "HUB_EPENDING"}
 
 
 class HubError(RuntimeError):
@@ -29,6 +29,35 @@ class LanczosResult(ctypes.Structure):
     _fields_ = [("energy", ctypes.c_double), ("residual", ctypes.c_double), ("err_bound", ctypes.c_double),
                 ("iters", ctypes.c_int32), ("status", ctypes.c_int32), ("breakdown", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class HubbardRequest(ctypes.Structure):
+    _fields_ = [("ns", ctypes.c_int32), ("nup", ctypes.c_int32), ("ndn", ctypes.c_int32),
+                ("n_bonds", ctypes.c_int32), ("bonds", ctypes.c_void_p), ("t", ctypes.c_double),
+                ("U", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
+HOST_SOLVER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, ctypes.POINTER(HubbardRequest),
+                               ctypes.c_int, ctypes.POINTER(LanczosResult))
+
+
+class ServerOpts(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_double), ("small_lanes", ctypes.c_int32), ("big_lanes", ctypes.c_int32),
+                ("small_max_dim", ctypes.c_int64), ("mid_max_dim", ctypes.c_int64), ("max_iters", ctypes.c_int32),
+                ("batch_max", ctypes.c_int32), ("store_vectors", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("host_solver", HOST_SOLVER), ("host_ctx", ctypes.c_void_p)]
+
+
+class Served(ctypes.Structure):
+    _fields_ = [("result", LanczosResult), ("path", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "completed", "failed", "verified", "running", "queued",
+                                              "max_backlog", "batches", "batched_requests", "binary64_solves",
+                                              "refined_solves")] + \
+               [(n, ctypes.c_double) for n in ("budget_bytes", "peak_bytes", "free_bytes")]
 
 
 _lib = None
@@ -68,6 +97,12 @@ SIGNATURES = {
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
+    "hubbard_server_create": (ctypes.c_int, [P, P]),
+    "hubbard_server_submit": (ctypes.c_int, [P, P, P]),
+    "hubbard_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, P]),
+    "hubbard_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, D, P]),
+    "hubbard_server_stats_get": (ctypes.c_int, [P, P]),
+    "hubbard_server_destroy": (None, [P]),
     "hubbard_last_error": (ctypes.c_char_p, []),
 }
 
@@ -423,3 +458,86 @@ def hubbard_kernel_launches():
 
 def hubbard_last_error():
     return load_library().hubbard_last_error().decode()
+
+
+PATH_NAMES = {0: "batch", 1: "binary64", 2: "refined"}
+
+
+class Server:
+    """Owns a hubbard_server_t: the native continuous-batching server.
+
+    submit() queues one request (lattice bonds, fillings, t, U, seed) and
+    returns its ticket; poll() / wait() return the result dict once it has
+    finished.  host_solver (tests without a GPU): a Python callable
+    (ticket, request_dict, path) -> dict(energy, residual, err_bound, iters,
+    status) run by the lanes instead of the CUDA solvers."""
+
+    def __init__(self, hbm_budget=0.0, small_lanes=2, big_lanes=8, small_max_dim=20_000, mid_max_dim=200_000,
+                 max_iters=1000, batch_max=1024, store_vectors=128, tol=1e-10, host_solver=None):
+        lib = load_library()
+        self._cb = None
+        cb = HOST_SOLVER()
+        if host_solver is not None:
+            def _solve(ctx, ticket, req, path, out):
+                q = req.contents
+                try:
+                    r = host_solver(int(ticket), dict(ns=q.ns, nup=q.nup, ndn=q.ndn, t=q.t, U=q.U, seed=q.seed),
+                                    int(path))
+                except Exception:  # noqa: BLE001  (a failing request fails alone)
+                    return HUB_EDEVICE
+                o = out.contents
+                o.energy, o.residual = float(r["energy"]), float(r.get("residual", 0.0))
+                o.err_bound, o.iters = float(r.get("err_bound", 0.0)), int(r.get("iters", 1))
+                o.status, o.breakdown = int(r.get("status", HUB_OK)), 0
+                return int(r.get("status", HUB_OK))
+            self._cb = cb = HOST_SOLVER(_solve)
+        opts = ServerOpts(float(hbm_budget), int(small_lanes), int(big_lanes), int(small_max_dim), int(mid_max_dim),
+                          int(max_iters), int(batch_max), int(store_vectors), 0, float(tol), cb, None)
+        h = ctypes.c_void_p()
+        _check(lib.hubbard_server_create(ctypes.byref(opts), ctypes.byref(h)))
+        self.handle = h
+        self._bonds = {}
+
+    def submit(self, ns, bonds, nup, ndn, t, U, seed):
+        arr = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+        req = HubbardRequest(int(ns), int(nup), int(ndn), arr.size // 2, arr.ctypes.data if arr.size else None,
+                             float(t), float(U), int(seed))
+        tk = ctypes.c_uint64()
+        _check(load_library().hubbard_server_submit(self.handle, ctypes.byref(req), ctypes.byref(tk)))
+        return tk.value
+
+    @staticmethod
+    def _served(sv):
+        r = sv.result
+        return dict(energy=r.energy, residual=r.residual, err_bound=r.err_bound, iters=r.iters, status=r.status,
+                    path=PATH_NAMES.get(sv.path, sv.path), t_submit=sv.t_submit, t_admit=sv.t_admit, t_done=sv.t_done)
+
+    def poll(self, ticket):
+        """The result dict once finished, else None."""
+        sv = Served()
+        rc = load_library().hubbard_server_poll(self.handle, int(ticket), ctypes.byref(sv))
+        if rc == HUB_EPENDING:
+            return None
+        _check(rc)
+        return self._served(sv)
+
+    def wait(self, ticket, timeout=3600.0):
+        sv = Served()
+        _check(load_library().hubbard_server_wait(self.handle, int(ticket), float(timeout), ctypes.byref(sv)))
+        return self._served(sv)
+
+    def stats(self):
+        st = ServerStats()
+        _check(load_library().hubbard_server_stats_get(self.handle, ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def close(self):
+        if self.handle:
+            load_library().hubbard_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -754,6 +754,7 @@ struct hubbard_batch {
     int* d_swp = nullptr;
     int64_t* d_rowoff = nullptr;
     int64_t rows_all = 0;                      // sum of D_up over all sectors (workspace bound)
+    cudaStream_t mem_stream = nullptr;         // stream of its allocations (batch_create_streamed)
 };
 
 namespace hub {
@@ -776,13 +777,14 @@ struct RowPools {
 
 int batch_upload(hubbard_batch* B, const std::vector<int32_t>& rp, const std::vector<uint32_t>& ent,
                  const std::vector<uint32_t>& st, const RowPools& rows) {
-    auto up = [](auto** dst, const auto& v) -> int {
+    const cudaStream_t ms = B->mem_stream;
+    auto up = [ms](auto** dst, const auto& v) -> int {
         using T = std::remove_reference_t<decltype(v[0])>;
         const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
-        cudaError_t e = cudaMalloc((void**)dst, bytes);
+        cudaError_t e = dev_alloc((void**)dst, bytes, ms);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(batch tables)");
         if (!v.empty()) {
-            e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+            e = dev_upload(*dst, v.data(), v.size() * sizeof(T), ms);
             if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(batch tables)");
         }
         return HUB_OK;
@@ -794,16 +796,17 @@ int batch_upload(hubbard_batch* B, const std::vector<int32_t>& rp, const std::ve
 }
 
 void batch_free(hubbard_batch* B) {
-    cudaFree(B->d_sec);
-    cudaFree(B->d_rp);
-    cudaFree(B->d_ent);
-    cudaFree(B->d_st);
-    cudaFree(B->d_bo);
-    cudaFree(B->d_bc);
-    cudaFree(B->d_be);
-    cudaFree(B->d_tasks);
-    cudaFree(B->d_swp);
-    cudaFree(B->d_rowoff);
+    const cudaStream_t ms = B->mem_stream;
+    dev_free(B->d_sec, ms);
+    dev_free(B->d_rp, ms);
+    dev_free(B->d_ent, ms);
+    dev_free(B->d_st, ms);
+    dev_free(B->d_bo, ms);
+    dev_free(B->d_bc, ms);
+    dev_free(B->d_be, ms);
+    dev_free(B->d_tasks, ms);
+    dev_free(B->d_swp, ms);
+    dev_free(B->d_rowoff, ms);
 }
 
 int batch_grid(hubbard_batch* B, int* smem_elems) {
@@ -849,28 +852,29 @@ int batch_schedule(hubbard_batch* B) {
     for (int s : swp) rowoff.push_back(rowoff.back() + B->sec[s].Dup);
     // the rest: one CTA per sector, largest work first (claimed dynamically)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
-    cudaFree(B->d_swp);
-    cudaFree(B->d_rowoff);
+    const cudaStream_t ms = B->mem_stream;
+    dev_free(B->d_swp, ms);
+    dev_free(B->d_rowoff, ms);
     B->d_swp = nullptr;
     B->d_rowoff = nullptr;
     B->nswp = (int)swp.size();
     {
-        cudaError_t e = cudaMalloc((void**)&B->d_swp, std::max<size_t>(swp.size(), 1) * sizeof(int));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_rowoff, rowoff.size() * sizeof(int64_t));
+        cudaError_t e = dev_alloc((void**)&B->d_swp, std::max<size_t>(swp.size(), 1) * sizeof(int), ms);
+        if (e == cudaSuccess) e = dev_alloc((void**)&B->d_rowoff, rowoff.size() * sizeof(int64_t), ms);
         if (e == cudaSuccess && !swp.empty())
-            e = cudaMemcpy(B->d_swp, swp.data(), swp.size() * sizeof(int), cudaMemcpyHostToDevice);
+            e = dev_upload(B->d_swp, swp.data(), swp.size() * sizeof(int), ms);
         if (e == cudaSuccess)
-            e = cudaMemcpy(B->d_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t), cudaMemcpyHostToDevice);
+            e = dev_upload(B->d_rowoff, rowoff.data(), rowoff.size() * sizeof(int64_t), ms);
         if (e != cudaSuccess) return cuda_fail(e, "batch sweep list upload");
     }
-    cudaFree(B->d_tasks);
+    dev_free(B->d_tasks, ms);
     B->d_tasks = nullptr;
     B->ntasks = (int)order.size();
-    cudaError_t e = cudaMalloc((void**)&B->d_tasks, std::max<size_t>(order.size(), 1) * sizeof(int));
+    cudaError_t e = dev_alloc((void**)&B->d_tasks, std::max<size_t>(order.size(), 1) * sizeof(int), ms);
     if (e == cudaSuccess && !order.empty())
-        e = cudaMemcpy(B->d_tasks, order.data(), order.size() * sizeof(int), cudaMemcpyHostToDevice);
+        e = dev_upload(B->d_tasks, order.data(), order.size() * sizeof(int), ms);
     if (e != cudaSuccess) return cuda_fail(e, "batch schedule upload");
-    e = cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice);
+    e = dev_upload(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), ms);
     if (e != cudaSuccess) return cuda_fail(e, "batch descriptor upload");
     B->sched_elems = B->elems_per_cta;
     return HUB_OK;
@@ -907,11 +911,19 @@ using namespace hub;
 extern "C" {
 
 int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubbard_batch_t* out) {
+    return batch_create_streamed(sectors, n_sectors, nullptr, out);
+}
+
+}  // extern "C"
+
+int hub::batch_create_streamed(const hubbard_sector_desc* sectors, int n_sectors, cudaStream_t ms,
+                               hubbard_batch_t* out) {
     clear_error();
     if (out == nullptr || n_sectors < 1 || sectors == nullptr) return fail(HUB_EINVAL, "bad batch arguments");
     *out = nullptr;
     hubbard_batch* B = new (std::nothrow) hubbard_batch();
     if (B == nullptr) return fail(HUB_ENOMEM, "host allocation");
+    B->mem_stream = ms;
     cudaGetDevice(&B->device);
     B->n = n_sectors;
     std::vector<int32_t> rp;
@@ -1013,9 +1025,12 @@ int hubbard_batch_create(const hubbard_sector_desc* sectors, int n_sectors, hubb
     return HUB_OK;
 }
 
+extern "C" {
+
 void hubbard_batch_destroy(hubbard_batch_t B) {
     if (B == nullptr) return;
-    cudaDeviceSynchronize();
+    // a batch tied to a stream frees in that stream's order
+    if (B->mem_stream == nullptr) cudaDeviceSynchronize();
     batch_free(B);
     delete B;
 }
@@ -1063,7 +1078,7 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
         if ((rc = batch_schedule(B))) return rc;      // uploads the descriptors too
         dirty = false;
     }
-    if (dirty) HUB_CUDA(cudaMemcpy(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), cudaMemcpyHostToDevice));
+    if (dirty) HUB_CUDA(dev_upload(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), B->mem_stream));
     cudaStream_t s = (cudaStream_t)stream;
     char* ws = (char*)workspace;
     // the barrier counter and the error word start at zero
@@ -1100,7 +1115,11 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     P.claim = (unsigned long long*)(ws + L.gbar + 16);
     void* args[] = {&P};
     const size_t smem = (size_t)B->smem_elems * sizeof(int2);
-    HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(B->grid), dim3(kBatchThreads), args, smem, s));
+    // without sweep sectors every CTA takes one-CTA tasks: a batch of a few
+    // sectors then occupies only as many CTAs as it has tasks, and the rest of
+    // the GPU stays free for concurrent work on other streams
+    const int grid = B->nswp == 0 ? std::max(1, std::min(B->grid, B->ntasks)) : B->grid;
+    HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(grid), dim3(kBatchThreads), args, smem, s));
     count_launches(1);
     return HUB_OK;
 }

@@ -83,12 +83,12 @@ void free_dev(hubbard_sector* H) {
         H->dev[s] = DevSpin{};                 // owned by the shared entry
         H->spin_owner[s].reset();
     }
-    cudaFree(H->fx_scratch);
+    dev_free(H->fx_scratch, H->mem_stream);
     H->fx_scratch = nullptr;
     H->fx_bytes = 0;
-    cudaFree(H->red);
-    cudaFree(H->status);
-    cudaFree(H->lz);
+    dev_free(H->red, H->mem_stream);
+    dev_free(H->status, H->mem_stream);
+    dev_free(H->lz, H->mem_stream);
     H->red = nullptr;
     H->status = nullptr;
     H->lz = nullptr;
@@ -242,10 +242,10 @@ int upload_spin(const SpinTables& T, DevSpin& d) {
 int ensure_fx_scratch(hubbard_sector* H) {
     const size_t need = (size_t)H->D * 16;
     if (H->fx_bytes >= need) return HUB_OK;
-    cudaFree(H->fx_scratch);
+    dev_free(H->fx_scratch, H->mem_stream);
     H->fx_scratch = nullptr;
     H->fx_bytes = 0;
-    cudaError_t e = cudaMalloc(&H->fx_scratch, std::max<size_t>(need, 256));
+    cudaError_t e = dev_alloc(&H->fx_scratch, std::max<size_t>(need, 256), H->mem_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(fixed-point scratch)");
     H->fx_bytes = need;
     return HUB_OK;
@@ -277,7 +277,7 @@ namespace {
 // their last handle is gone, so creating the same sector again (a solve
 // loop, a server) skips the table build, colouring and upload.
 using SpinKey = std::tuple<int, int, std::vector<std::pair<int, int>>, int>;
-constexpr size_t kSpinCacheKeep = 64;
+constexpr size_t kSpinCacheKeep = 256;
 std::mutex g_spin_mu;
 std::map<SpinKey, std::weak_ptr<SpinEntry>> g_spin_index;
 std::list<std::shared_ptr<SpinEntry>> g_spin_recent;
@@ -480,6 +480,13 @@ int hubbard_host_row_table(int Ns, const int32_t* bonds, int n_bonds, int N, int
 
 int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn, double t, double U,
                           hubbard_t* out) {
+    return sector_create_streamed(Ns, bonds, n_bonds, Nup, Ndn, t, U, nullptr, out);
+}
+
+}  // extern "C"
+
+int hub::sector_create_streamed(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn, double t, double U,
+                                cudaStream_t ms, hubbard_t* out) {
     clear_error();
     if (out == nullptr) return fail(HUB_EINVAL, "out is null");
     *out = nullptr;
@@ -494,6 +501,7 @@ int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, in
         delete H;
         return fail(HUB_ECUDA, "no CUDA device");
     }
+    H->mem_stream = ms;
     H->ns = Ns;
     H->nup = Nup;
     H->ndn = Ndn;
@@ -516,10 +524,13 @@ int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, in
     H->Ddn = H->host[1].D;
     H->D = H->Dup * H->Ddn;
     if (rc == HUB_OK) {
-        cudaError_t e = cudaMalloc((void**)&H->red, kRedSlots * sizeof(double));
-        if (e == cudaSuccess) e = cudaMalloc((void**)&H->status, 4 * sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(H->status, 0, 4 * sizeof(int));
-        if (e == cudaSuccess) e = cudaMemset(H->red, 0, kRedSlots * sizeof(double));
+        cudaError_t e = dev_alloc((void**)&H->red, kRedSlots * sizeof(double), ms);
+        if (e == cudaSuccess) e = dev_alloc((void**)&H->status, 4 * sizeof(int), ms);
+        if (e == cudaSuccess)
+            e = ms ? cudaMemsetAsync(H->status, 0, 4 * sizeof(int), ms) : cudaMemset(H->status, 0, 4 * sizeof(int));
+        if (e == cudaSuccess)
+            e = ms ? cudaMemsetAsync(H->red, 0, kRedSlots * sizeof(double), ms)
+                   : cudaMemset(H->red, 0, kRedSlots * sizeof(double));
         if (e != cudaSuccess) rc = cuda_fail(e, "cudaMalloc(reduction scratch)");
     }
     if (rc != HUB_OK) {
@@ -532,9 +543,13 @@ int hubbard_sector_create(int Ns, const int32_t* bonds, int n_bonds, int Nup, in
     return HUB_OK;
 }
 
+extern "C" {
+
 void hubbard_sector_destroy(hubbard_t H) {
     if (H == nullptr) return;
-    cudaDeviceSynchronize();
+    // a handle tied to a stream frees in that stream's order; any other waits
+    // for the device, since its scratch may be in use on any stream
+    if (H->mem_stream == nullptr) cudaDeviceSynchronize();
     free_dev(H);
     delete H;
 }
@@ -827,11 +842,11 @@ static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_
 // cap steps (grown on demand; freed with the handle).
 static int ensure_lz(hubbard_sector* H, int cap) {
     if (H->lz != nullptr && H->lz_cap >= cap) return HUB_OK;
-    cudaFree(H->lz);
+    dev_free(H->lz, H->mem_stream);
     H->lz = nullptr;
     H->lz_cap = 0;
     const size_t bytes = 256 + 2 * (size_t)cap * sizeof(double);
-    cudaError_t e = cudaMalloc(&H->lz, bytes);
+    cudaError_t e = dev_alloc(&H->lz, bytes, H->mem_stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(Lanczos control)");
     H->lz_cap = cap;
     return HUB_OK;
@@ -1151,6 +1166,9 @@ int lanczos_ground_state(hubbard_t H, const void* v0, int max_iters, double tol,
     return HUB_OK;
 }
 
+// binary64 Lanczos steps of the refined solver's polish (at most)
+constexpr int kPolishSteps = 150;
+
 size_t lanczos_refined_workspace_bytes(hubbard_t H) {
     if (H == nullptr) return 0;
     const size_t D = (size_t)H->D;
@@ -1287,13 +1305,18 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         // resolved, else rho itself
         const double want = tol * std::max(1.0, std::fabs(th));
         const double rho_target = gap > 0.0 ? std::sqrt(want * gap) : want;
-        if ((rc = lanczos_core(H, psi, HUB_F64, 60, rho_target, HUB_F64, pf, pg, s, P))) return rc;
+        if ((rc = lanczos_core(H, psi, HUB_F64, kPolishSteps, rho_target, HUB_F64, pf, pg, s, P))) return rc;
+        const int mp = (int)P.a.size();
+        // the polish's own second Ritz pair gives a second lower estimate of the
+        // gap (same assumption); the larger one is used
+        const double gap_p = tridiag_gap_lower(P.a.data(), P.b.data(), mp, P.b.back(), P.theta);
+        out->gap = std::max(gap, gap_p);
         out->energy = P.theta;
         out->residual = P.rho;
-        out->error_bound = energy_error_bound(P.rho, gap) +
+        out->error_bound = energy_error_bound(P.rho, out->gap) +
                            rounding_floor(H->host[0].W + H->host[1].W + 1, HUB_F64,
-                                          tridiag_scale(P.a.data(), P.b.data(), (int)P.a.size()));
-        out->iters_f64 = (int)P.a.size();
+                                          tridiag_scale(P.a.data(), P.b.data(), mp));
+        out->iters_f64 = mp;
     }
     out->status = (out->error_bound <= tol * std::max(1.0, std::fabs(out->energy))) ? HUB_OK : HUB_ENOTCONV;
     if (out->status != HUB_OK) return fail(HUB_ENOTCONV, "refined energy bound above tol");

@@ -18,6 +18,24 @@ void clear_error();
 int fail(int code, const std::string& msg);
 int cuda_fail(cudaError_t e, const char* what);
 
+// Device memory of an object tied to one stream (ms != nullptr): allocated,
+// uploaded and freed in that stream's order, so releasing it does not wait for
+// the whole device (cudaFree would).  ms == nullptr: cudaMalloc / cudaMemcpy /
+// cudaFree.
+inline cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t ms) {
+    return ms ? cudaMallocAsync(p, bytes, ms) : cudaMalloc(p, bytes);
+}
+inline void dev_free(void* p, cudaStream_t ms) {
+    if (p == nullptr) return;
+    if (ms) cudaFreeAsync(p, ms);
+    else cudaFree(p);
+}
+// host -> device; pageable sources are staged before the call returns
+inline cudaError_t dev_upload(void* dst, const void* src, size_t bytes, cudaStream_t ms) {
+    return ms ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, ms)
+              : cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+}
+
 #define HUB_CUDA(call)                                   \
     do {                                                 \
         cudaError_t e_ = (call);                         \
@@ -105,6 +123,9 @@ struct hubbard_sector {
     // device-resident Lanczos control (LzDev) and a/b history for lz_cap steps
     void* lz = nullptr;
     int lz_cap = 0;
+    // stream of the handle's own allocations (nullptr: cudaMalloc / cudaFree;
+    // set by sector_create_streamed for handles that live on one stream)
+    cudaStream_t mem_stream = nullptr;
 };
 
 namespace hub {
@@ -114,6 +135,14 @@ constexpr int kPartStride = 1024;    // stride of the partial arrays of a fused 
 
 // process-wide count of kernel launches (hubbard_kernel_launches)
 void count_launches(int n);
+
+// Handles and batches whose allocations live on one stream (server lanes):
+// created like hubbard_sector_create / hubbard_batch_create, released without
+// a device-wide synchronisation (the caller's later work on that stream is
+// ordered after the frees; work on other streams is not waited for).
+int sector_create_streamed(int Ns, const int32_t* bonds, int n_bonds, int Nup, int Ndn, double t, double U,
+                           cudaStream_t ms, hubbard_t* out);
+int batch_create_streamed(const hubbard_sector_desc* sectors, int n_sectors, cudaStream_t ms, hubbard_batch_t* out);
 
 // Device-resident control of a Lanczos run (Algorithm 1 steps enqueued without
 // a host round trip): the scalars the next step's kernels read, written by the

@@ -29,6 +29,7 @@ def declared_functions():
             continue
         text = open(os.path.join(inc, fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"^\s*typedef[^;]*;", "", text, flags=re.M | re.S)       # function-pointer types
         for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b([a-z_][a-z0-9_]*)\s*\(", text, flags=re.M):
             if m.group(1) not in ("if", "while", "for", "return", "sizeof"):
                 names.append(m.group(1))

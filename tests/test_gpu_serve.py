@@ -32,34 +32,79 @@ def _trace(n, seed):
             enumerate(serve_requests(n, rate=500.0, seed=seed, lattices=LATS))]
 
 
+def _server(**kw):
+    args = dict(hbm_budget=60e9, n_slots=4, small_lanes=2, small_max_dim=20_000, mid_max_dim=400_000)
+    args.update(kw)
+    return SolveServer(**args)
+
+
 def test_serve_mixed_trace(dev):
+    """60 requests of every path (micro-batched small sectors, binary64 and
+    refined lanes), all answered, each energy within 1e-9 of the oracle and
+    within its own error bound."""
     reqs = _trace(60, 21)
-    assert any(r.D > 200_000 for r in reqs) and any(r.D <= 200_000 for r in reqs)
-    srv = SolveServer(60e9, n_slots=4, small_max_dim=200_000)
+    srv = _server()
     st = srv.run_trace(reqs, timeout=600)
     srv.stop()
-    assert st["requests"] == 60 and not srv.errors
-    assert all(r.result["status"] == hub.HUB_OK for r in reqs)
+    assert st["requests"] == 60 and st["failed"] == 0
+    assert {r.path for r in reqs} == {"batch", "binary64", "refined"}
+    assert st["verified"] == 60
     for r in reqs:
         e_ref, route = ground_energy(*r.spec(), seed=r.seed)
-        assert abs(r.result["energy"] - e_ref) <= 1e-9 * max(1.0, abs(e_ref)), (r.path, r.D, route)
+        err = abs(r.result["energy"] - e_ref)
+        assert err <= 1e-9 * max(1.0, abs(e_ref)), (r.path, r.D, route)
+        assert err <= r.result["err_bound"] + 1e-12 * max(1.0, abs(e_ref)), (r.path, r.D, r.result)
 
 
 def test_serve_alone_equals_in_mix(dev):
+    """A request's answer in the mix equals its answer served alone (fixed-order
+    reductions on every path), and both match the oracle."""
     reqs = _trace(40, 22)
-    srv = SolveServer(60e9, n_slots=4, small_max_dim=200_000)
+    srv = _server()
     srv.run_trace(reqs, timeout=600)
     srv.stop()
-    picks = [r for r in reqs if r.path == "batch"][:3] + [r for r in reqs if r.path == "refined"][:2]
+    picks = ([r for r in reqs if r.path == "batch"][:3] + [r for r in reqs if r.path == "binary64"][:2] +
+             [r for r in reqs if r.path == "refined"][:2])
+    assert {r.path for r in picks} == {"batch", "binary64", "refined"}
     for r in picks:
         solo = Request(1000 + r.id, dict(lattice=r.lattice, nup=r.nup, ndn=r.ndn, t=r.t, U=r.U, seed=r.seed), 0.0)
-        s2 = SolveServer(60e9, n_slots=1, small_max_dim=200_000)
+        s2 = _server(n_slots=1, small_lanes=1)
         s2.run_trace([solo], timeout=600)
         s2.stop()
         assert solo.path == r.path
-        assert abs(solo.result["energy"] - r.result["energy"]) <= 1e-12 * max(1.0, abs(r.result["energy"]))
+        assert solo.result["energy"] == r.result["energy"], (r.path, solo.result, r.result)
         e_ref, _ = ground_energy(*r.spec(), seed=r.seed)
         assert abs(r.result["energy"] - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
+
+
+def test_serve_c_abi_submit_poll(dev):
+    """The C ABI directly: submit, poll until done, wait; a bad request is refused."""
+    from workload import ring
+    srv = hub.Server(8e9, small_lanes=1, big_lanes=2, small_max_dim=20_000, mid_max_dim=400_000)
+    tks = [srv.submit(8, ring(8), 4, 4, 1.0, 4.0, 1234), srv.submit(10, ring(10), 5, 5, 1.0, 6.0, 7),
+           srv.submit(12, ring(12), 5, 6, 1.0, 4.5, 11)]
+    import time
+    deadline = time.time() + 120
+    res = {}
+    while len(res) < len(tks) and time.time() < deadline:
+        for tk in tks:
+            if tk not in res:
+                r = srv.poll(tk)
+                if r is not None:
+                    res[tk] = r
+        time.sleep(0.01)
+    assert len(res) == 3
+    assert [res[tk]["path"] for tk in tks] == ["batch", "binary64", "refined"]
+    for tk, (ns, bonds, nup, ndn, U, seed) in zip(tks, [(8, ring(8), 4, 4, 4.0, 1234), (10, ring(10), 5, 5, 6.0, 7),
+                                                      (12, ring(12), 5, 6, 4.5, 11)]):
+        e_ref, _ = ground_energy(ns, bonds, nup, ndn, 1.0, U, seed=seed)
+        assert res[tk]["status"] == 0 and abs(res[tk]["energy"] - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
+        assert srv.wait(tk, 1.0)["energy"] == res[tk]["energy"]
+    with pytest.raises(hub.HubError):
+        srv.submit(4, [(0, 4)], 1, 1, 1.0, 1.0, 1)          # bond endpoint out of range
+    st = srv.stats()
+    assert st["completed"] == 3 and st["verified"] == 3 and st["free_bytes"] == st["budget_bytes"]
+    srv.close()
 
 
 def test_fill_start_vector_matches_host_recipe(dev):
