@@ -262,11 +262,13 @@ int hubbard_lanczos_step(hubbard_t H, const void* f, void* g, double beta_j, int
  *              a_1..a_m and b_2..b_{m+1}
  *   out        host result: energy (lowest Ritz value), residual rho,
  *              err_bound, iters, status, breakdown flag
- * err_bound is the a-posteriori bound min(rho, rho^2 / gap) on |energy - E0|,
- * gap = (theta_2 - rho_2) - energy from the second distinct Ritz pair of T_m
- * (theta_2, residual estimate rho_2); when T_m resolves no positive gap it is
- * rho.  The quadratic form assumes no eigenvalue of H other than E0 (counted
- * once if degenerate) lies below theta_2 - rho_2.  A rounding floor
+ * err_bound is the a-posteriori bound min(rho, 10 rho^2 / gap) on
+ * |energy - E0|, gap = (theta_2 - rho_2) - energy from the second distinct
+ * Ritz pair of T_m (theta_2, residual estimate rho_2); when T_m resolves no
+ * positive gap it is rho.  The quadratic form assumes that no eigenvalue of H
+ * other than E0 (counted once if degenerate) lies below a tenth of that gap
+ * above E0: the estimate is not rigorous (a Ritz pair can resolve an
+ * eigenvalue above an unresolved lambda_2), hence the factor 10.  A rounding floor
  * (W_up + W_dn + 1) u max(1, max|a_j|, max b_j) is added, u = 2^-47 for
  * HUB_F64 (the fixed-point grid of unit vectors) and 2^-24 for HUB_F32.
  * Breakdown (beta_{m+1} <= 1e-13 * max(1, max|a|, max b)) counts as
@@ -322,14 +324,13 @@ uint64_t hubbard_kernel_launches(void);
  * gap is a lower estimate of lambda_2 - E0 from the binary32 run:
  * (theta_2 - rho_2) - theta with theta_2 its second distinct Ritz value and
  * rho_2 that Ritz pair's residual estimate (a Ritz value alone only bounds
- * lambda_2 from above).  error_bound = min(residual, residual^2 / gap), or the
- * residual when gap <= 0, plus the binary64 rounding floor of
+ * lambda_2 from above).  error_bound = min(residual, 10 residual^2 / gap), or
+ * the residual when gap <= 0, plus the binary64 rounding floor of
  * lanczos_ground_state; the quadratic form assumes no eigenvalue other than
- * E0 lies below theta_2 - rho_2.  After a polish, gap is the larger of that
- * estimate and the same estimate from the polish's own tridiagonal matrix.  The
- * polish runs until error_bound <= tol * max(1, |energy|) (at most 150
- * binary64 steps); status is HUB_OK exactly when that holds.  Returns
- * HUB_ENOTCONV otherwise.  Synchronises stream.
+ * E0 lies within a tenth of gap above it.  The polish runs until
+ * error_bound <= tol * max(1, |energy|) / 2 (at most 150 binary64 steps);
+ * status is HUB_OK exactly when error_bound <= tol * max(1, |energy|).
+ * Returns HUB_ENOTCONV otherwise.  Synchronises stream.
  * ------------------------------------------------------------------------- */
 typedef struct {
     double energy;
@@ -431,7 +432,9 @@ int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iter
  *   D > mid_max_dim                   : a big lane, binary32 Lanczos with
  *       binary64 refinement (lanczos_ground_state_refined, tol relative on the
  *       error bound), keeping up to store_vectors binary32 Lanczos vectors
- *       within half of the spare budget.
+ *       within a quarter of the spare budget and 16 GB; a request the
+ *       refinement cannot certify is solved again by the binary64 Lanczos
+ *       (its result then reports path 1).
  * Requests that arrive while others run are admitted as lanes and memory free
  * up, and their work overlaps on the device.  Handles, batches and buffers of
  * a lane are allocated on its stream, so finishing a request never waits for

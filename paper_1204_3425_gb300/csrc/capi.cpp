@@ -1303,17 +1303,17 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
         LanczosRun P;
         // stop as soon as the bound meets tol: rho^2 / gap when a gap is
         // resolved, else rho itself
+        // target: the bound (quadratic part plus the rounding floor) at half of
+        // tol; the gap stays the binary32 run's (a polish started from psi
+        // resolves little of lambda_2: its second Ritz pair overestimated the
+        // gap threefold in a test)
         const double want = tol * std::max(1.0, std::fabs(th));
-        const double rho_target = gap > 0.0 ? std::sqrt(want * gap) : want;
+        const double rho_target = gap > 0.0 ? std::sqrt(0.5 * want * gap / kGapSafety) : 0.5 * want;
         if ((rc = lanczos_core(H, psi, HUB_F64, kPolishSteps, rho_target, HUB_F64, pf, pg, s, P))) return rc;
         const int mp = (int)P.a.size();
-        // the polish's own second Ritz pair gives a second lower estimate of the
-        // gap (same assumption); the larger one is used
-        const double gap_p = tridiag_gap_lower(P.a.data(), P.b.data(), mp, P.b.back(), P.theta);
-        out->gap = std::max(gap, gap_p);
         out->energy = P.theta;
         out->residual = P.rho;
-        out->error_bound = energy_error_bound(P.rho, out->gap) +
+        out->error_bound = energy_error_bound(P.rho, gap) +
                            rounding_floor(H->host[0].W + H->host[1].W + 1, HUB_F64,
                                           tridiag_scale(P.a.data(), P.b.data(), mp));
         out->iters_f64 = mp;

@@ -191,6 +191,16 @@ int solve_big_gpu(hubbard_server* S, Req* r, size_t store_bytes, cudaStream_t st
         res.iters = rr.iters_f32 + rr.iters_f64;
         res.status = rr.status;
         res.breakdown = 0;
+        if (rc == HUB_ENOTCONV) {
+            // the refinement could not certify tol (a gap too small to resolve in
+            // its polish): the binary64 Lanczos, in the same workspace, certifies
+            // through its own Ritz estimates
+            r->out.path = kPathBinary64;
+            const int it0 = res.iters;
+            rc = lanczos_ground_state(H, v0, S->opts.max_iters, S->opts.tol, HUB_F64, ws, wsb, nullptr, st, nullptr,
+                                      nullptr, &res);
+            res.iters += it0;
+        }
     }
     hubbard_sector_destroy(H);
     return rc;
