@@ -569,10 +569,22 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune
         stream.synchronize()
     ms = ev[0].elapsed_time(ev[1])
     res = B.results(ws, max_iters, stream=stream)
+    table = B.schedule_table()
     B.close()
+    mode_name = {3: "smem", 2: "rows-staged", 0: "rows-L2"}
+    by = {}
+    for t in table:
+        key = t["path"] if t["path"] == "sweep" else "task-" + mode_name.get(t["mode"], str(t["mode"]))
+        by[key] = by.get(key, 0) + t["sectors"]
+    schedule_table = dict(shapes=len(table), sectors_by_schedule=by,
+                          rows="[D_up, D_dn, W, sectors, path, mode]",
+                          table=[[t["Dup"], t["Ddn"], t["W"], t["sectors"], t["path"],
+                                  mode_name.get(t["mode"], t["mode"]) if t["path"] == "task" else "staged"]
+                                 for t in table])
     ok = sum(1 for r in res if r["status"] == 0)
     return dict(sectors=count, ms=ms, solves_per_s=ok / (ms * 1e-3), converged=ok, elems_per_cta=chosen,
                 autotune_s=tune_s, create_s=create_s, iters_total=sum(r["iters"] for r in res),
+                schedule_table=schedule_table,
                 launches_per_batch=1, timed="CUDA graph replay", tol="rho < 1e-10 max(1,|theta|)",
                 _energies=[r["energy"] if r["status"] == 0 else None for r in res])
 

@@ -410,10 +410,39 @@ int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iter
  * memory for the call; synchronises `stream`. */
 int hubbard_selftest_wait_timeout(void* stream);
 
-/* Times full solves for elems_per_cta in {2^12 .. 2^17} and keeps the fastest
- * (written to *chosen).  Synchronises `stream`. */
+/* Autotuner of the batch's schedule (the paper tunes its kernels' shape by
+ * measurement, Sec. 4.3).  First, per sector shape (D_up, D_dn, W = W_up +
+ * W_dn) small enough to be a one-CTA task: up to one grid of that shape's
+ * sectors is solved alone for 16 steps in each candidate mode --
+ * the whole vector in shared memory when it fits, or warp-per-row passes over
+ * the L2 copy with or without the row staged in shared memory for the
+ * down-hops -- and the fastest (the default unless another is 3 % faster) is
+ * kept in the batch's schedule table.  Then full solves for elems_per_cta in
+ * {2^12 .. 2^17} pick the sweep/task threshold (written to *chosen).  The
+ * table persists in the batch and is used by every later solve (including a
+ * graph-captured one).  Each sector's arithmetic depends only on its own
+ * shape's entry and on whether it is swept, so results stay independent of
+ * the other sectors under a given table.  v0_all, workspace and ws_bytes as
+ * for hubbard_batch_solve_async; the workspace's results are overwritten.
+ * Synchronises `stream`. */
 int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iters, double tol, void* workspace,
                            size_t ws_bytes, void* stream, int64_t* chosen);
+
+/* The schedule table, one row of six int64 per distinct sector shape, in
+ * order of first appearance: {D_up, D_dn, W_up + W_dn, number of sectors of
+ * that shape, path (1: one-CTA task, 2: grid-wide sweep, by the current
+ * threshold), mode bits (1: a task keeps its whole vector in shared memory
+ * when it fits; 2: warp-per-row passes stage the row in shared memory for the
+ * down-hops; 3 is the default)}.  rows: host, 6 * cap int64 (may be NULL when
+ * cap = 0); writes min(cap, shapes) rows and sets *n_shapes to the number of
+ * shapes.  HUB_EINVAL on a null batch or n_shapes, or rows NULL with cap > 0. */
+int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int* n_shapes);
+
+/* Sets the mode bits (0 .. 3, as in the schedule table) of shape number
+ * `shape` (its row in hubbard_batch_schedule_table), e.g. to pin a table
+ * measured earlier; the next solve uploads the descriptors synchronously.
+ * HUB_EINVAL on a null batch or an out-of-range shape or mode. */
+int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode);
 
 /* ---------------------------------------------------------------------------
  * Continuous-batching ground-state server (the paper notes that a small

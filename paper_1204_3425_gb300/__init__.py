@@ -94,6 +94,8 @@ SIGNATURES = {
     "hubbard_batch_solve_async": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P]),
     "hubbard_batch_results": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "hubbard_batch_autotune": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P]),
+    "hubbard_batch_schedule_table": (ctypes.c_int, [P, P, ctypes.c_int, P]),
+    "hubbard_batch_set_shape_mode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
@@ -439,6 +441,19 @@ class Batch:
                                                      _ptr(workspace), workspace.numel(), _stream(stream),
                                                      ctypes.byref(chosen)))
         return chosen.value
+
+    def set_shape_mode(self, shape, mode):
+        _check(load_library().hubbard_batch_set_shape_mode(self.handle, int(shape), int(mode)))
+
+    def schedule_table(self):
+        """One dict per sector shape: D_up, D_dn, W, sectors, path ('task' / 'sweep'), mode bits."""
+        lib = load_library()
+        n = ctypes.c_int()
+        _check(lib.hubbard_batch_schedule_table(self.handle, None, 0, ctypes.byref(n)))
+        rows = (ctypes.c_int64 * (6 * max(n.value, 1)))()
+        _check(lib.hubbard_batch_schedule_table(self.handle, rows, n.value, ctypes.byref(n)))
+        return [dict(Dup=rows[6 * k], Ddn=rows[6 * k + 1], W=rows[6 * k + 2], sectors=rows[6 * k + 3],
+                     path="sweep" if rows[6 * k + 4] == 2 else "task", mode=rows[6 * k + 5]) for k in range(n.value)]
 
     def close(self):
         if self.handle:

@@ -34,6 +34,11 @@ namespace {
 constexpr int kBatchThreads = 480;   // 15 warps: two CTAs per SM leave each warp a 945-element row slice
 constexpr int kCheckEvery = 4;        // Ritz-value test every few steps
 
+// Per-shape schedule bits (the autotuner's table, one entry per sector shape):
+constexpr int kModeFlat = 1;    // a one-CTA task keeps its whole fixed-point vector in shared memory when it fits
+constexpr int kModeStage = 2;   // a warp-per-row pass stages the row in shared memory for the down-hops
+constexpr int kModeDefault = kModeFlat | kModeStage;
+
 struct SectorDesc {
     int64_t Dup, Ddn, D;
     int64_t voff;          // element offset of the sector's vectors in the pools
@@ -43,6 +48,8 @@ struct SectorDesc {
     int64_t ab;            // offset of its a/b history (2 * max_iters doubles)
     int64_t dn_blk;        // first group of its down-spin row table in the block pools (-1: none)
     double t, U;
+    int32_t mode;          // schedule bits of its shape (kModeFlat, kModeStage)
+    int32_t pad;
 };
 
 struct BatchParams {
@@ -62,14 +69,17 @@ struct BatchParams {
     double* ab;            // a/b histories
     lanczos_result* res;   // [sector]
     int* err;              // batch error word
-    int max_iters;
+    int max_iters;         // stride of the a/b histories
+    int iter_cap;          // steps at most (<= max_iters; shorter in autotuner trials)
     double tol;
     int smem_elems;        // capacity of the shared fixed-point buffer
+    int mode_force;        // >= 0: schedule bits for every sector (autotuner trials); -1: per sector
     long long spin_limit;  // bounded waits
     // grid-synchronous sweep (sectors above the schedule's size threshold)
     int nswp;
     const int* swp;        // [nswp] sector ids
     const int64_t* rowoff; // [nswp + 1] prefix sums of their D_up
+    const int32_t* rowsec; // [rowoff[nswp]] sweep index k of each row
     double* rowpart;       // [rowoff[nswp]][3] per-row partial sums
     struct SweepState* sst;// [nswp]
     unsigned int* gbar;    // grid barrier counter
@@ -356,15 +366,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw_all = (int64_t)gridDim.x * nwarps;
     const int64_t nrows = P.rowoff[P.nswp];
-    auto locate = [&](int64_t r) -> int {          // k with rowoff[k] <= r < rowoff[k + 1]
-        int lo = 0, hi = P.nswp - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (P.rowoff[mid] <= r) lo = mid;
-            else hi = mid - 1;
-        }
-        return lo;
-    };
+    auto locate = [&](int64_t r) -> int { return __ldg(P.rowsec + r); };   // k: rowoff[k] <= r < rowoff[k + 1]
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.nactive = P.nswp;
     // rows of the element and update phases are claimed one at a time (heaviest
     // sectors first), so warps that drew cheap rows take more of them
@@ -372,6 +374,12 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         unsigned long long r = 0ull;
         if (lane == 0) r = atomicAdd(P.claim + c, 1ull);
         return (int64_t)__shfl_sync(0xffffffffu, r, 0);
+    };
+    // a claimed row of a sector that has stopped: move the counter past the
+    // sector's last row (the counter only grows, so every row it skips is of
+    // that sector), and the other warps stop claiming its rows one by one
+    auto skip_sector = [&](int c, int k) {
+        if (lane == 0) atomicMax(P.claim + c, (unsigned long long)P.rowoff[k + 1]);
     };
     // |v0|^2 by rows, then per sector
     for (int64_t r = gw; r < nrows; r += nw_all) {
@@ -414,18 +422,22 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
     }
     if (!gsync()) return false;
     int nact = P.nswp;
-    for (int it = 0; it < P.max_iters && nact > 0; ++it) {
+    for (int it = 0; it < P.iter_cap && nact > 0; ++it) {
         double* fp = (it & 1) ? P.g : P.f;          // f_j and f_{j-1} swap pools each step
         double* gp = (it & 1) ? P.f : P.g;
         // E
         for (int64_t r = claim(0); r < nrows; r = claim(0)) {
             const int k = locate(r);
-            if (!__ldcg(&P.sst[k].active)) continue;
+            if (!__ldcg(&P.sst[k].active)) {
+                skip_sector(0, k);
+                continue;
+            }
             const SectorDesc S = P.sec[P.swp[k]];
             // warps of one CTA work on rows of different sectors: each owns a
             // fixed slice of the shared buffer, long rows read from L2 instead
             const int64_t slice = P.smem_elems / nwarps;
-            int2* buf = S.Ddn <= slice ? xs + (int64_t)warp * slice : nullptr;
+            const int mode = P.mode_force >= 0 ? P.mode_force : S.mode;
+            int2* buf = (mode & kModeStage) && S.Ddn <= slice ? xs + (int64_t)warp * slice : nullptr;
             const bool blk = S.dn_blk >= 0 && row_slots(S.Ddn) <= slice;
             const SecView V{P.xg + S.voff, fp + S.voff, gp + S.voff, P.rp + S.up_rp, P.rp + S.dn_rp,
                             P.ent + S.up_ent, P.ent + S.dn_ent, P.st + S.up_st, P.st + S.dn_st, S.Ddn, S.U,
@@ -474,7 +486,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
                 B[it] = bn;
             }
             const int m = it + 1;
-            const int mcap = (int)((int64_t)P.max_iters < S.D ? (int64_t)P.max_iters : S.D);
+            const int mcap = (int)((int64_t)P.iter_cap < S.D ? (int64_t)P.iter_cap : S.D);
             st.amax = fmax(st.amax, fmax(fabs(alpha), bn));
             st.broke = bn <= 1e-13 * st.amax;
             if (st.broke || (m >= 8 && (m % (m >= 32 ? 2 * kCheckEvery : kCheckEvery)) == 0) || m == mcap) {
@@ -518,16 +530,32 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         if (blockIdx.x == 0 && threadIdx.x == 0) P.claim[0] = 0ull;   // E of the next step starts after a barrier
         for (int64_t r = claim(1); r < nrows; r = claim(1)) {
             const int k = locate(r);
-            if (!__ldcg(&P.sst[k].active)) continue;
+            if (!__ldcg(&P.sst[k].active)) {
+                skip_sector(1, k);
+                continue;
+            }
             const SectorDesc S = P.sec[P.swp[k]];
             const double alpha = __ldcg(&P.sst[k].alpha), ib = __ldcg(&P.sst[k].ib);
             const int fused = __ldcg(&P.sst[k].fused);
             const int64_t j0 = S.voff + (r - P.rowoff[k]) * S.Ddn;
-            for (int64_t d = lane; d < S.Ddn; d += 32) {
-                const int64_t j = j0 + d;
-                const double x = (fused ? fma(-alpha, __ldcg(fp + j), __ldcg(gp + j)) : __ldcg(gp + j)) * ib;
-                gp[j] = x;
-                P.xg[j] = fixed47(x);
+            // four elements per lane in flight: every load of a group before its stores
+            for (int64_t d0 = lane; d0 < S.Ddn; d0 += 128) {
+                double fv[4], gv[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t d = d0 + 32 * i;
+                    fv[i] = (fused && d < S.Ddn) ? __ldcg(fp + j0 + d) : 0.0;
+                    gv[i] = d < S.Ddn ? __ldcg(gp + j0 + d) : 0.0;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int64_t d = d0 + 32 * i;
+                    if (d < S.Ddn) {
+                        const double x = (fused ? fma(-alpha, fv[i], gv[i]) : gv[i]) * ib;
+                        gp[j0 + d] = x;
+                        P.xg[j0 + d] = fixed47(x);
+                    }
+                }
             }
         }
         if (!gsync()) return false;
@@ -560,13 +588,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         const SectorDesc S = P.sec[sid];
         const int64_t D = S.D, Ddn = S.Ddn, Dup = S.Dup;
         const int64_t j0 = 0, j1 = D;
-        const bool in_smem = D <= P.smem_elems;
+        const int mode = P.mode_force >= 0 ? P.mode_force : S.mode;
+        const bool in_smem = (mode & kModeFlat) && D <= P.smem_elems;
         // per-warp row buffer for the global-memory path (rows of the fixed-point copy)
         const int nwarps = blockDim.x >> 5, warp = threadIdx.x >> 5;
         // (row_slots(Ddn) per warp for the coloured down-hop table, else Ddn)
         const bool blk = S.dn_blk >= 0 && row_slots(Ddn) * nwarps <= P.smem_elems;
         const int64_t rstride = blk ? row_slots(Ddn) : Ddn;
-        const bool rowbuf = !in_smem && rstride * nwarps <= P.smem_elems;
+        const bool rowbuf = (mode & kModeStage) && !in_smem && rstride * nwarps <= P.smem_elems;
         int2* X = in_smem ? xs : (P.xg + S.voff);
         double* f = P.f + S.voff;
         double* g = P.g + S.voff;
@@ -596,7 +625,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         }
         __syncthreads();
         const double scale = -S.t * 0x1p-47;           // -t times the fixed-point unit
-        const int mcap = (int)((int64_t)P.max_iters < D ? (int64_t)P.max_iters : D);
+        const int mcap = (int)((int64_t)P.iter_cap < D ? (int64_t)P.iter_cap : D);
         double beta = 0.0, theta = 0.0, rho = 0.0;
         int m = 0, broke = 0, conv = 0;
         if (threadIdx.x == 0) sh_prev = __longlong_as_double(0x7ff8000000000000ll);   // NaN: no previous value
@@ -733,6 +762,14 @@ struct hubbard_batch {
     int64_t total = 0;                         // sum of D
     std::vector<double> cost;                  // per-sector work estimate
     std::vector<int> hops1;                    // per-sector W_up + W_dn + 1 (error-bound floor)
+    // schedule table: one entry per sector shape (D_up, D_dn, W_up + W_dn)
+    struct Shape {
+        int64_t Dup, Ddn;
+        int W, count, mode;
+    };
+    std::vector<Shape> shapes;
+    std::vector<int> shape_of;                 // per sector
+    bool desc_dirty = false;                   // modes changed since the last descriptor upload
     hub::SectorDesc* d_sec = nullptr;
     int32_t* d_rp = nullptr;
     uint32_t* d_ent = nullptr;
@@ -753,6 +790,7 @@ struct hubbard_batch {
     int nswp = 0;
     int* d_swp = nullptr;
     int64_t* d_rowoff = nullptr;
+    int32_t* d_rowsec = nullptr;
     int64_t rows_all = 0;                      // sum of D_up over all sectors (workspace bound)
     cudaStream_t mem_stream = nullptr;         // stream of its allocations (batch_create_streamed)
 };
@@ -807,6 +845,7 @@ void batch_free(hubbard_batch* B) {
     dev_free(B->d_tasks, ms);
     dev_free(B->d_swp, ms);
     dev_free(B->d_rowoff, ms);
+    dev_free(B->d_rowsec, ms);
 }
 
 int batch_grid(hubbard_batch* B, int* smem_elems) {
@@ -849,18 +888,27 @@ int batch_schedule(hubbard_batch* B) {
     std::stable_sort(swp.begin(), swp.end(), [&](int a, int b) {
         return B->cost[a] / (double)B->sec[a].Dup > B->cost[b] / (double)B->sec[b].Dup;
     });
-    for (int s : swp) rowoff.push_back(rowoff.back() + B->sec[s].Dup);
+    std::vector<int32_t> rowsec;
+    for (int s : swp) {
+        rowsec.insert(rowsec.end(), (size_t)B->sec[s].Dup, (int32_t)(rowoff.size() - 1));
+        rowoff.push_back(rowoff.back() + B->sec[s].Dup);
+    }
     // the rest: one CTA per sector, largest work first (claimed dynamically)
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return B->cost[a] > B->cost[b]; });
     const cudaStream_t ms = B->mem_stream;
     dev_free(B->d_swp, ms);
     dev_free(B->d_rowoff, ms);
+    dev_free(B->d_rowsec, ms);
     B->d_swp = nullptr;
     B->d_rowoff = nullptr;
+    B->d_rowsec = nullptr;
     B->nswp = (int)swp.size();
     {
         cudaError_t e = dev_alloc((void**)&B->d_swp, std::max<size_t>(swp.size(), 1) * sizeof(int), ms);
         if (e == cudaSuccess) e = dev_alloc((void**)&B->d_rowoff, rowoff.size() * sizeof(int64_t), ms);
+        if (e == cudaSuccess) e = dev_alloc((void**)&B->d_rowsec, std::max<size_t>(rowsec.size(), 1) * sizeof(int32_t), ms);
+        if (e == cudaSuccess && !rowsec.empty())
+            e = dev_upload(B->d_rowsec, rowsec.data(), rowsec.size() * sizeof(int32_t), ms);
         if (e == cudaSuccess && !swp.empty())
             e = dev_upload(B->d_swp, swp.data(), swp.size() * sizeof(int), ms);
         if (e == cudaSuccess)
@@ -903,6 +951,57 @@ WsLayout batch_layout(const hubbard_batch* B, int max_iters) {
     return L;
 }
 
+// One cooperative launch: the sweep over the schedule's sweep list (when
+// `sweep`), then the one-CTA tasks d_tasks[0 .. ntasks).  mode_force >= 0
+// gives every sector those schedule bits (autotuner trials).
+int batch_launch(hubbard_batch* B, const double* v0_all, int max_iters, double tol, char* ws, const WsLayout& L,
+                 cudaStream_t s, const int* d_tasks, int ntasks, bool sweep, int mode_force, int iter_cap) {
+    // the barrier counter and the error word start at zero
+    HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
+    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 64, s));
+    BatchParams P;
+    P.sec = B->d_sec;
+    P.tasks = d_tasks;
+    P.ntasks = ntasks;
+    P.rp = B->d_rp;
+    P.ent = B->d_ent;
+    P.st = B->d_st;
+    P.bo = B->d_bo;
+    P.bc = B->d_bc;
+    P.be = B->d_be;
+    P.v0 = v0_all;
+    P.f = (double*)(ws + L.f);
+    P.g = (double*)(ws + L.g);
+    P.xg = (int2*)(ws + L.xg);
+    P.ab = (double*)(ws + L.ab);
+    P.res = (lanczos_result*)(ws + L.res);
+    P.err = (int*)(ws + L.err);
+    P.max_iters = max_iters;
+    P.iter_cap = std::min(max_iters, iter_cap);
+    P.tol = tol > 0.0 ? tol : 1e-10;
+    P.smem_elems = B->smem_elems;
+    P.mode_force = mode_force;
+    P.spin_limit = 20000000;            // ~2.5 s of 128 ns sleeps per barrier
+    P.nswp = sweep ? B->nswp : 0;
+    P.swp = B->d_swp;
+    P.rowoff = B->d_rowoff;
+    P.rowsec = B->d_rowsec;
+    P.rowpart = (double*)(ws + L.rowpart);
+    P.sst = (SweepState*)(ws + L.sst);
+    P.gbar = (unsigned int*)(ws + L.gbar);
+    P.nactive = (int*)(ws + L.gbar + 4);
+    P.claim = (unsigned long long*)(ws + L.gbar + 16);
+    void* args[] = {&P};
+    const size_t smem = (size_t)B->smem_elems * sizeof(int2);
+    // without sweep sectors every CTA takes one-CTA tasks: a batch of a few
+    // sectors then occupies only as many CTAs as it has tasks, and the rest of
+    // the GPU stays free for concurrent work on other streams
+    const int grid = P.nswp == 0 ? std::max(1, std::min(B->grid, ntasks)) : B->grid;
+    HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(grid), dim3(kBatchThreads), args, smem, s));
+    count_launches(1);
+    return HUB_OK;
+}
+
 }  // namespace
 }  // namespace hub
 
@@ -930,6 +1029,7 @@ int hub::batch_create_streamed(const hubbard_sector_desc* sectors, int n_sectors
     std::vector<uint32_t> ent, st;
     RowPools rows;
     std::map<std::tuple<int, std::vector<std::pair<int, int>>, int>, Cached> cache;
+    std::map<std::tuple<int64_t, int64_t, int>, int> shape_ids;
     auto spin = [&](int ns, const std::vector<std::pair<int, int>>& bl, int N) -> Cached {
         auto key = std::make_tuple(ns, bl, N);
         auto it = cache.find(key);
@@ -1002,6 +1102,17 @@ int hub::batch_create_streamed(const hubbard_sector_desc* sectors, int n_sectors
             s.dn_blk = cd.blk;
             s.t = d.t;
             s.U = d.U;
+            {
+                const auto key = std::make_tuple(s.Dup, s.Ddn, (int)(cu.W + cd.W));
+                auto it = shape_ids.find(key);
+                if (it == shape_ids.end()) {
+                    it = shape_ids.emplace(key, (int)B->shapes.size()).first;
+                    B->shapes.push_back({s.Dup, s.Ddn, (int)(cu.W + cd.W), 0, kModeDefault});
+                }
+                B->shapes[(size_t)it->second].count++;
+                B->shape_of.push_back(it->second);
+                s.mode = kModeDefault;
+            }
             B->sec.push_back(s);
             B->cost.push_back((double)s.D * (cu.hops + cd.hops + 8.0));
             B->hops1.push_back(cu.W + cd.W + 1);
@@ -1077,51 +1188,14 @@ int hubbard_batch_solve_async(hubbard_batch_t B, const double* v0_all, int max_i
     if (B->sched_elems != B->elems_per_cta) {
         if ((rc = batch_schedule(B))) return rc;      // uploads the descriptors too
         dirty = false;
+        B->desc_dirty = false;
     }
-    if (dirty) HUB_CUDA(dev_upload(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), B->mem_stream));
-    cudaStream_t s = (cudaStream_t)stream;
-    char* ws = (char*)workspace;
-    // the barrier counter and the error word start at zero
-    HUB_CUDA(cudaMemsetAsync(ws + L.err, 0, 4, s));
-    HUB_CUDA(cudaMemsetAsync(ws + L.gbar, 0, 64, s));
-    BatchParams P;
-    P.sec = B->d_sec;
-    P.tasks = B->d_tasks;
-    P.ntasks = B->ntasks;
-    P.rp = B->d_rp;
-    P.ent = B->d_ent;
-    P.st = B->d_st;
-    P.bo = B->d_bo;
-    P.bc = B->d_bc;
-    P.be = B->d_be;
-    P.v0 = v0_all;
-    P.f = (double*)(ws + L.f);
-    P.g = (double*)(ws + L.g);
-    P.xg = (int2*)(ws + L.xg);
-    P.ab = (double*)(ws + L.ab);
-    P.res = (lanczos_result*)(ws + L.res);
-    P.err = (int*)(ws + L.err);
-    P.max_iters = max_iters;
-    P.tol = tol > 0.0 ? tol : 1e-10;
-    P.smem_elems = B->smem_elems;
-    P.spin_limit = 20000000;            // ~2.5 s of 128 ns sleeps per barrier
-    P.nswp = B->nswp;
-    P.swp = B->d_swp;
-    P.rowoff = B->d_rowoff;
-    P.rowpart = (double*)(ws + L.rowpart);
-    P.sst = (SweepState*)(ws + L.sst);
-    P.gbar = (unsigned int*)(ws + L.gbar);
-    P.nactive = (int*)(ws + L.gbar + 4);
-    P.claim = (unsigned long long*)(ws + L.gbar + 16);
-    void* args[] = {&P};
-    const size_t smem = (size_t)B->smem_elems * sizeof(int2);
-    // without sweep sectors every CTA takes one-CTA tasks: a batch of a few
-    // sectors then occupies only as many CTAs as it has tasks, and the rest of
-    // the GPU stays free for concurrent work on other streams
-    const int grid = B->nswp == 0 ? std::max(1, std::min(B->grid, B->ntasks)) : B->grid;
-    HUB_CUDA(cudaLaunchCooperativeKernel((const void*)k_batch_lanczos, dim3(grid), dim3(kBatchThreads), args, smem, s));
-    count_launches(1);
-    return HUB_OK;
+    if (dirty || B->desc_dirty) {
+        HUB_CUDA(dev_upload(B->d_sec, B->sec.data(), B->sec.size() * sizeof(SectorDesc), B->mem_stream));
+        B->desc_dirty = false;
+    }
+    return batch_launch(B, v0_all, max_iters, tol, (char*)workspace, L, (cudaStream_t)stream, B->d_tasks, B->ntasks,
+                        true, -1, max_iters);
 }
 
 int hubbard_batch_results(hubbard_batch_t B, const void* workspace, int max_iters, void* stream,
@@ -1186,25 +1260,81 @@ int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iter
     clear_error();
     if (B == nullptr) return fail(HUB_EINVAL, "null batch");
     cudaStream_t s = (cudaStream_t)stream;
+    // the first solve checks the arguments and fixes the descriptors for max_iters
+    int rc = hubbard_batch_solve_async(B, v0_all, max_iters, tol, workspace, ws_bytes, stream);
+    if (rc != HUB_OK) return rc;
+    HUB_CUDA(cudaStreamSynchronize(s));
     cudaEvent_t e0, e1;
     HUB_CUDA(cudaEventCreate(&e0));
-    HUB_CUDA(cudaEventCreate(&e1));
-    const int64_t cands[] = {1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, 1 << 17};
-    float best = 1e30f;
-    int64_t best_e = B->elems_per_cta;
-    int rc = HUB_OK;
-    for (int64_t c : cands) {
-        B->elems_per_cta = c;
-        for (int rep = 0; rep < 2 && rc == HUB_OK; ++rep) {   // first run warms up
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(HUB_ECUDA, "event");
+    }
+    // a warm-up run, then the timed one; < 0 on failure (rc set)
+    auto timed = [&](auto&& launch) -> float {
+        float ms = -1.0f;
+        for (int rep = 0; rep < 2 && rc == HUB_OK; ++rep) {
             if (cudaEventRecord(e0, s) != cudaSuccess) rc = fail(HUB_ECUDA, "event");
-            if (rc == HUB_OK) rc = hubbard_batch_solve_async(B, v0_all, max_iters, tol, workspace, ws_bytes, stream);
+            if (rc == HUB_OK) rc = launch();
             if (rc == HUB_OK && cudaEventRecord(e1, s) != cudaSuccess) rc = fail(HUB_ECUDA, "event");
             if (rc == HUB_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = fail(HUB_ECUDA, "event sync");
         }
+        if (rc == HUB_OK) cudaEventElapsedTime(&ms, e0, e1);
+        return rc == HUB_OK ? ms : -1.0f;
+    };
+    // 1. per-shape schedule bits of the one-CTA tasks: for every shape that is
+    // a task under the largest threshold tried, up to one grid of its sectors
+    // is solved alone as tasks for 16 steps in each candidate mode -- the whole vector in
+    // shared memory (when it fits) or warp-per-row passes over the L2 copy,
+    // with or without the row staged for the down-hops -- and the fastest mode
+    // (the default unless another is 3 % faster) goes into the shape's entry
+    const int64_t kMaxTask = (int64_t)1 << 17;
+    constexpr int kTrialSteps = 16;                   // steps per trial solve (the cost per step is what differs)
+    const WsLayout L = batch_layout(B, max_iters);
+    std::vector<std::vector<int>> members(B->shapes.size());
+    for (int i = 0; i < B->n; ++i) members[(size_t)B->shape_of[(size_t)i]].push_back(i);
+    int* d_trial = nullptr;
+    const size_t trial_cap = (size_t)std::max(1, B->grid);
+    if (dev_alloc((void**)&d_trial, trial_cap * sizeof(int), B->mem_stream) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        return fail(HUB_ENOMEM, "autotune trial list");
+    }
+    for (size_t k = 0; k < B->shapes.size() && rc == HUB_OK; ++k) {
+        auto& sh = B->shapes[k];
+        const int64_t D = sh.Dup * sh.Ddn;
+        if (D > kMaxTask || members[k].empty()) continue;
+        std::vector<int> ids(members[k].begin(), members[k].begin() + std::min(members[k].size(), trial_cap));
+        if (cudaMemcpyAsync(d_trial, ids.data(), ids.size() * sizeof(int), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            rc = fail(HUB_ECUDA, "autotune trial upload");
+            break;
+        }
+        const int cands_flat[] = {kModeDefault, kModeStage};
+        const int cands_rows[] = {kModeStage, 0};
+        const int* cands = D <= B->smem_elems ? cands_flat : cands_rows;
+        float t[2];
+        for (int c = 0; c < 2 && rc == HUB_OK; ++c)
+            t[c] = timed([&] {
+                return batch_launch(B, v0_all, max_iters, tol, (char*)workspace, L, s, d_trial, (int)ids.size(),
+                                    false, cands[c], kTrialSteps);
+            });
+        if (rc == HUB_OK) sh.mode = (t[1] < 0.97f * t[0]) ? cands[1] : cands[0];
+    }
+    dev_free(d_trial, B->mem_stream);
+    for (int i = 0; i < B->n; ++i) B->sec[(size_t)i].mode = B->shapes[(size_t)B->shape_of[(size_t)i]].mode;
+    B->desc_dirty = true;
+    // 2. the size threshold between the grid-wide sweep and the tasks: full
+    // solves for elems_per_cta in 2^12 .. 2^17 with the shapes' modes
+    const int64_t cands[] = {1 << 12, 1 << 13, 1 << 14, 1 << 15, 1 << 16, kMaxTask};
+    float best = 1e30f;
+    int64_t best_e = B->elems_per_cta;
+    for (int64_t c : cands) {
         if (rc != HUB_OK) break;
-        float ms = 0.0f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
+        B->elems_per_cta = c;
+        const float ms =
+            timed([&] { return hubbard_batch_solve_async(B, v0_all, max_iters, tol, workspace, ws_bytes, stream); });
+        if (rc == HUB_OK && ms < best) {
             best = ms;
             best_e = c;
         }
@@ -1214,6 +1344,35 @@ int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iter
     B->elems_per_cta = best_e;
     if (chosen) *chosen = best_e;
     return rc;
+}
+
+int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode) {
+    clear_error();
+    if (B == nullptr || shape < 0 || shape >= (int)B->shapes.size() || mode < 0 || mode > kModeDefault)
+        return fail(HUB_EINVAL, "bad shape or mode");
+    B->shapes[(size_t)shape].mode = mode;
+    for (int i = 0; i < B->n; ++i)
+        if (B->shape_of[(size_t)i] == shape) B->sec[(size_t)i].mode = mode;
+    B->desc_dirty = true;
+    return HUB_OK;
+}
+
+int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int* n_out) {
+    clear_error();
+    if (B == nullptr || n_out == nullptr || cap < 0 || (cap > 0 && rows == nullptr))
+        return fail(HUB_EINVAL, "bad schedule table arguments");
+    *n_out = (int)B->shapes.size();
+    for (int k = 0; k < std::min(cap, *n_out); ++k) {
+        const auto& sh = B->shapes[(size_t)k];
+        int64_t* r = rows + 6 * (size_t)k;
+        r[0] = sh.Dup;
+        r[1] = sh.Ddn;
+        r[2] = sh.W;
+        r[3] = sh.count;
+        r[4] = sh.Dup * sh.Ddn > B->elems_per_cta ? 2 : 1;
+        r[5] = sh.mode;
+    }
+    return HUB_OK;
 }
 
 }  // extern "C"

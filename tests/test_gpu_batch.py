@@ -135,6 +135,41 @@ def test_batch_autotune_and_graph_replay(dev):
     assert [r["energy"] for r in again] == [r["energy"] for r in res]
 
 
+def test_batch_schedule_table_modes(dev):
+    """The autotuner's per-shape table covers every sector; each mode (whole
+    vector in shared memory, warp-per-row with staged rows, warp-per-row from
+    L2 alone) gives energies within 1e-9 of the oracle, and under a pinned
+    table a sector's result is bit-identical alone and in the mix."""
+    reqs = _small_reqs(40, 17, 60000)
+    specs = _specs(reqs)
+    seeds = [r["seed"] for r in reqs]
+    B, v0, ws, _ = _solve(specs, seeds, autotune=True)
+    table = B.schedule_table()
+    assert sum(t["sectors"] for t in table) == len(specs)
+    assert all(t["mode"] in (0, 2, 3) and t["path"] in ("task", "sweep") for t in table)
+    ref = [_oracle(sp) for sp in specs]
+    for mode in (3, 2, 0):
+        for k in range(len(table)):
+            B.set_shape_mode(k, mode)
+        B.set_schedule(1 << 30)                                   # every sector a one-CTA task
+        B.solve_async(v0, MAXIT, TOL, ws)
+        res = B.results(ws, MAXIT)
+        for spec, r, e in zip(specs, res, ref):
+            assert r["status"] == hub.HUB_OK, (mode, spec[2:], r)
+            assert abs(r["energy"] - e) <= 1e-9 * max(1.0, abs(e)), (mode, spec[2:], r, e)
+        for i in (0, 13, 39):
+            A = hub.Batch([specs[i]])
+            A.set_schedule(1 << 30)
+            A.set_shape_mode(0, mode)
+            v1 = _v0(A, [specs[i]], [seeds[i]])
+            w1 = torch.empty(A.workspace_bytes(MAXIT), dtype=torch.uint8, device="cuda")
+            A.solve_async(v1, MAXIT, TOL, w1)
+            alone = A.results(w1, MAXIT)[0]
+            assert alone["energy"] == res[i]["energy"] and alone["iters"] == res[i]["iters"], (mode, i)
+            A.close()
+    B.close()
+
+
 def test_batch_full_config(dev):
     """2048 uneven sectors (rings 6-12, 2x3, 2x4, 3x3, 3x4; random fillings and U)."""
     reqs = batch_sectors(2048, seed=1234)
