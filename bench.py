@@ -57,11 +57,12 @@ def workload_config(name):
     return ns, bonds, nup, ndn, U, dt, cfg
 
 
-# DRAM bytes per hubbard_apply from one ncu metrics capture (dram__bytes_read.sum
-# + dram__bytes_write.sum over the apply's kernels, a smaller sector scaled by D
-# to the bench sector), each with the SHA-256 prefix of the H*v kernel sources it
-# was taken on: a figure is reported only while those sources are unchanged.
-TRAFFIC = {"sq4x4_n8_8_U8_f64": (9.16e9, "e76d3a12eb13f131")}
+# DRAM bytes per hubbard_apply from one ncu metrics capture on the bench sector
+# itself (dram__bytes_read.sum + dram__bytes_write.sum over the apply's three
+# kernels; one replay pass each), with the SHA-256 prefix of the H*v kernel
+# sources it was taken on: a figure is reported only while those sources are
+# unchanged.
+TRAFFIC = {"sq4x4_n8_8_U8_f64": (9.467e9, "e76d3a12eb13f131")}
 KERNEL_SOURCES = ("paper_1204_3425_gb300/csrc/hv_phases.cu", "paper_1204_3425_gb300/csrc/row_blocks.cuh",
                   "paper_1204_3425_gb300/csrc/hv_epilogue.cuh")
 NOMINAL_HBM_GBS = 7900.0          # HBM3e nominal per GPU (vendor figure)
