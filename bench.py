@@ -245,7 +245,7 @@ def run_ours(args):
     # every step uploads its input from pinned host memory, applies H and
     # downloads its result; three streams overlap step i+1's upload and step
     # i-1's download with step i's H*v (two device buffers each way)
-    e2e_ms = e2e_pipelined(hub, torch, H, v_pin, D, tdt, dev, max(4, min(args.steps, 8)))
+    e2e_ms = e2e_host_apply(hub, torch, H, v_pin, D, tdt, dev, max(4, min(args.steps, 8)))
     e2e_val = ws * nbytes / (e2e_ms * 1e-3) / 1e9
 
     # ---- ground-state solves ----------------------------------------------
@@ -318,7 +318,8 @@ def run_ours(args):
                      "kernel_sources_sha": kernel_sources_hash(),
                      "kernel": "hubbard_apply (row phase + up phase kernels)"},
         "e2e": {"value": e2e_val, "unit": "GB/s", "h2d_bytes_per_step": D * esize, "d2h_bytes_per_step": D * esize,
-                "ms_per_step": e2e_ms, "pipelined": "3 streams: upload i+1 | H*v i | download i-1"},
+                "ms_per_step": e2e_ms, "api": "hubbard_apply_host (C ABI, page-locked host buffers)",
+                "pipelined": "inside the library: upload i+1 | H*v i | download i-1 (two staging slots, three streams)"},
         "gpu_launches": int(launches),
         "clocks": clk,
         "solve": solve,
@@ -336,44 +337,21 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
-def e2e_pipelined(hub, torch, H, v_pin, D, tdt, dev, k):
-    """ms per step of k host -> device -> H*v -> host steps, pipelined over three streams."""
-    sc = torch.cuda.current_stream()
-    sh, sd = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
-    vbuf = [torch.empty(D, dtype=tdt, device=dev) for _ in range(2)]
-    wbuf = [torch.empty(D, dtype=tdt, device=dev) for _ in range(2)]
+def e2e_host_apply(hub, torch, H, v_pin, D, tdt, dev, k):
+    """ms per step of k hubbard_apply_host calls (the C ABI's host-buffer product:
+    page-locked input and output; the library overlaps the upload of call i+1 and
+    the download of call i-1 with the H*v of call i).  CUDA events on the caller's
+    stream, which waits for every download; the device is idle when t0 is recorded,
+    so the first upload starts after it."""
+    s = torch.cuda.current_stream()
     wpin = [torch.empty(D, dtype=tdt).pin_memory() for _ in range(2)]
-    up = [torch.cuda.Event() for _ in range(2)]
-    done = [torch.cuda.Event() for _ in range(2)]
-    down = [torch.cuda.Event() for _ in range(2)]
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    hub.hubbard_apply(H, vbuf[0].copy_(v_pin), wbuf[0])      # warm
+    hub.hubbard_apply_host(H, v_pin, wpin[0], stream=s)      # warm: allocates the staging
     torch.cuda.synchronize()
-    t0.record(sc)
-    sh.wait_event(t0)
-    with torch.cuda.stream(sh):
-        vbuf[0].copy_(v_pin, non_blocking=True)
-        up[0].record(sh)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0.record(s)
     for i in range(k):
-        b = i & 1
-        if i + 1 < k:
-            with torch.cuda.stream(sh):
-                if i >= 1:
-                    sh.wait_event(done[1 - b])                 # vbuf[1-b] free once step i-1 is computed
-                vbuf[1 - b].copy_(v_pin, non_blocking=True)
-                up[1 - b].record(sh)
-        sc.wait_event(up[b])
-        if i >= 2:
-            sc.wait_event(down[b])                             # wbuf[b] free once step i-2 is downloaded
-        hub.hubbard_apply(H, vbuf[b], wbuf[b], stream=sc)
-        done[b].record(sc)
-        with torch.cuda.stream(sd):
-            sd.wait_event(done[b])
-            wpin[b].copy_(wbuf[b], non_blocking=True)
-            down[b].record(sd)
-    for e in down:
-        sc.wait_event(e)
-    t1.record(sc)
+        hub.hubbard_apply_host(H, v_pin, wpin[i & 1], stream=s)
+    t1.record(s)
     torch.cuda.synchronize()
     return t0.elapsed_time(t1) / k
 

@@ -148,6 +148,24 @@ int hubbard_host_row_table(int Ns, const int32_t* bonds, int n_bonds, int N, int
  * ------------------------------------------------------------------------- */
 int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream);
 
+/* w_host = H v_host with both vectors in host memory (same product and
+ * accuracy as hubbard_apply).  The call copies v_host to device staging owned
+ * by the handle, applies H, and copies the result back into w_host, on three
+ * streams of the handle, with two staging slots: consecutive calls overlap
+ * (the upload of call i+1 and the download of call i-1 run during the H*v of
+ * call i) when the host buffers are page-locked; with pageable buffers the
+ * copies are synchronous.  Returns once the work is enqueued; `stream` waits
+ * for the download, so w_host holds the result once `stream` has reached this
+ * call.  The upload is not ordered after earlier work on `stream`: v_host must
+ * hold the input when the call is made and stay unchanged, and w_host must not
+ * be read or written, until `stream` has reached the call.  The first call,
+ * and a call with another dtype, allocates 4 * D elements of staging (freed
+ * with the handle).  Calls on one handle, of this and the other functions,
+ * must not run concurrently (they share the handle's scratch).  HUB_EINVAL:
+ * null or overlapping vectors, a device pointer, a bad dtype, a handle from
+ * hubbard_server's lanes; HUB_ECUDA on a CUDA error. */
+int hubbard_apply_host(hubbard_t H, const void* v_host, void* w_host, int dtype, void* stream);
+
 /* Same as hubbard_apply, reference kernel: one thread per element and native
  * arithmetic of `dtype` (binary64 DADD/DFMA for HUB_F64), the paper's own
  * kernel organisation (Sec. 4.3, Algorithms 2-4: each thread gathers its

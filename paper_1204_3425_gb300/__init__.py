@@ -71,6 +71,7 @@ SIGNATURES = {
     "hubbard_table_nnz": (I64, [P, ctypes.c_int]),
     "hubbard_export_tables": (ctypes.c_int, [P, ctypes.c_int, P, P, P, P]),
     "hubbard_apply": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "hubbard_apply_host": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_apply_reference": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_apply_noalloc": (ctypes.c_int, [P, P, P, P]),
     "hubbard_set_schedule": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -252,6 +253,18 @@ def hubbard_apply(H, v, w, stream=None):
     _vec_pair(H, v, w)
     _check(load_library().hubbard_apply(H.handle, _ptr(v), _ptr(w), _dtype_code(v), _stream(stream)))
     return w
+
+
+def hubbard_apply_host(H, v, w, stream=None):
+    """w = H v for CPU tensors (page-locked for overlap); asynchronous on `stream` (see hubbard.h)."""
+    if v.device.type != "cpu" or w.device.type != "cpu":
+        raise ValueError("hubbard_apply_host takes CPU tensors")
+    if v.dtype != w.dtype:
+        raise TypeError("v and w must have the same dtype")
+    if v.numel() != H.D or w.numel() != H.D or not v.is_contiguous() or not w.is_contiguous():
+        raise ValueError(f"v and w must be contiguous with {H.D} elements")
+    _check(load_library().hubbard_apply_host(H.handle, ctypes.c_void_p(v.data_ptr()), ctypes.c_void_p(w.data_ptr()),
+                                             _dtype_code(v), _stream(stream)))
 
 
 def hubbard_apply_reference(H, v, w, stream=None):

@@ -78,7 +78,44 @@ void free_spin_dev(DevSpin& d) {
     d = DevSpin{};
 }
 
+}  // namespace
+
+// Staging of hubbard_apply_host: call i uses slot i % 2 -- its input copied
+// to v[slot] on `up`, H applied on `comp`, the result copied back from
+// w[slot] on `down` -- so consecutive calls overlap (upload i+1 | H*v i |
+// download i-1).  Events order the reuse of a slot after the call two back.
+struct HostPipe {
+    int dtype = -1;
+    size_t bytes = 0;
+    void* v[2] = {nullptr, nullptr};
+    void* w[2] = {nullptr, nullptr};
+    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+    cudaEvent_t uploaded[2] = {}, computed[2] = {}, downloaded[2] = {};
+    bool used[2] = {false, false};
+    unsigned long long calls = 0;
+};
+
+void host_pipe_free(hubbard_sector* H) {
+    HostPipe* P = H->host_pipe;
+    if (P == nullptr) return;
+    for (cudaStream_t st : {P->up, P->comp, P->down})
+        if (st) cudaStreamSynchronize(st);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(P->v[b]);
+        cudaFree(P->w[b]);
+        for (cudaEvent_t e : {P->uploaded[b], P->computed[b], P->downloaded[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    for (cudaStream_t st : {P->up, P->comp, P->down})
+        if (st) cudaStreamDestroy(st);
+    delete P;
+    H->host_pipe = nullptr;
+}
+
+namespace {
+
 void free_dev(hubbard_sector* H) {
+    host_pipe_free(H);
     for (int s = 0; s < 2; ++s) {
         H->dev[s] = DevSpin{};                 // owned by the shared entry
         H->spin_owner[s].reset();
@@ -602,6 +639,73 @@ int hubbard_apply(hubbard_t H, const void* v, void* w, int dtype, void* stream) 
     if (dtype == HUB_F64 && !fixed_point_ok(H)) return launch_hv_reference(H, v, w, dtype, s);
     if ((rc = ensure_fx_scratch(H))) return rc;
     return launch_hv_fast(H, v, w, dtype, 0.0, nullptr, 0, s);
+}
+
+int hubbard_apply_host(hubbard_t H, const void* v_host, void* w_host, int dtype, void* stream) {
+    clear_error();
+    int rc;
+    if ((rc = check_handle(H))) return rc;
+    if ((rc = check_dtype(dtype))) return rc;
+    if (v_host == nullptr || w_host == nullptr) return fail(HUB_EINVAL, "null vector");
+    if (H->mem_stream != nullptr) return fail(HUB_EINVAL, "host apply on a stream-owned handle");
+    const size_t bytes = (size_t)H->D * elem_size(dtype);
+    const char* a = (const char*)v_host;
+    const char* b = (const char*)w_host;
+    if (a < b + bytes && b < a + bytes) return fail(HUB_EINVAL, "v and w overlap");
+    cudaPointerAttributes pa{};
+    for (const void* p : {v_host, (const void*)w_host})
+        if (cudaPointerGetAttributes(&pa, p) == cudaSuccess && pa.type == cudaMemoryTypeDevice)
+            return fail(HUB_EINVAL, "hubbard_apply_host takes host buffers");
+    cudaGetLastError();                                  // a plain host pointer may leave an error behind
+    HostPipe* P = H->host_pipe;
+    if (P != nullptr && (P->dtype != dtype || P->bytes != bytes)) {
+        host_pipe_free(H);
+        P = nullptr;
+    }
+    if (P == nullptr) {
+        P = new (std::nothrow) HostPipe;
+        if (P == nullptr) return fail(HUB_ENOMEM, "host allocation (host apply staging)");
+        H->host_pipe = P;
+        P->dtype = dtype;
+        P->bytes = bytes;
+        cudaError_t e = cudaSuccess;
+        for (cudaStream_t* st : {&P->up, &P->comp, &P->down})
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            for (cudaEvent_t* ev : {&P->uploaded[k], &P->computed[k], &P->downloaded[k]})
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaMalloc(&P->v[k], std::max<size_t>(bytes, 256));
+            if (e == cudaSuccess) e = cudaMalloc(&P->w[k], std::max<size_t>(bytes, 256));
+        }
+        if (e != cudaSuccess) {
+            host_pipe_free(H);
+            return cuda_fail(e, "host apply staging");
+        }
+    }
+    const int k = (int)(P->calls & 1ull);
+    // upload: v[k] is free once the call two back has been computed
+    if (P->used[k]) HUB_CUDA(cudaStreamWaitEvent(P->up, P->computed[k], 0));
+    HUB_CUDA(cudaMemcpyAsync(P->v[k], v_host, bytes, cudaMemcpyHostToDevice, P->up));
+    HUB_CUDA(cudaEventRecord(P->uploaded[k], P->up));
+    // compute: after the upload, and once w[k] has been downloaded by the call two back
+    HUB_CUDA(cudaStreamWaitEvent(P->comp, P->uploaded[k], 0));
+    if (P->used[k]) HUB_CUDA(cudaStreamWaitEvent(P->comp, P->downloaded[k], 0));
+    if (dtype == HUB_F64 && !fixed_point_ok(H)) {
+        rc = launch_hv_reference(H, P->v[k], P->w[k], dtype, P->comp);
+    } else {
+        rc = ensure_fx_scratch(H);
+        if (rc == HUB_OK) rc = launch_hv_fast(H, P->v[k], P->w[k], dtype, 0.0, nullptr, 0, P->comp);
+    }
+    if (rc != HUB_OK) return rc;
+    HUB_CUDA(cudaEventRecord(P->computed[k], P->comp));
+    // download, then `stream` waits for it
+    HUB_CUDA(cudaStreamWaitEvent(P->down, P->computed[k], 0));
+    HUB_CUDA(cudaMemcpyAsync(w_host, P->w[k], bytes, cudaMemcpyDeviceToHost, P->down));
+    HUB_CUDA(cudaEventRecord(P->downloaded[k], P->down));
+    HUB_CUDA(cudaStreamWaitEvent((cudaStream_t)stream, P->downloaded[k], 0));
+    P->used[k] = true;
+    ++P->calls;
+    return HUB_OK;
 }
 
 int hubbard_set_schedule(hubbard_t H, int vec_rows, int vec_cols, int ctas_rows, int ctas_cols) {

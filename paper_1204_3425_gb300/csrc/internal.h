@@ -98,6 +98,8 @@ namespace hub {
 // same device, lattice and particle number (read-only once uploaded; the
 // device arrays are freed with the last owner).
 struct SpinEntry;
+// Device staging and streams of hubbard_apply_host (allocated on first use).
+struct HostPipe;
 }
 
 struct hubbard_sector {
@@ -126,6 +128,8 @@ struct hubbard_sector {
     // stream of the handle's own allocations (nullptr: cudaMalloc / cudaFree;
     // set by sector_create_streamed for handles that live on one stream)
     cudaStream_t mem_stream = nullptr;
+    // hubbard_apply_host: two slots of device staging, three streams
+    hub::HostPipe* host_pipe = nullptr;
 };
 
 namespace hub {
