@@ -463,6 +463,47 @@ int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int*
 int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode);
 
 /* ---------------------------------------------------------------------------
+ * Queued solver: the batch kernel's one-CTA task path kept running while
+ * sectors are posted (Algorithm 1 on the device for each sector, as in a
+ * batch; the paper notes that small sectors leave the GPU idle, Sec. 5).  A
+ * posted sector is taken by the next CTA of the running kernel that frees up,
+ * so work joins the device while other sectors are being solved.  Capacity
+ * slots each hold one task's descriptor, vectors (max_dim elements), a/b
+ * history and result; the kernel uses `ctas` CTAs (0: two per SM), leaves
+ * after ~0.1 s without work and is launched again by the next post or poll.
+ * Each task draws its start vector from its seed exactly as
+ * hubbard_fill_start_vector does, stops on rho < tol * max(1, |theta|) (tol 0:
+ * 1e-10), breakdown or max_iters (capped at D), and gets err_bound as
+ * lanczos_ground_state defines it.  A task's arithmetic depends only on its
+ * sector, so its result is the same whatever else is queued.  Hop tables are
+ * cached per (lattice, particle number); the kernel leaves before a table pool
+ * has to grow.  Calls on one queue are serialised internally; destroy must not
+ * race other calls.
+ * ------------------------------------------------------------------------- */
+typedef struct hubbard_queue* hubbard_queue_t;
+
+/* Allocates capacity * (24 * max_dim + 16 * max_iters) bytes of device
+ * memory (plus the table pools) and a few host-mapped words.  HUB_EINVAL on
+ * capacity outside [1, 2^20], max_dim outside [1, 2^31], max_iters < 1,
+ * ctas < 0 or tol < 0; HUB_ENOMEM / HUB_ECUDA on allocation failure. */
+int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double tol, int ctas, hubbard_queue_t* out);
+
+/* Posts one sector (host descriptor; same rules as hubbard_batch_create) with
+ * the seed of its start vector; *ticket numbers the posts from 0.  Returns
+ * HUB_EPENDING without posting when the oldest unfinished task still holds
+ * the slot this post needs (the queue is full: poll, then post again);
+ * HUB_EINVAL for a bad sector, more than 127 hops per state or D > max_dim. */
+int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* sector, uint64_t seed, int64_t* ticket);
+
+/* HUB_OK with the result once the task has finished (each result is returned
+ * once), HUB_EPENDING before that; HUB_EINVAL for an unknown or already
+ * collected ticket.  Does not block. */
+int hubbard_queue_poll(hubbard_queue_t Q, int64_t ticket, lanczos_result* out);
+
+/* Lets the kernel finish what was posted, then frees everything. */
+void hubbard_queue_destroy(hubbard_queue_t Q);
+
+/* ---------------------------------------------------------------------------
  * Continuous-batching ground-state server (the paper notes that a small
  * sector alone leaves the GPU idle, Sec. 5; this serves many requests at once).
  * Requests are queued by hubbard_server_submit and taken by worker lanes (host

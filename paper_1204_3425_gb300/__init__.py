@@ -96,6 +96,10 @@ SIGNATURES = {
     "hubbard_batch_results": (ctypes.c_int, [P, P, ctypes.c_int, P, P]),
     "hubbard_batch_autotune": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P]),
     "hubbard_batch_schedule_table": (ctypes.c_int, [P, P, ctypes.c_int, P]),
+    "hubbard_queue_create": (ctypes.c_int, [ctypes.c_int, I64, ctypes.c_int, D, ctypes.c_int, P]),
+    "hubbard_queue_post": (ctypes.c_int, [P, P, ctypes.c_uint64, P]),
+    "hubbard_queue_poll": (ctypes.c_int, [P, I64, P]),
+    "hubbard_queue_destroy": (None, [P]),
     "hubbard_batch_set_shape_mode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
@@ -489,6 +493,60 @@ def hubbard_last_error():
 
 
 PATH_NAMES = {0: "batch", 1: "binary64", 2: "refined"}
+
+
+class Queue:
+    """Owns a hubbard_queue_t: sectors posted to a persistent solver while it runs."""
+
+    def __init__(self, capacity=256, max_dim=20_000, max_iters=1000, tol=1e-10, ctas=0):
+        h = ctypes.c_void_p()
+        _check(load_library().hubbard_queue_create(int(capacity), int(max_dim), int(max_iters), float(tol), int(ctas),
+                                                   ctypes.byref(h)))
+        self.handle = h
+
+    def post(self, ns, bonds, nup, ndn, t, U, seed):
+        """Ticket of the posted sector, or None when the queue is full."""
+        arr = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1))
+        d = SectorDesc(int(ns), int(nup), int(ndn), arr.size // 2, arr.ctypes.data if arr.size else None, float(t),
+                       float(U))
+        tk = I64()
+        rc = load_library().hubbard_queue_post(self.handle, ctypes.byref(d), int(seed), ctypes.byref(tk))
+        if rc == HUB_EPENDING:
+            return None
+        _check(rc)
+        return tk.value
+
+    def poll(self, ticket):
+        """The result dict once finished (returned once), else None."""
+        r = LanczosResult()
+        rc = load_library().hubbard_queue_poll(self.handle, int(ticket), ctypes.byref(r))
+        if rc == HUB_EPENDING:
+            return None
+        _check(rc)
+        return dict(energy=r.energy, residual=r.residual, err_bound=r.err_bound, iters=r.iters, status=r.status,
+                    breakdown=bool(r.breakdown))
+
+    def wait(self, ticket, timeout=60.0):
+        import time
+        end = time.perf_counter() + timeout
+        while True:
+            r = self.poll(ticket)
+            if r is not None:
+                return r
+            if time.perf_counter() > end:
+                raise TimeoutError(f"queue ticket {ticket} not finished after {timeout} s")
+            time.sleep(0.0005)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            load_library().hubbard_queue_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -22,11 +22,14 @@
 #include <map>
 #include <new>
 #include <numeric>
+#include <mutex>
 #include <tuple>
+#include <unordered_map>
 #include <vector>
 
 #include "internal.h"
 #include "row_blocks.cuh"
+#include "splitmix.cuh"
 
 namespace hub {
 namespace {
@@ -50,6 +53,7 @@ struct SectorDesc {
     double t, U;
     int32_t mode;          // schedule bits of its shape (kModeFlat, kModeStage)
     int32_t pad;
+    unsigned long long seed;   // queued tasks: start vector drawn in place from this seed
 };
 
 struct BatchParams {
@@ -85,7 +89,33 @@ struct BatchParams {
     unsigned int* gbar;    // grid barrier counter
     int* nactive;          // sectors of the sweep still iterating
     unsigned long long* claim; // [3] row counters of the sweep's element and update phases, task counter
+    // queue mode (hubbard_queue_*; q_posted == nullptr: a batch): tasks are
+    // posted while the kernel runs; task n uses descriptor / vector / result
+    // slot n % q_cap, its start vector drawn from its seed
+    const volatile unsigned int* q_posted;  // host-mapped: tasks posted so far
+    const volatile unsigned int* q_stop;    // host-mapped: nonzero -> leave once nothing is left to claim
+    unsigned int* q_claim;                  // device: tasks claimed so far
+    volatile unsigned int* q_done;          // host-mapped, per slot: task number + 1 once its result is written
+    int q_cap;
+    long long q_idle;                       // polls of an empty queue before the kernel leaves
 };
+
+__device__ __forceinline__ unsigned int ld_acquire_sys(const volatile unsigned int* p) {
+    unsigned int v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// a queued task's descriptor, read through L2 (the slot was rewritten by the host since the last task in it)
+__device__ __forceinline__ SectorDesc load_desc_cg(const SectorDesc* p) {
+    static_assert(sizeof(SectorDesc) % 8 == 0, "descriptor of 8-byte words");
+    SectorDesc d;
+    const long long* src = reinterpret_cast<const long long*>(p);
+    long long* dst = reinterpret_cast<long long*>(&d);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(SectorDesc) / 8); ++i) dst[i] = __ldcg(src + i);
+    return d;
+}
 
 // Lanczos state of a swept sector between the phases of one iteration.
 struct SweepState {
@@ -577,15 +607,37 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     // smaller ones, one CTA each
     if (P.nswp > 0 && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out)) return;
     __shared__ int sh_task;
+    const bool queued = P.q_posted != nullptr;
     while (true) {
-        // the next task (largest work first) goes to the CTA that asks first
-        if (threadIdx.x == 0) sh_task = (int)atomicAdd(P.claim + 2, 1ull);
+        // the next task (largest work first) goes to the CTA that asks first;
+        // queued: a task number is taken only once that task has been posted,
+        // so a CTA that leaves an idle queue holds none
+        if (threadIdx.x == 0) {
+            if (!queued) {
+                sh_task = (int)atomicAdd(P.claim + 2, 1ull);
+            } else {
+                sh_task = -1;
+                for (long long it = 0; it < P.q_idle; ++it) {
+                    const unsigned c = *(volatile unsigned int*)P.q_claim;
+                    const unsigned n = ld_acquire_sys(P.q_posted);
+                    if (c < n) {
+                        if (atomicCAS(P.q_claim, c, c + 1u) == c) {
+                            sh_task = (int)c;
+                            break;
+                        }
+                        continue;
+                    }
+                    if (*P.q_stop != 0u) break;
+                    __nanosleep(it < 256 ? 200 : 2000);
+                }
+            }
+        }
         __syncthreads();
         const int ti = sh_task;
         __syncthreads();
-        if (ti >= P.ntasks) break;
-        const int sid = P.tasks[ti];
-        const SectorDesc S = P.sec[sid];
+        if (queued ? ti < 0 : ti >= P.ntasks) break;
+        const int sid = queued ? ti % P.q_cap : P.tasks[ti];
+        const SectorDesc S = queued ? load_desc_cg(P.sec + sid) : P.sec[sid];
         const int64_t D = S.D, Ddn = S.Ddn, Dup = S.Dup;
         const int64_t j0 = 0, j1 = D;
         const int mode = P.mode_force >= 0 ? P.mode_force : S.mode;
@@ -599,7 +651,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         int2* X = in_smem ? xs : (P.xg + S.voff);
         double* f = P.f + S.voff;
         double* g = P.g + S.voff;
-        const double* v0 = P.v0 + S.voff;
+        const double* v0 = queued ? nullptr : P.v0 + S.voff;
+        auto v0at = [&](int64_t j) -> double { return queued ? splitmix_uniform(S.seed, j) : v0[j]; };
         const int32_t* urp = P.rp + S.up_rp;
         const int32_t* drp = P.rp + S.dn_rp;
         const uint32_t* uent = P.ent + S.up_ent;
@@ -614,11 +667,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
         };
         // f_1 = v0 / |v0|, f_0 = 0, and the fixed-point copy of f_1 (|f| <= 1)
         double nn[1] = {0.0};
-        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) nn[0] = fma(v0[j], v0[j], nn[0]);
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            const double x = v0at(j);
+            nn[0] = fma(x, x, nn[0]);
+        }
         cta_sum(1, nn);
         const double inv0 = 1.0 / sqrt(nn[0]);
         for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-            const double x = v0[j] * inv0;
+            const double x = v0at(j) * inv0;
             f[j] = x;
             g[j] = 0.0;
             X[j] = fixed47(x);
@@ -738,6 +794,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
             r.status = conv ? HUB_OK : HUB_ENOTCONV;
             r.reserved = 0;
             P.res[sid] = r;
+            if (queued) {
+                __threadfence_system();                      // result and a/b history before the flag
+                P.q_done[sid] = (unsigned)ti + 1u;
+            }
         }
         __syncthreads();
     }
@@ -848,7 +908,19 @@ void batch_free(hubbard_batch* B) {
     dev_free(B->d_rowsec, ms);
 }
 
+int kernel_shape_impl(int* smem_elems, int* grid);
+// dynamic shared memory (bytes; elements to *smem_elems) and grid (two CTAs
+// per SM) of the batch kernel; sets the kernel's shared-memory attribute
+int kernel_shape(int* smem_elems, int* grid) { return kernel_shape_impl(smem_elems, grid); }
+
 int batch_grid(hubbard_batch* B, int* smem_elems) {
+    int grid = 0;
+    const int smem = kernel_shape(smem_elems, &grid);
+    if (smem > 0) B->grid = grid;
+    return smem;
+}
+
+int kernel_shape_impl(int* smem_elems, int* grid) {
     int dev = 0;
     cudaGetDevice(&dev);
     int sms = 0, optin = 0, per_sm_bytes = 0;
@@ -868,7 +940,7 @@ int batch_grid(hubbard_batch* B, int* smem_elems) {
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_lanczos, kBatchThreads, smem);
     if (e != cudaSuccess || per_sm < 1) return -1;
-    B->grid = sms * std::min(per_sm, 2);
+    *grid = sms * std::min(per_sm, 2);
     return smem;
 }
 
@@ -991,6 +1063,12 @@ int batch_launch(hubbard_batch* B, const double* v0_all, int max_iters, double t
     P.gbar = (unsigned int*)(ws + L.gbar);
     P.nactive = (int*)(ws + L.gbar + 4);
     P.claim = (unsigned long long*)(ws + L.gbar + 16);
+    P.q_posted = nullptr;
+    P.q_stop = nullptr;
+    P.q_claim = nullptr;
+    P.q_done = nullptr;
+    P.q_cap = 1;
+    P.q_idle = 0;
     void* args[] = {&P};
     const size_t smem = (size_t)B->smem_elems * sizeof(int2);
     // without sweep sectors every CTA takes one-CTA tasks: a batch of a few
@@ -1373,6 +1451,443 @@ int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int*
         r[5] = sh.mode;
     }
     return HUB_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Queued solver (hubbard_queue_*): the batch kernel's one-CTA task path kept
+// running while sectors are posted.  A task is one sector solved by one CTA
+// (Algorithm 1 on the device, as in a batch).  Slot n % capacity holds task
+// n's descriptor, vectors, a/b history and result; the host publishes a task
+// by raising the posted count in host-mapped memory after its descriptor has
+// been copied, a CTA takes task numbers below that count, and writes the
+// result and then the slot's done word (task number + 1) to host-mapped memory.
+// The kernel leaves after ~0.1 s without work (or at destroy) and is launched
+// again when tasks are posted; a task number is only ever taken once posted,
+// so leaving loses none.  Hop tables are cached per (lattice, particle number)
+// in device pools that grow (between launches) as new ones are needed.
+struct hubbard_queue {
+    int device = 0;
+    int cap = 0;
+    int64_t max_dim = 0, vstride = 0;
+    int max_iters = 0;
+    double tol = 0.0;
+    int ctas = 0;
+    int smem_elems = 0;
+    std::mutex mu;
+    cudaStream_t kstream = nullptr;            // the kernel
+    cudaStream_t cstream = nullptr;            // uploads and reads
+    bool running = false;
+    // device
+    hub::SectorDesc* d_sec = nullptr;          // [cap]
+    double* d_f = nullptr;                     // [cap * vstride] each
+    double* d_g = nullptr;
+    int2* d_xg = nullptr;
+    double* d_ab = nullptr;                    // [cap * 2 * max_iters]
+    int* d_err = nullptr;
+    unsigned int* d_claim = nullptr;
+    // table pools (device, with host-side fill counts and capacities in elements)
+    int32_t* d_rp = nullptr;
+    uint32_t* d_ent = nullptr;
+    uint32_t* d_st = nullptr;
+    int64_t* d_bo = nullptr;
+    int32_t* d_bc = nullptr;
+    uint16_t* d_be = nullptr;
+    size_t n_rp = 0, n_ent = 0, n_st = 0, n_bo = 0, n_bc = 0, n_be = 0;
+    size_t c_rp = 0, c_ent = 0, c_st = 0, c_bo = 0, c_bc = 0, c_be = 0;
+    // host-mapped
+    unsigned int* h_ctl = nullptr;             // [0] posted, [1] stop
+    unsigned int* h_done = nullptr;            // [cap]
+    lanczos_result* h_res = nullptr;           // [cap]
+    unsigned int* m_ctl = nullptr;             // device views of the mapped buffers
+    unsigned int* m_done = nullptr;
+    lanczos_result* m_res = nullptr;
+    // host state
+    struct Cached {
+        int64_t rp, ent, st, D;
+        int W;
+        int64_t blk;
+    };
+    std::map<std::tuple<int, std::vector<std::pair<int, int>>, int>, Cached> cache;
+    uint64_t posted = 0;
+    std::vector<int64_t> slot_ticket;          // task in the slot not yet harvested, -1: free
+    std::vector<int> slot_hops1;               // W_up + W_dn + 1 of that task
+    std::unordered_map<int64_t, lanczos_result> finished;
+};
+
+namespace hub {
+namespace {
+
+// appends n elements to a device pool (capacity in elements), growing it
+// 2x (copying the old contents) when full; the caller has stopped the kernel
+// before a pool may move.  Regions start on 256-byte boundaries, so no cache
+// line mixes the tables of two uploads.
+template <typename T>
+int pool_append(T** pool, size_t* used, size_t* capn, const T* src, size_t n, cudaStream_t s, bool* moved,
+                int64_t* at, size_t align = 256 / sizeof(T)) {
+    const size_t start = (*used + align - 1) / align * align;
+    if (start + n > *capn) {
+        size_t nc = std::max<size_t>(*capn * 2, start + n + align);
+        T* np = nullptr;
+        if (cudaMalloc((void**)&np, nc * sizeof(T)) != cudaSuccess) return fail(HUB_ENOMEM, "queue table pool");
+        if (*used > 0) HUB_CUDA(cudaMemcpyAsync(np, *pool, *used * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        HUB_CUDA(cudaStreamSynchronize(s));
+        cudaFree(*pool);
+        *pool = np;
+        *capn = nc;
+        *moved = true;
+    }
+    if (n > 0) HUB_CUDA(cudaMemcpyAsync(*pool + start, src, n * sizeof(T), cudaMemcpyHostToDevice, s));
+    *used = start + n;
+    *at = (int64_t)start;
+    return HUB_OK;
+}
+
+}  // namespace
+}  // namespace hub
+
+namespace hub {
+namespace {
+
+void queue_set_stop(hubbard_queue* Q, unsigned v) {
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *(volatile unsigned int*)(Q->h_ctl + 1) = v;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+}
+
+// lets the running kernel finish every posted task and leave
+int queue_stop_kernel(hubbard_queue* Q) {
+    if (!Q->running) return HUB_OK;
+    queue_set_stop(Q, 1u);
+    const cudaError_t e = cudaStreamSynchronize(Q->kstream);
+    queue_set_stop(Q, 0u);
+    Q->running = false;
+    if (e != cudaSuccess) return cuda_fail(e, "queue kernel");
+    return HUB_OK;
+}
+
+// device tables of one spin species (cached per lattice and particle number)
+int queue_spin(hubbard_queue* Q, int ns, const std::vector<std::pair<int, int>>& bl, int N,
+               hubbard_queue::Cached* out) {
+    const auto key = std::make_tuple(ns, bl, N);
+    auto it = Q->cache.find(key);
+    if (it != Q->cache.end()) {
+        *out = it->second;
+        return HUB_OK;
+    }
+    SpinTables T;
+    build_spin_tables(ns, N, bl, T);
+    std::vector<uint32_t> ent(T.tgt.size());
+    for (size_t k = 0; k < T.tgt.size(); ++k) ent[k] = ((uint32_t)T.tgt[k] << 1) | (T.sign[k] < 0 ? 1u : 0u);
+    RowBlocks rb;
+    bool rows = false;
+    std::vector<uint16_t> be;
+    if (T.D <= kRowTableMaxD) {
+        build_row_blocks(T, 8, rb);
+        rows = rb.narrow;
+        if (rows) {
+            be.resize(rb.ent.size());
+            for (size_t i = 0; i < rb.ent.size(); ++i) be[i] = (uint16_t)rb.ent[i];
+        }
+    }
+    // a pool that must grow moves: the kernel leaves first
+    // (the per-group arrays bo and bc advance in step: the same alignment, 64 groups)
+    auto fits = [](size_t used, size_t capn, size_t n, size_t align) {
+        return (used + align - 1) / align * align + n <= capn;
+    };
+    const bool grow = !fits(Q->n_rp, Q->c_rp, T.rowptr.size(), 64) || !fits(Q->n_ent, Q->c_ent, ent.size(), 64) ||
+                      !fits(Q->n_st, Q->c_st, T.states.size(), 64) ||
+                      (rows && (!fits(Q->n_bo, Q->c_bo, rb.boff.size(), 64) ||
+                                !fits(Q->n_bc, Q->c_bc, rb.bcnt.size(), 64) || !fits(Q->n_be, Q->c_be, be.size(), 128)));
+    int rc;
+    if (grow && (rc = queue_stop_kernel(Q))) return rc;
+    bool moved = false;
+    hubbard_queue::Cached c{0, 0, 0, T.D, T.W, -1};
+    if ((rc = pool_append(&Q->d_rp, &Q->n_rp, &Q->c_rp, T.rowptr.data(), T.rowptr.size(), Q->cstream, &moved, &c.rp)))
+        return rc;
+    if ((rc = pool_append(&Q->d_ent, &Q->n_ent, &Q->c_ent, ent.data(), ent.size(), Q->cstream, &moved, &c.ent)))
+        return rc;
+    if ((rc = pool_append(&Q->d_st, &Q->n_st, &Q->c_st, T.states.data(), T.states.size(), Q->cstream, &moved, &c.st)))
+        return rc;
+    if (rows) {
+        int64_t be_at = 0, bc_at = 0;
+        if ((rc = pool_append(&Q->d_be, &Q->n_be, &Q->c_be, be.data(), be.size(), Q->cstream, &moved, &be_at)))
+            return rc;
+        std::vector<int64_t> bo(rb.boff.size());
+        for (size_t g = 0; g < bo.size(); ++g) bo[g] = be_at + rb.boff[g];
+        if ((rc = pool_append(&Q->d_bo, &Q->n_bo, &Q->c_bo, bo.data(), bo.size(), Q->cstream, &moved, &c.blk, 64)))
+            return rc;
+        if ((rc = pool_append(&Q->d_bc, &Q->n_bc, &Q->c_bc, rb.bcnt.data(), rb.bcnt.size(), Q->cstream, &moved,
+                              &bc_at, 64)))
+            return rc;
+        if (bc_at != c.blk) {
+            // the two per-group arrays are indexed by the same group number
+            return fail(HUB_EDEVICE, "queue row-table pools out of step");
+        }
+    }
+    HUB_CUDA(cudaStreamSynchronize(Q->cstream));
+    Q->cache.emplace(key, c);
+    *out = c;
+    return HUB_OK;
+}
+
+}  // namespace
+}  // namespace hub
+
+namespace hub {
+namespace {
+
+// launches the task kernel over the queue (the caller holds the lock)
+int queue_launch(hubbard_queue* Q) {
+    BatchParams P{};
+    P.sec = Q->d_sec;
+    P.tasks = nullptr;
+    P.ntasks = 0;
+    P.rp = Q->d_rp;
+    P.ent = Q->d_ent;
+    P.st = Q->d_st;
+    P.bo = Q->d_bo;
+    P.bc = Q->d_bc;
+    P.be = Q->d_be;
+    P.v0 = nullptr;
+    P.f = Q->d_f;
+    P.g = Q->d_g;
+    P.xg = Q->d_xg;
+    P.ab = Q->d_ab;
+    P.res = Q->m_res;
+    P.err = Q->d_err;
+    P.max_iters = Q->max_iters;
+    P.iter_cap = Q->max_iters;
+    P.tol = Q->tol;
+    P.smem_elems = Q->smem_elems;
+    P.mode_force = -1;
+    P.spin_limit = 20000000;
+    P.nswp = 0;
+    P.q_posted = Q->m_ctl;
+    P.q_stop = Q->m_ctl + 1;
+    P.q_claim = Q->d_claim;
+    P.q_done = Q->m_done;
+    P.q_cap = Q->cap;
+    P.q_idle = 50000;                      // ~0.1 s of 2-us sleeps without a posted task
+    k_batch_lanczos<<<Q->ctas, kBatchThreads, (size_t)Q->smem_elems * sizeof(int2), Q->kstream>>>(P);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    Q->running = true;
+    return HUB_OK;
+}
+
+// moves finished tasks' results (with their a-posteriori bounds) to the host
+// map and frees their slots; relaunches the kernel if it left with tasks posted
+int queue_harvest(hubbard_queue* Q) {
+    std::vector<int> ready;
+    for (int k = 0; k < Q->cap; ++k) {
+        const int64_t t = Q->slot_ticket[(size_t)k];
+        if (t < 0) continue;
+        const unsigned d = *(volatile unsigned int*)(Q->h_done + k);
+        if (d == (unsigned)(t + 1)) ready.push_back(k);
+    }
+    if (!ready.empty()) {
+        std::atomic_thread_fence(std::memory_order_acquire);
+        const size_t m = (size_t)2 * Q->max_iters;
+        std::vector<double> ab(ready.size() * m);
+        for (size_t i = 0; i < ready.size(); ++i)
+            HUB_CUDA(cudaMemcpyAsync(ab.data() + i * m, Q->d_ab + (size_t)ready[i] * m, m * sizeof(double),
+                                     cudaMemcpyDeviceToHost, Q->cstream));
+        HUB_CUDA(cudaStreamSynchronize(Q->cstream));
+        for (size_t i = 0; i < ready.size(); ++i) {
+            const int k = ready[i];
+            lanczos_result r;
+            std::memcpy(&r, (const void*)(Q->h_res + k), sizeof r);
+            const int it = r.iters;
+            if (it >= 1 && it <= Q->max_iters) {
+                const double* A = ab.data() + i * m;
+                const double* Bv = A + Q->max_iters;
+                const double gap = tridiag_gap_lower(A, Bv, it, Bv[it - 1], r.energy);
+                r.err_bound = energy_error_bound(r.residual, gap) +
+                              rounding_floor(Q->slot_hops1[(size_t)k], HUB_F64, tridiag_scale(A, Bv, it));
+            } else {
+                r.err_bound = INFINITY;
+            }
+            Q->finished[Q->slot_ticket[(size_t)k]] = r;
+            Q->slot_ticket[(size_t)k] = -1;
+        }
+    }
+    if (Q->running && cudaStreamQuery(Q->kstream) == cudaSuccess) Q->running = false;
+    if (!Q->running) {
+        bool pending = false;
+        for (int k = 0; k < Q->cap && !pending; ++k) pending = Q->slot_ticket[(size_t)k] >= 0;
+        if (pending) return queue_launch(Q);
+    }
+    return HUB_OK;
+}
+
+void queue_free(hubbard_queue* Q) {
+    if (Q->h_ctl != nullptr && Q->running) {
+        queue_set_stop(Q, 1u);
+        cudaStreamSynchronize(Q->kstream);
+    }
+    if (Q->cstream) cudaStreamSynchronize(Q->cstream);
+    cudaFree(Q->d_sec);
+    cudaFree(Q->d_f);
+    cudaFree(Q->d_g);
+    cudaFree(Q->d_xg);
+    cudaFree(Q->d_ab);
+    cudaFree(Q->d_err);
+    cudaFree(Q->d_claim);
+    cudaFree(Q->d_rp);
+    cudaFree(Q->d_ent);
+    cudaFree(Q->d_st);
+    cudaFree(Q->d_bo);
+    cudaFree(Q->d_bc);
+    cudaFree(Q->d_be);
+    if (Q->h_ctl) cudaFreeHost(Q->h_ctl);
+    if (Q->h_done) cudaFreeHost(Q->h_done);
+    if (Q->h_res) cudaFreeHost(Q->h_res);
+    if (Q->kstream) cudaStreamDestroy(Q->kstream);
+    if (Q->cstream) cudaStreamDestroy(Q->cstream);
+    delete Q;
+}
+
+}  // namespace
+}  // namespace hub
+
+extern "C" {
+
+int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double tol, int ctas, hubbard_queue_t* out) {
+    using namespace hub;
+    clear_error();
+    if (out == nullptr || capacity < 1 || capacity > (1 << 20) || max_dim < 1 || max_dim > ((int64_t)1 << 31) ||
+        max_iters < 1 || ctas < 0 || !(tol >= 0.0))
+        return fail(HUB_EINVAL, "bad queue arguments");
+    *out = nullptr;
+    hubbard_queue* Q = new (std::nothrow) hubbard_queue();
+    if (Q == nullptr) return fail(HUB_ENOMEM, "host allocation");
+    cudaGetDevice(&Q->device);
+    Q->cap = capacity;
+    Q->max_dim = max_dim;
+    Q->vstride = (max_dim + 1) / 2 * 2;           // every slot's vectors 16-byte aligned
+    Q->max_iters = max_iters;
+    Q->tol = tol > 0.0 ? tol : 1e-10;
+    int grid = 0;
+    if (kernel_shape(&Q->smem_elems, &grid) < 0) {
+        queue_free(Q);
+        return fail(HUB_ECUDA, "queue kernel occupancy");
+    }
+    Q->ctas = ctas > 0 ? std::min(ctas, grid) : grid;
+    Q->slot_ticket.assign((size_t)capacity, -1);
+    Q->slot_hops1.assign((size_t)capacity, 1);
+    const size_t nv = (size_t)capacity * (size_t)Q->vstride;
+    cudaError_t e = cudaStreamCreateWithFlags(&Q->kstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&Q->cstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_sec, (size_t)capacity * sizeof(SectorDesc));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_f, nv * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_g, nv * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_xg, nv * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_ab, (size_t)capacity * 2 * max_iters * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_err, 256);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_claim, 256);
+    if (e == cudaSuccess) e = cudaMemset(Q->d_err, 0, 256);
+    if (e == cudaSuccess) e = cudaMemset(Q->d_claim, 0, 256);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&Q->h_ctl, 256, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&Q->h_done, (size_t)capacity * sizeof(unsigned int), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostAlloc((void**)&Q->h_res, (size_t)capacity * sizeof(lanczos_result), cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&Q->m_ctl, Q->h_ctl, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&Q->m_done, Q->h_done, 0);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&Q->m_res, Q->h_res, 0);
+    if (e != cudaSuccess) {
+        queue_free(Q);
+        return cuda_fail(e, "queue allocation");
+    }
+    std::memset(Q->h_ctl, 0, 256);
+    std::memset(Q->h_done, 0, (size_t)capacity * sizeof(unsigned int));
+    std::memset((void*)Q->h_res, 0, (size_t)capacity * sizeof(lanczos_result));
+    *out = Q;
+    return HUB_OK;
+}
+
+int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* d, uint64_t seed, int64_t* ticket) {
+    using namespace hub;
+    clear_error();
+    if (Q == nullptr || d == nullptr || ticket == nullptr) return fail(HUB_EINVAL, "null argument");
+    if (d->ns < 1 || d->ns > 32 || d->nup < 0 || d->nup > d->ns || d->ndn < 0 || d->ndn > d->ns || d->n_bonds < 0 ||
+        (d->n_bonds > 0 && d->bonds == nullptr) || !std::isfinite(d->t) || !std::isfinite(d->U))
+        return fail(HUB_EINVAL, "queue: invalid sector");
+    std::vector<std::pair<int, int>> bl;
+    for (int b = 0; b < d->n_bonds; ++b) {
+        const int x = d->bonds[2 * b], y = d->bonds[2 * b + 1];
+        const std::pair<int, int> key(std::min(x, y), std::max(x, y));
+        if (x < 0 || x >= d->ns || y < 0 || y >= d->ns || x == y)
+            return fail(HUB_EINVAL, "queue: bad bond");
+        for (const auto& q : bl)
+            if (std::min(q.first, q.second) == key.first && std::max(q.first, q.second) == key.second)
+                return fail(HUB_EINVAL, "queue: duplicate bond");
+        bl.emplace_back(x, y);
+    }
+    std::lock_guard<std::mutex> lk(Q->mu);
+    int rc;
+    if ((rc = queue_harvest(Q))) return rc;
+    const int k = (int)(Q->posted % (uint64_t)Q->cap);
+    if (Q->slot_ticket[(size_t)k] >= 0) return HUB_EPENDING;     // full: the oldest task's slot is still in use
+    hubbard_queue::Cached cu{}, cd{};
+    if ((rc = queue_spin(Q, d->ns, bl, d->nup, &cu)) || (rc = queue_spin(Q, d->ns, bl, d->ndn, &cd))) return rc;
+    if (cu.W + cd.W > 127) return fail(HUB_EINVAL, "queue: more than 127 hops per state");
+    if (cu.D * cd.D > Q->max_dim) return fail(HUB_EINVAL, "queue: sector above the queue's max_dim");
+    SectorDesc s{};
+    s.Dup = cu.D;
+    s.Ddn = cd.D;
+    s.D = cu.D * cd.D;
+    s.voff = (int64_t)k * Q->vstride;
+    s.up_rp = cu.rp;
+    s.dn_rp = cd.rp;
+    s.up_ent = cu.ent;
+    s.dn_ent = cd.ent;
+    s.up_st = cu.st;
+    s.dn_st = cd.st;
+    s.ab = (int64_t)k * 2 * Q->max_iters;
+    s.dn_blk = cd.blk;
+    s.t = d->t;
+    s.U = d->U;
+    s.mode = kModeDefault;
+    s.seed = (unsigned long long)seed;
+    HUB_CUDA(cudaMemcpyAsync(Q->d_sec + k, &s, sizeof s, cudaMemcpyHostToDevice, Q->cstream));
+    HUB_CUDA(cudaStreamSynchronize(Q->cstream));
+    Q->slot_ticket[(size_t)k] = (int64_t)Q->posted;
+    Q->slot_hops1[(size_t)k] = cu.W + cd.W + 1;
+    *(volatile unsigned int*)(Q->h_done + k) = 0u;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *(volatile unsigned int*)Q->h_ctl = (unsigned int)(Q->posted + 1);       // publish
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    *ticket = (int64_t)Q->posted;
+    ++Q->posted;
+    if (!Q->running) return queue_launch(Q);
+    return HUB_OK;
+}
+
+int hubbard_queue_poll(hubbard_queue_t Q, int64_t ticket, lanczos_result* out) {
+    using namespace hub;
+    clear_error();
+    if (Q == nullptr || out == nullptr) return fail(HUB_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(Q->mu);
+    if (ticket < 0 || (uint64_t)ticket >= Q->posted) return fail(HUB_EINVAL, "unknown ticket");
+    int rc;
+    if ((rc = queue_harvest(Q))) return rc;
+    auto it = Q->finished.find(ticket);
+    if (it == Q->finished.end()) {
+        if (Q->slot_ticket[(size_t)(ticket % Q->cap)] != ticket) return fail(HUB_EINVAL, "ticket already collected");
+        int err = 0;
+        if (!Q->running && cudaMemcpy(&err, Q->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err != 0)
+            return fail(err, "queue kernel reported an error");
+        return HUB_EPENDING;
+    }
+    *out = it->second;
+    Q->finished.erase(it);
+    return HUB_OK;
+}
+
+void hubbard_queue_destroy(hubbard_queue_t Q) {
+    if (Q == nullptr) return;
+    hub::queue_free(Q);
 }
 
 }  // extern "C"

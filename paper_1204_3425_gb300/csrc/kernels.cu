@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.h"
+#include "splitmix.cuh"
 
 namespace hub {
 
@@ -387,17 +388,10 @@ __global__ void k_psi_multi(const float* __restrict__ base, int64_t stride, int 
     }
 }
 
-// Seeded uniform [-1, 1) start vector: SplitMix64 (Steele, Lea, Flood 2014)
-// in counter mode, counter = seed * 2^40 + (start + i); the top 53 bits of
-// the output give x in [0, 1), v = 2x - 1 (exact in binary64).
+// Seeded uniform [-1, 1) start vector (splitmix.cuh), elements start .. start + n
 __global__ void k_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        unsigned long long z = seed * (1ull << 40) + (unsigned long long)(start + i) + 0x9E3779B97F4A7C15ull;
-        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-        z ^= z >> 31;
-        const double x = (double)(z >> 11) * 0x1p-53;
-        const double val = 2.0 * x - 1.0;
+        const double val = splitmix_uniform(seed, start + i);
         if (dtype == HUB_F64) ((double*)v)[i] = val;
         else ((float*)v)[i] = (float)val;
     }
