@@ -500,6 +500,10 @@ int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* sector, uin
  * collected ticket.  Does not block. */
 int hubbard_queue_poll(hubbard_queue_t Q, int64_t ticket, lanczos_result* out);
 
+/* Up to cap finished results not yet returned, in any order, with their
+ * tickets (host arrays of cap); *n_found = how many.  Does not block. */
+int hubbard_queue_collect(hubbard_queue_t Q, int64_t* tickets, lanczos_result* out, int cap, int* n_found);
+
 /* Lets the kernel finish what was posted, then frees everything. */
 void hubbard_queue_destroy(hubbard_queue_t Q);
 
@@ -510,11 +514,16 @@ void hubbard_queue_destroy(hubbard_queue_t Q);
  * threads, each with its own non-blocking stream) as soon as a lane is free and
  * the request's device-memory footprint fits what remains of the budget, first
  * come first served within each queue:
- *   D <= small_max_dim                : the small queue; a small lane takes every
+ *   D <= small_max_dim                : the small queue.  With a GPU, one
+ *       small lane posts each small request to a queued solver
+ *       (hubbard_queue_*) as soon as it arrives: the request joins the
+ *       persistent kernel that is already solving the earlier ones, on its
+ *       next free CTA (small_ctas CTAs, 0: 32; the rest of the GPU stays
+ *       with the big lanes); the queue's memory (up to 1024 slots of
+ *       small_max_dim elements, within a quarter of the budget) is taken
+ *       from the budget when the server starts.  With host_solver (or small_ctas < 0), small lanes take every
  *       small request waiting (up to batch_max, within the budget) into one
- *       launch of the batched solver, each sector a one-CTA task (the launch
- *       occupies one CTA per sector, the rest of the GPU stays with the other
- *       lanes); tol is relative, rho < tol max(1, |theta|);
+ *       micro-batch instead.  tol is relative, rho < tol max(1, |theta|);
  *   small_max_dim < D <= mid_max_dim  : a big lane, binary64 Lanczos
  *       (lanczos_ground_state, absolute rho < tol);
  *   D > mid_max_dim                   : a big lane, binary32 Lanczos with
@@ -548,14 +557,14 @@ typedef int (*hubbard_host_solver)(void* ctx, uint64_t ticket, const hubbard_req
 
 typedef struct {
     double hbm_budget;         /* bytes of device memory for requests (<= 0: 80 % of the free memory) */
-    int32_t small_lanes;       /* concurrent micro-batches */
+    int32_t small_lanes;       /* lanes of the small queue (micro-batch mode: concurrent micro-batches) */
     int32_t big_lanes;         /* concurrent single-sector solves */
     int64_t small_max_dim;
     int64_t mid_max_dim;
     int32_t max_iters;         /* <= 0: 1000 */
     int32_t batch_max;         /* requests per micro-batch (<= 0: 1024) */
     int32_t store_vectors;     /* binary32 Lanczos vectors kept per refined request (>= 0) */
-    int32_t reserved;
+    int32_t small_ctas;        /* CTAs of the queued small-sector solver (0: 32; < 0: micro-batches) */
     double tol;                /* <= 0: 1e-10 */
     hubbard_host_solver host_solver;
     void* host_ctx;

@@ -44,7 +44,7 @@ HOST_SOLVER = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_uint64, c
 class ServerOpts(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_double), ("small_lanes", ctypes.c_int32), ("big_lanes", ctypes.c_int32),
                 ("small_max_dim", ctypes.c_int64), ("mid_max_dim", ctypes.c_int64), ("max_iters", ctypes.c_int32),
-                ("batch_max", ctypes.c_int32), ("store_vectors", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("batch_max", ctypes.c_int32), ("store_vectors", ctypes.c_int32), ("small_ctas", ctypes.c_int32),
                 ("tol", ctypes.c_double), ("host_solver", HOST_SOLVER), ("host_ctx", ctypes.c_void_p)]
 
 
@@ -100,6 +100,7 @@ SIGNATURES = {
     "hubbard_queue_post": (ctypes.c_int, [P, P, ctypes.c_uint64, P]),
     "hubbard_queue_poll": (ctypes.c_int, [P, I64, P]),
     "hubbard_queue_destroy": (None, [P]),
+    "hubbard_queue_collect": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_batch_set_shape_mode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
@@ -526,6 +527,16 @@ class Queue:
         return dict(energy=r.energy, residual=r.residual, err_bound=r.err_bound, iters=r.iters, status=r.status,
                     breakdown=bool(r.breakdown))
 
+    def collect(self, cap=1024):
+        """{ticket: result dict} of finished tasks not yet returned (each returned once)."""
+        tk = (ctypes.c_int64 * max(cap, 1))()
+        rs = (LanczosResult * max(cap, 1))()
+        n = ctypes.c_int()
+        _check(load_library().hubbard_queue_collect(self.handle, tk, rs, int(cap), ctypes.byref(n)))
+        return {tk[i]: dict(energy=rs[i].energy, residual=rs[i].residual, err_bound=rs[i].err_bound,
+                            iters=rs[i].iters, status=rs[i].status, breakdown=bool(rs[i].breakdown))
+                for i in range(n.value)}
+
     def wait(self, ticket, timeout=60.0):
         import time
         end = time.perf_counter() + timeout
@@ -559,7 +570,7 @@ class Server:
     status) run by the lanes instead of the CUDA solvers."""
 
     def __init__(self, hbm_budget=0.0, small_lanes=2, big_lanes=8, small_max_dim=20_000, mid_max_dim=200_000,
-                 max_iters=1000, batch_max=1024, store_vectors=128, tol=1e-10, host_solver=None):
+                 max_iters=1000, batch_max=1024, store_vectors=128, tol=1e-10, host_solver=None, small_ctas=0):
         lib = load_library()
         self._cb = None
         cb = HOST_SOLVER()
@@ -578,7 +589,7 @@ class Server:
                 return int(r.get("status", HUB_OK))
             self._cb = cb = HOST_SOLVER(_solve)
         opts = ServerOpts(float(hbm_budget), int(small_lanes), int(big_lanes), int(small_max_dim), int(mid_max_dim),
-                          int(max_iters), int(batch_max), int(store_vectors), 0, float(tol), cb, None)
+                          int(max_iters), int(batch_max), int(store_vectors), int(small_ctas), float(tol), cb, None)
         h = ctypes.c_void_p()
         _check(lib.hubbard_server_create(ctypes.byref(opts), ctypes.byref(h)))
         self.handle = h

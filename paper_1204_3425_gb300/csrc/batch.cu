@@ -1885,6 +1885,26 @@ int hubbard_queue_poll(hubbard_queue_t Q, int64_t ticket, lanczos_result* out) {
     return HUB_OK;
 }
 
+int hubbard_queue_collect(hubbard_queue_t Q, int64_t* tickets, lanczos_result* out, int cap, int* n_out) {
+    using namespace hub;
+    clear_error();
+    if (Q == nullptr || n_out == nullptr || cap < 0 || (cap > 0 && (tickets == nullptr || out == nullptr)))
+        return fail(HUB_EINVAL, "bad collect arguments");
+    std::lock_guard<std::mutex> lk(Q->mu);
+    *n_out = 0;
+    int rc;
+    if ((rc = queue_harvest(Q))) return rc;
+    int n = 0;
+    for (auto it = Q->finished.begin(); it != Q->finished.end() && n < cap;) {
+        tickets[n] = it->first;
+        out[n] = it->second;
+        ++n;
+        it = Q->finished.erase(it);
+    }
+    *n_out = n;
+    return HUB_OK;
+}
+
 void hubbard_queue_destroy(hubbard_queue_t Q) {
     if (Q == nullptr) return;
     hub::queue_free(Q);

@@ -72,6 +72,8 @@ struct hubbard_server {
     size_t budget = 0, free_bytes = 0, peak = 0;
     hubbard_server_stats st{};
     bool stop = false;
+    bool queued_small = false;                 // small requests go to a queued persistent solver
+    int queue_cap = 0;                         // its slots
     std::vector<std::thread> threads;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -257,6 +259,79 @@ void small_lane(hubbard_server* S) {
     if (st) cudaStreamDestroy(st);
 }
 
+// The small queue with a GPU: every small request is posted to one queued
+// solver as soon as it is taken (its CTAs solve posted sectors while others
+// are being posted); finished results are collected and answered.
+void queue_lane(hubbard_server* S) {
+    cudaSetDevice(S->device);
+    hubbard_queue_t Q = nullptr;
+    const int qrc = hubbard_queue_create(S->queue_cap, std::max<int64_t>(S->opts.small_max_dim, 1), S->opts.max_iters,
+                                         S->opts.tol, S->opts.small_ctas > 0 ? S->opts.small_ctas : 32, &Q);
+    std::deque<Req*> local;                                   // taken, not yet posted (queue full)
+    std::unordered_map<int64_t, Req*> inflight;
+    const int kCollect = 256;
+    std::vector<int64_t> tks(kCollect);
+    std::vector<lanczos_result> rs(kCollect);
+    while (true) {
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            if (inflight.empty() && local.empty())
+                S->cv_work.wait(lk, [&] { return S->stop || !S->small_q.empty(); });
+            if (S->stop && inflight.empty()) break;          // posted requests finish first
+            int taken = 0;
+            while (!S->stop && !S->small_q.empty()) {
+                Req* r = S->small_q.front();
+                S->small_q.pop_front();
+                r->state = 1;
+                r->out.t_admit = S->now();
+                S->st.running += 1;
+                S->st.batched_requests += 1;
+                local.push_back(r);
+                ++taken;
+            }
+            if (taken) S->st.batches += 1;
+        }
+        while (!local.empty()) {
+            Req* r = local.front();
+            if (qrc != HUB_OK) {
+                local.pop_front();
+                finish(S, r, lanczos_result{}, qrc);
+                continue;
+            }
+            const hubbard_request& q = r->desc;
+            const hubbard_sector_desc d{q.ns, q.nup, q.ndn, q.n_bonds, q.bonds, q.t, q.U};
+            int64_t tk = -1;
+            const int rc = hubbard_queue_post(Q, &d, q.seed, &tk);
+            if (rc == HUB_EPENDING) break;                       // every slot busy: collect first
+            local.pop_front();
+            if (rc != HUB_OK) finish(S, r, lanczos_result{}, rc);
+            else inflight.emplace(tk, r);
+        }
+        bool progress = false;
+        if (Q != nullptr && !inflight.empty()) {
+            int n = 0;
+            const int rc = hubbard_queue_collect(Q, tks.data(), rs.data(), kCollect, &n);
+            if (rc != HUB_OK) {
+                for (auto& kv : inflight) finish(S, kv.second, lanczos_result{}, rc);
+                inflight.clear();
+            }
+            for (int i = 0; i < n; ++i) {
+                auto it = inflight.find(tks[(size_t)i]);
+                if (it == inflight.end()) continue;
+                finish(S, it->second, rs[(size_t)i], rs[(size_t)i].status);
+                inflight.erase(it);
+                progress = true;
+            }
+        }
+        if (!progress && (!inflight.empty() || !local.empty())) {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+    for (Req* r : local) finish(S, r, lanczos_result{}, HUB_EINVAL);   // taken at stop, never posted
+    hubbard_queue_destroy(Q);
+}
+
 void big_lane(hubbard_server* S) {
     cudaStream_t st = nullptr;
     if (!S->opts.host_solver) {
@@ -360,9 +435,27 @@ int hubbard_server_create(const hubbard_server_opts* opts, hubbard_server_t* out
     }
     S->budget = S->free_bytes = (size_t)budget;
     S->st.budget_bytes = (double)S->budget;
+    // small requests: a queued persistent solver (GPU) or micro-batches; the
+    // queue's slots (vectors of small_max_dim elements and a/b histories) and
+    // its table pools come out of the budget now
+    S->queued_small = !o.host_solver && o.small_ctas >= 0 && o.small_lanes > 0 && o.small_max_dim > 0;
+    if (S->queued_small) {
+        const size_t per = 24 * (size_t)((o.small_max_dim + 1) / 2 * 2) + 16 * (size_t)o.max_iters;
+        const size_t pools = (size_t)64 << 20;
+        const size_t room = S->budget / 4 > pools ? S->budget / 4 - pools : 0;
+        S->queue_cap = (int)std::min<size_t>(1024, room / per);
+        if (S->queue_cap < 1) {
+            S->queued_small = false;
+        } else {
+            S->free_bytes -= (size_t)S->queue_cap * per + pools;
+            S->peak = S->budget - S->free_bytes;
+        }
+    }
     S->t0 = Clock::now();
     try {
-        for (int i = 0; i < o.small_lanes; ++i) S->threads.emplace_back(small_lane, S);
+        if (S->queued_small) S->threads.emplace_back(queue_lane, S);
+        else
+            for (int i = 0; i < o.small_lanes; ++i) S->threads.emplace_back(small_lane, S);
         for (int i = 0; i < o.big_lanes; ++i) S->threads.emplace_back(big_lane, S);
     } catch (...) {
         {
@@ -394,7 +487,7 @@ int hubbard_server_submit(hubbard_server_t S, const hubbard_request* req, uint64
     r->D = (int64_t)D;
     r->path = r->D <= S->opts.small_max_dim ? kPathBatch
                                             : (r->D <= S->opts.mid_max_dim ? kPathBinary64 : kPathRefined);
-    r->footprint = base_footprint(S, r->path, r->D);
+    r->footprint = (r->path == kPathBatch && S->queued_small) ? 0 : base_footprint(S, r->path, r->D);
     r->out.path = r->path;
     std::lock_guard<std::mutex> lk(S->mu);
     if (r->footprint > S->budget) return fail(HUB_ENOMEM, "request footprint above the server budget");

@@ -3,9 +3,10 @@
 The scheduling and every numerical step run in the library
 (hubbard_server_*, csrc/server.cpp): requests are queued with
 hubbard_server_submit and taken by lanes (host threads with their own
-streams) as lanes and device memory free up; small sectors are micro-batched
-into the persistent batched solver, mid-sized ones solved in binary64, large
-ones in binary32 with binary64 refinement.  This module only submits the
+streams) as lanes and device memory free up; small sectors are posted, as
+they arrive, to a queued persistent solver whose CTAs take each new sector as
+they free up, mid-sized ones solved in binary64, large ones in binary32 with
+binary64 refinement.  This module only submits the
 requests of a trace at their arrival times, waits for the answers and
 summarises latencies (arrival to answer, on the server's clock) and
 throughput.

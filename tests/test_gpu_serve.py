@@ -39,8 +39,8 @@ def _server(**kw):
 
 
 def test_serve_mixed_trace(dev):
-    """60 requests of every path (micro-batched small sectors, binary64 and
-    refined lanes), all answered, each energy within 1e-9 of the oracle and
+    """60 requests of every path (small sectors through the queued persistent
+    solver, binary64 and refined lanes), all answered, each energy within 1e-9 of the oracle and
     within its own error bound."""
     reqs = _trace(60, 21)
     srv = _server()
@@ -81,6 +81,8 @@ def test_serve_c_abi_submit_poll(dev):
     """The C ABI directly: submit, poll until done, wait; a bad request is refused."""
     from workload import ring
     srv = hub.Server(8e9, small_lanes=1, big_lanes=2, small_max_dim=20_000, mid_max_dim=400_000)
+    free0 = srv.stats()["free_bytes"]                    # the queued solver's memory is reserved at start
+    assert free0 < srv.stats()["budget_bytes"]
     tks = [srv.submit(8, ring(8), 4, 4, 1.0, 4.0, 1234), srv.submit(10, ring(10), 5, 5, 1.0, 6.0, 7),
            srv.submit(12, ring(12), 5, 6, 1.0, 4.5, 11)]
     import time
@@ -103,8 +105,33 @@ def test_serve_c_abi_submit_poll(dev):
     with pytest.raises(hub.HubError):
         srv.submit(4, [(0, 4)], 1, 1, 1.0, 1.0, 1)          # bond endpoint out of range
     st = srv.stats()
-    assert st["completed"] == 3 and st["verified"] == 3 and st["free_bytes"] == st["budget_bytes"]
+    assert st["completed"] == 3 and st["verified"] == 3 and st["free_bytes"] == free0
     srv.close()
+
+
+def test_serve_small_request_joins_running_work(dev):
+    """Continuous batching of small sectors: a request submitted while 24 others
+    are being solved by the queued solver (4 CTAs) is taken by its next free CTA
+    and answered before the earlier requests are all done -- a micro-batch would
+    have made it wait for all of them."""
+    import time
+    from workload import lattice_by_name, ring
+    srv = hub.Server(8e9, small_lanes=1, big_lanes=1, small_max_dim=20_000, mid_max_dim=400_000, small_ctas=4)
+    ns, bonds = lattice_by_name("sq3x3")
+    early = [srv.submit(ns, bonds, 4, 4, 1.0, 2.0 + 0.25 * k, 100 + k) for k in range(24)]
+    time.sleep(0.05)
+    late = srv.submit(4, ring(4), 2, 2, 1.0, 4.0, 5)
+    r_late = srv.wait(late, 120.0)
+    r_early = [srv.wait(tk, 120.0) for tk in early]
+    srv.close()
+    assert r_late["status"] == 0 and all(r["status"] == 0 for r in r_early)
+    assert r_late["t_admit"] < max(r["t_done"] for r in r_early)       # admitted while the others ran
+    assert r_late["t_done"] < max(r["t_done"] for r in r_early)        # and answered before they all were
+    e_ref, _ = ground_energy(4, ring(4), 2, 2, 1.0, 4.0, seed=5)
+    assert abs(r_late["energy"] - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
+    for k, r in enumerate(r_early[:4]):
+        e_ref, _ = ground_energy(ns, bonds, 4, 4, 1.0, 2.0 + 0.25 * k, seed=100 + k)
+        assert abs(r["energy"] - e_ref) <= 1e-9 * max(1.0, abs(e_ref))
 
 
 def test_fill_start_vector_matches_host_recipe(dev):
