@@ -469,8 +469,12 @@ int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode);
  * posted sector is taken by the next CTA of the running kernel that frees up,
  * so work joins the device while other sectors are being solved.  Capacity
  * slots each hold one task's descriptor, vectors (max_dim elements), a/b
- * history and result; the kernel uses `ctas` CTAs (0: two per SM), leaves
- * after ~0.1 s without work and is launched again by the next post or poll.
+ * history and result.  The kernel runs as up to 8 workers (launches on
+ * streams of the queue) of at most `ctas` CTAs each (0: two per SM): another
+ * starts while the unfinished tasks outnumber the running workers' CTAs, and
+ * a worker leaves ~2 ms after it last found a task to claim (the first one
+ * after ~20 ms), so the solver's width follows the backlog; posts and polls
+ * start them.
  * Each task draws its start vector from its seed exactly as
  * hubbard_fill_start_vector does, stops on rho < tol * max(1, |theta|) (tol 0:
  * 1e-10), breakdown or max_iters (capped at D), and gets err_bound as
@@ -483,7 +487,8 @@ int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode);
 typedef struct hubbard_queue* hubbard_queue_t;
 
 /* Allocates capacity * (24 * max_dim + 16 * max_iters) bytes of device
- * memory (plus the table pools) and a few host-mapped words.  HUB_EINVAL on
+ * memory, 52 MB of table pools (grown when needed) and a few host-mapped
+ * words.  HUB_EINVAL on
  * capacity outside [1, 2^20], max_dim outside [1, 2^31], max_iters < 1,
  * ctas < 0 or tol < 0; HUB_ENOMEM / HUB_ECUDA on allocation failure. */
 int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double tol, int ctas, hubbard_queue_t* out);
@@ -494,6 +499,12 @@ int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double to
  * the slot this post needs (the queue is full: poll, then post again);
  * HUB_EINVAL for a bad sector, more than 127 hops per state or D > max_dim. */
 int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* sector, uint64_t seed, int64_t* ticket);
+
+/* Builds and uploads the hop tables of a sector's two spin species, if not
+ * cached yet, without posting it (a caller can warm the cache from another
+ * thread; the host tables are built without holding the queue's lock).
+ * HUB_EINVAL for a bad sector. */
+int hubbard_queue_prepare(hubbard_queue_t Q, const hubbard_sector_desc* sector);
 
 /* HUB_OK with the result once the task has finished (each result is returned
  * once), HUB_EPENDING before that; HUB_EINVAL for an unknown or already
@@ -518,7 +529,7 @@ void hubbard_queue_destroy(hubbard_queue_t Q);
  *       small lane posts each small request to a queued solver
  *       (hubbard_queue_*) as soon as it arrives: the request joins the
  *       persistent kernel that is already solving the earlier ones, on its
- *       next free CTA (small_ctas CTAs, 0: 32; the rest of the GPU stays
+ *       next free CTA (small_ctas CTAs, 0: 16; the rest of the GPU stays
  *       with the big lanes); the queue's memory (up to 1024 slots of
  *       small_max_dim elements, within a quarter of the budget) is taken
  *       from the budget when the server starts.  With host_solver (or small_ctas < 0), small lanes take every
@@ -564,7 +575,7 @@ typedef struct {
     int32_t max_iters;         /* <= 0: 1000 */
     int32_t batch_max;         /* requests per micro-batch (<= 0: 1024) */
     int32_t store_vectors;     /* binary32 Lanczos vectors kept per refined request (>= 0) */
-    int32_t small_ctas;        /* CTAs of the queued small-sector solver (0: 32; < 0: micro-batches) */
+    int32_t small_ctas;        /* CTAs of the queued small-sector solver (0: 16; < 0: micro-batches) */
     double tol;                /* <= 0: 1e-10 */
     hubbard_host_solver host_solver;
     void* host_ctx;

@@ -101,6 +101,7 @@ SIGNATURES = {
     "hubbard_queue_poll": (ctypes.c_int, [P, I64, P]),
     "hubbard_queue_destroy": (None, [P]),
     "hubbard_queue_collect": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
+    "hubbard_queue_prepare": (ctypes.c_int, [P, P]),
     "hubbard_batch_set_shape_mode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),

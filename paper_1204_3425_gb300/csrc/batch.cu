@@ -17,6 +17,7 @@
 // fast).  Every reduction is summed in a fixed order, so the result of a
 // sector does not depend on which other sectors share the launch.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <map>
@@ -1463,9 +1464,11 @@ int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int*
 // by raising the posted count in host-mapped memory after its descriptor has
 // been copied, a CTA takes task numbers below that count, and writes the
 // result and then the slot's done word (task number + 1) to host-mapped memory.
-// The kernel leaves after ~0.1 s without work (or at destroy) and is launched
-// again when tasks are posted; a task number is only ever taken once posted,
-// so leaving loses none.  Hop tables are cached per (lattice, particle number)
+// The kernel runs as up to 8 workers (launches on the queue's streams), one
+// more started while unfinished tasks outnumber the running workers' CTAs; a
+// worker leaves ~2 ms after the last task was claimed (the first after
+// ~20 ms) or at destroy; a task number is
+// only ever taken once posted, so leaving loses none.  Hop tables are cached per (lattice, particle number)
 // in device pools that grow (between launches) as new ones are needed.
 struct hubbard_queue {
     int device = 0;
@@ -1476,9 +1479,16 @@ struct hubbard_queue {
     int ctas = 0;
     int smem_elems = 0;
     std::mutex mu;
-    cudaStream_t kstream = nullptr;            // the kernel
+    // workers: launches of the task kernel over this queue, each on its own
+    // stream with `ctas` CTAs; another starts while posted tasks outnumber the
+    // CTAs of the running ones, so the solver's width follows the backlog
+    static constexpr int kWorkers = 8;
+    cudaStream_t ks[kWorkers] = {};
+    bool wrun[kWorkers] = {};
+    int wctas[kWorkers] = {};
+    int resident = 0;                          // CTAs of the workers running at the last check
+    std::chrono::steady_clock::time_point checked{};
     cudaStream_t cstream = nullptr;            // uploads and reads
-    bool running = false;
     // device
     hub::SectorDesc* d_sec = nullptr;          // [cap]
     double* d_f = nullptr;                     // [cap * vstride] each
@@ -1556,25 +1566,42 @@ void queue_set_stop(hubbard_queue* Q, unsigned v) {
     std::atomic_thread_fence(std::memory_order_seq_cst);
 }
 
-// lets the running kernel finish every posted task and leave
+bool queue_any_running(const hubbard_queue* Q) {
+    for (int w = 0; w < hubbard_queue::kWorkers; ++w)
+        if (Q->wrun[w]) return true;
+    return false;
+}
+
+// lets the running workers finish every posted task and leave
 int queue_stop_kernel(hubbard_queue* Q) {
-    if (!Q->running) return HUB_OK;
+    if (!queue_any_running(Q)) return HUB_OK;
     queue_set_stop(Q, 1u);
-    const cudaError_t e = cudaStreamSynchronize(Q->kstream);
+    cudaError_t e = cudaSuccess;
+    for (int w = 0; w < hubbard_queue::kWorkers; ++w) {
+        if (!Q->wrun[w]) continue;
+        const cudaError_t ew = cudaStreamSynchronize(Q->ks[w]);
+        if (e == cudaSuccess) e = ew;
+        Q->wrun[w] = false;
+    }
+    Q->resident = 0;
     queue_set_stop(Q, 0u);
-    Q->running = false;
     if (e != cudaSuccess) return cuda_fail(e, "queue kernel");
     return HUB_OK;
 }
 
-// device tables of one spin species (cached per lattice and particle number)
+// device tables of one spin species (cached per lattice and particle number).
+// Called without the queue's lock: the host tables of a new species are built
+// unlocked (milliseconds for the larger ones), then appended under the lock.
 int queue_spin(hubbard_queue* Q, int ns, const std::vector<std::pair<int, int>>& bl, int N,
                hubbard_queue::Cached* out) {
     const auto key = std::make_tuple(ns, bl, N);
-    auto it = Q->cache.find(key);
-    if (it != Q->cache.end()) {
-        *out = it->second;
-        return HUB_OK;
+    {
+        std::lock_guard<std::mutex> lk(Q->mu);
+        auto it = Q->cache.find(key);
+        if (it != Q->cache.end()) {
+            *out = it->second;
+            return HUB_OK;
+        }
     }
     SpinTables T;
     build_spin_tables(ns, N, bl, T);
@@ -1589,6 +1616,14 @@ int queue_spin(hubbard_queue* Q, int ns, const std::vector<std::pair<int, int>>&
         if (rows) {
             be.resize(rb.ent.size());
             for (size_t i = 0; i < rb.ent.size(); ++i) be[i] = (uint16_t)rb.ent[i];
+        }
+    }
+    std::lock_guard<std::mutex> lk(Q->mu);
+    {
+        auto it = Q->cache.find(key);                    // built meanwhile by another caller
+        if (it != Q->cache.end()) {
+            *out = it->second;
+            return HUB_OK;
         }
     }
     // a pool that must grow moves: the kernel leaves first
@@ -1638,8 +1673,8 @@ int queue_spin(hubbard_queue* Q, int ns, const std::vector<std::pair<int, int>>&
 namespace hub {
 namespace {
 
-// launches the task kernel over the queue (the caller holds the lock)
-int queue_launch(hubbard_queue* Q) {
+// launches the task kernel over the queue on worker w (the caller holds the lock)
+int queue_launch(hubbard_queue* Q, int w, int ctas) {
     BatchParams P{};
     P.sec = Q->d_sec;
     P.tasks = nullptr;
@@ -1669,11 +1704,40 @@ int queue_launch(hubbard_queue* Q) {
     P.q_claim = Q->d_claim;
     P.q_done = Q->m_done;
     P.q_cap = Q->cap;
-    P.q_idle = 50000;                      // ~0.1 s of 2-us sleeps without a posted task
-    k_batch_lanczos<<<Q->ctas, kBatchThreads, (size_t)Q->smem_elems * sizeof(int2), Q->kstream>>>(P);
+    // worker 0 waits ~20 ms (2-us sleeps) for the next task, so a new arrival
+    // finds resident CTAs; the others leave after ~2 ms with nothing left to
+    // claim, giving their SMs back to the rest of the device
+    P.q_idle = w == 0 ? 10000 : 1200;
+    k_batch_lanczos<<<ctas, kBatchThreads, (size_t)Q->smem_elems * sizeof(int2), Q->ks[w]>>>(P);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
-    Q->running = true;
+    Q->wrun[w] = true;
+    Q->wctas[w] = ctas;
+    return HUB_OK;
+}
+
+// retires finished workers and starts one more while the tasks not yet
+// finished outnumber the CTAs of the running workers
+int queue_scale(hubbard_queue* Q) {
+    int outstanding = 0;
+    for (int k = 0; k < Q->cap; ++k) outstanding += Q->slot_ticket[(size_t)k] >= 0 ? 1 : 0;
+    // the workers' streams are queried only when more CTAs may be needed or
+    // every 2 ms (each query is a driver call the other lanes' launches wait on)
+    const auto now = std::chrono::steady_clock::now();
+    if (outstanding <= Q->resident && now - Q->checked < std::chrono::milliseconds(2)) return HUB_OK;
+    Q->checked = now;
+    int resident = 0, free_w = -1;
+    for (int w = 0; w < hubbard_queue::kWorkers; ++w) {
+        if (Q->wrun[w] && cudaStreamQuery(Q->ks[w]) == cudaSuccess) Q->wrun[w] = false;
+        if (Q->wrun[w]) resident += Q->wctas[w];
+        else if (free_w < 0) free_w = w;
+    }
+    Q->resident = resident;
+    if (outstanding > resident && free_w >= 0) {
+        const int c = std::min(Q->ctas, outstanding - resident);
+        Q->resident += c;
+        return queue_launch(Q, free_w, c);
+    }
     return HUB_OK;
 }
 
@@ -1713,19 +1777,14 @@ int queue_harvest(hubbard_queue* Q) {
             Q->slot_ticket[(size_t)k] = -1;
         }
     }
-    if (Q->running && cudaStreamQuery(Q->kstream) == cudaSuccess) Q->running = false;
-    if (!Q->running) {
-        bool pending = false;
-        for (int k = 0; k < Q->cap && !pending; ++k) pending = Q->slot_ticket[(size_t)k] >= 0;
-        if (pending) return queue_launch(Q);
-    }
-    return HUB_OK;
+    return queue_scale(Q);
 }
 
 void queue_free(hubbard_queue* Q) {
-    if (Q->h_ctl != nullptr && Q->running) {
+    if (Q->h_ctl != nullptr && queue_any_running(Q)) {
         queue_set_stop(Q, 1u);
-        cudaStreamSynchronize(Q->kstream);
+        for (int w = 0; w < hubbard_queue::kWorkers; ++w)
+            if (Q->wrun[w]) cudaStreamSynchronize(Q->ks[w]);
     }
     if (Q->cstream) cudaStreamSynchronize(Q->cstream);
     cudaFree(Q->d_sec);
@@ -1744,7 +1803,8 @@ void queue_free(hubbard_queue* Q) {
     if (Q->h_ctl) cudaFreeHost(Q->h_ctl);
     if (Q->h_done) cudaFreeHost(Q->h_done);
     if (Q->h_res) cudaFreeHost(Q->h_res);
-    if (Q->kstream) cudaStreamDestroy(Q->kstream);
+    for (int w = 0; w < hubbard_queue::kWorkers; ++w)
+        if (Q->ks[w]) cudaStreamDestroy(Q->ks[w]);
     if (Q->cstream) cudaStreamDestroy(Q->cstream);
     delete Q;
 }
@@ -1778,8 +1838,9 @@ int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double to
     Q->slot_ticket.assign((size_t)capacity, -1);
     Q->slot_hops1.assign((size_t)capacity, 1);
     const size_t nv = (size_t)capacity * (size_t)Q->vstride;
-    cudaError_t e = cudaStreamCreateWithFlags(&Q->kstream, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&Q->cstream, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithFlags(&Q->cstream, cudaStreamNonBlocking);
+    for (int w = 0; w < hubbard_queue::kWorkers && e == cudaSuccess; ++w)
+        e = cudaStreamCreateWithFlags(&Q->ks[w], cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_sec, (size_t)capacity * sizeof(SectorDesc));
     if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_f, nv * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc((void**)&Q->d_g, nv * sizeof(double));
@@ -1798,6 +1859,26 @@ int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double to
     if (e != cudaSuccess) {
         queue_free(Q);
         return cuda_fail(e, "queue allocation");
+    }
+    // table pools sized for a few hundred small sectors' tables, so that
+    // growing one (which waits for the running tasks) stays rare
+    {
+        Q->c_rp = (size_t)1 << 20;
+        Q->c_ent = (size_t)8 << 20;
+        Q->c_st = (size_t)1 << 20;
+        Q->c_bo = (size_t)1 << 18;
+        Q->c_bc = (size_t)1 << 18;
+        Q->c_be = (size_t)4 << 20;
+        cudaError_t e2 = cudaMalloc((void**)&Q->d_rp, Q->c_rp * sizeof(int32_t));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&Q->d_ent, Q->c_ent * sizeof(uint32_t));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&Q->d_st, Q->c_st * sizeof(uint32_t));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&Q->d_bo, Q->c_bo * sizeof(int64_t));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&Q->d_bc, Q->c_bc * sizeof(int32_t));
+        if (e2 == cudaSuccess) e2 = cudaMalloc((void**)&Q->d_be, Q->c_be * sizeof(uint16_t));
+        if (e2 != cudaSuccess) {
+            queue_free(Q);
+            return cuda_fail(e2, "queue table pools");
+        }
     }
     std::memset(Q->h_ctl, 0, 256);
     std::memset(Q->h_done, 0, (size_t)capacity * sizeof(unsigned int));
@@ -1824,13 +1905,13 @@ int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* d, uint64_t
                 return fail(HUB_EINVAL, "queue: duplicate bond");
         bl.emplace_back(x, y);
     }
-    std::lock_guard<std::mutex> lk(Q->mu);
     int rc;
+    hubbard_queue::Cached cu{}, cd{};
+    if ((rc = queue_spin(Q, d->ns, bl, d->nup, &cu)) || (rc = queue_spin(Q, d->ns, bl, d->ndn, &cd))) return rc;
+    std::lock_guard<std::mutex> lk(Q->mu);
     if ((rc = queue_harvest(Q))) return rc;
     const int k = (int)(Q->posted % (uint64_t)Q->cap);
     if (Q->slot_ticket[(size_t)k] >= 0) return HUB_EPENDING;     // full: the oldest task's slot is still in use
-    hubbard_queue::Cached cu{}, cd{};
-    if ((rc = queue_spin(Q, d->ns, bl, d->nup, &cu)) || (rc = queue_spin(Q, d->ns, bl, d->ndn, &cd))) return rc;
     if (cu.W + cd.W > 127) return fail(HUB_EINVAL, "queue: more than 127 hops per state");
     if (cu.D * cd.D > Q->max_dim) return fail(HUB_EINVAL, "queue: sector above the queue's max_dim");
     SectorDesc s{};
@@ -1860,7 +1941,25 @@ int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* d, uint64_t
     std::atomic_thread_fence(std::memory_order_seq_cst);
     *ticket = (int64_t)Q->posted;
     ++Q->posted;
-    if (!Q->running) return queue_launch(Q);
+    return queue_scale(Q);
+}
+
+int hubbard_queue_prepare(hubbard_queue_t Q, const hubbard_sector_desc* d) {
+    using namespace hub;
+    clear_error();
+    if (Q == nullptr || d == nullptr) return fail(HUB_EINVAL, "null argument");
+    if (d->ns < 1 || d->ns > 32 || d->nup < 0 || d->nup > d->ns || d->ndn < 0 || d->ndn > d->ns || d->n_bonds < 0 ||
+        (d->n_bonds > 0 && d->bonds == nullptr))
+        return fail(HUB_EINVAL, "queue: invalid sector");
+    std::vector<std::pair<int, int>> bl;
+    for (int b = 0; b < d->n_bonds; ++b) {
+        const int x = d->bonds[2 * b], y = d->bonds[2 * b + 1];
+        if (x < 0 || x >= d->ns || y < 0 || y >= d->ns || x == y) return fail(HUB_EINVAL, "queue: bad bond");
+        bl.emplace_back(x, y);
+    }
+    hubbard_queue::Cached cu{}, cd{};
+    int rc;
+    if ((rc = queue_spin(Q, d->ns, bl, d->nup, &cu)) || (rc = queue_spin(Q, d->ns, bl, d->ndn, &cd))) return rc;
     return HUB_OK;
 }
 
@@ -1876,7 +1975,9 @@ int hubbard_queue_poll(hubbard_queue_t Q, int64_t ticket, lanczos_result* out) {
     if (it == Q->finished.end()) {
         if (Q->slot_ticket[(size_t)(ticket % Q->cap)] != ticket) return fail(HUB_EINVAL, "ticket already collected");
         int err = 0;
-        if (!Q->running && cudaMemcpy(&err, Q->d_err, sizeof err, cudaMemcpyDeviceToHost) == cudaSuccess && err != 0)
+        if (!queue_any_running(Q) &&
+            cudaMemcpyAsync(&err, Q->d_err, sizeof err, cudaMemcpyDeviceToHost, Q->cstream) == cudaSuccess &&
+            cudaStreamSynchronize(Q->cstream) == cudaSuccess && err != 0)
             return fail(err, "queue kernel reported an error");
         return HUB_EPENDING;
     }

@@ -74,6 +74,9 @@ struct hubbard_server {
     bool stop = false;
     bool queued_small = false;                 // small requests go to a queued persistent solver
     int queue_cap = 0;                         // its slots
+    bool queue_ready = false;                  // its lane has warmed the solver up
+    hubbard_queue_t queue = nullptr;
+    std::deque<Req*> prep_q;                   // small requests whose hop tables are being made
     std::vector<std::thread> threads;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -264,14 +267,32 @@ void small_lane(hubbard_server* S) {
 // are being posted); finished results are collected and answered.
 void queue_lane(hubbard_server* S) {
     cudaSetDevice(S->device);
-    hubbard_queue_t Q = nullptr;
-    const int qrc = hubbard_queue_create(S->queue_cap, std::max<int64_t>(S->opts.small_max_dim, 1), S->opts.max_iters,
-                                         S->opts.tol, S->opts.small_ctas > 0 ? S->opts.small_ctas : 32, &Q);
+    hubbard_queue_t Q = S->queue;
+    const int qrc = Q != nullptr ? HUB_OK : HUB_ECUDA;
     std::deque<Req*> local;                                   // taken, not yet posted (queue full)
     std::unordered_map<int64_t, Req*> inflight;
     const int kCollect = 256;
     std::vector<int64_t> tks(kCollect);
     std::vector<lanczos_result> rs(kCollect);
+    // warm-up: one two-site sector through the solver, so the first requests
+    // do not pay for the first launch (create waits for this)
+    if (qrc == HUB_OK) {
+        const int32_t dimer[2] = {0, 1};
+        const hubbard_sector_desc d{2, 1, 1, 1, dimer, 1.0, 0.0};
+        int64_t tk = -1;
+        if (hubbard_queue_post(Q, &d, 1, &tk) == HUB_OK) {
+            const auto end = Clock::now() + std::chrono::seconds(10);
+            int n = 0;
+            while (Clock::now() < end && hubbard_queue_collect(Q, tks.data(), rs.data(), kCollect, &n) == HUB_OK &&
+                   n == 0)
+                std::this_thread::sleep_for(std::chrono::microseconds(200));
+        }
+    }
+    {
+        std::lock_guard<std::mutex> lk(S->mu);
+        S->queue_ready = true;
+    }
+    S->cv_done.notify_all();
     while (true) {
         {
             std::unique_lock<std::mutex> lk(S->mu);
@@ -291,6 +312,25 @@ void queue_lane(hubbard_server* S) {
             }
             if (taken) S->st.batches += 1;
         }
+        bool progress = false;
+        // answers whatever has finished (after every post too: a post that builds a
+        // new lattice's tables takes milliseconds, and results should not wait on it)
+        auto collect = [&] {
+            if (Q == nullptr || inflight.empty()) return;
+            int n = 0;
+            const int rc = hubbard_queue_collect(Q, tks.data(), rs.data(), kCollect, &n);
+            if (rc != HUB_OK) {
+                for (auto& kv : inflight) finish(S, kv.second, lanczos_result{}, rc);
+                inflight.clear();
+            }
+            for (int i = 0; i < n; ++i) {
+                auto it = inflight.find(tks[(size_t)i]);
+                if (it == inflight.end()) continue;
+                finish(S, it->second, rs[(size_t)i], rs[(size_t)i].status);
+                inflight.erase(it);
+                progress = true;
+            }
+        };
         while (!local.empty()) {
             Req* r = local.front();
             if (qrc != HUB_OK) {
@@ -306,30 +346,40 @@ void queue_lane(hubbard_server* S) {
             local.pop_front();
             if (rc != HUB_OK) finish(S, r, lanczos_result{}, rc);
             else inflight.emplace(tk, r);
+            collect();
         }
-        bool progress = false;
-        if (Q != nullptr && !inflight.empty()) {
-            int n = 0;
-            const int rc = hubbard_queue_collect(Q, tks.data(), rs.data(), kCollect, &n);
-            if (rc != HUB_OK) {
-                for (auto& kv : inflight) finish(S, kv.second, lanczos_result{}, rc);
-                inflight.clear();
-            }
-            for (int i = 0; i < n; ++i) {
-                auto it = inflight.find(tks[(size_t)i]);
-                if (it == inflight.end()) continue;
-                finish(S, it->second, rs[(size_t)i], rs[(size_t)i].status);
-                inflight.erase(it);
-                progress = true;
-            }
-        }
+        collect();
         if (!progress && (!inflight.empty() || !local.empty())) {
             std::unique_lock<std::mutex> lk(S->mu);
-            S->cv_work.wait_for(lk, std::chrono::microseconds(200));
+            S->cv_work.wait_for(lk, std::chrono::microseconds(500));
         }
     }
     for (Req* r : local) finish(S, r, lanczos_result{}, HUB_EINVAL);   // taken at stop, never posted
-    hubbard_queue_destroy(Q);
+}
+
+// Small requests on their way to the queued solver: their lattice's hop
+// tables are made here (milliseconds for a new lattice and filling, nothing
+// once cached), so the lane that posts and answers never waits on them.
+void prep_lane(hubbard_server* S) {
+    cudaSetDevice(S->device);
+    while (true) {
+        Req* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lk(S->mu);
+            S->cv_work.wait(lk, [&] { return S->stop || !S->prep_q.empty(); });
+            if (S->stop) break;
+            r = S->prep_q.front();
+            S->prep_q.pop_front();
+        }
+        const hubbard_request& q = r->desc;
+        const hubbard_sector_desc d{q.ns, q.nup, q.ndn, q.n_bonds, q.bonds, q.t, q.U};
+        hubbard_queue_prepare(S->queue, &d);          // a failure shows again when the request is posted
+        {
+            std::lock_guard<std::mutex> lk(S->mu);
+            S->small_q.push_back(r);
+        }
+        S->cv_work.notify_all();
+    }
 }
 
 void big_lane(hubbard_server* S) {
@@ -444,8 +494,11 @@ int hubbard_server_create(const hubbard_server_opts* opts, hubbard_server_t* out
         const size_t pools = (size_t)64 << 20;
         const size_t room = S->budget / 4 > pools ? S->budget / 4 - pools : 0;
         S->queue_cap = (int)std::min<size_t>(1024, room / per);
-        if (S->queue_cap < 1) {
-            S->queued_small = false;
+        if (S->queue_cap < 1 ||
+            hubbard_queue_create(S->queue_cap, o.small_max_dim, o.max_iters, o.tol, o.small_ctas > 0 ? o.small_ctas : 16,
+                                 &S->queue) != HUB_OK) {
+            S->queued_small = false;                  // micro-batches instead
+            S->queue = nullptr;
         } else {
             S->free_bytes -= (size_t)S->queue_cap * per + pools;
             S->peak = S->budget - S->free_bytes;
@@ -453,7 +506,10 @@ int hubbard_server_create(const hubbard_server_opts* opts, hubbard_server_t* out
     }
     S->t0 = Clock::now();
     try {
-        if (S->queued_small) S->threads.emplace_back(queue_lane, S);
+        if (S->queued_small) {
+            S->threads.emplace_back(queue_lane, S);
+            S->threads.emplace_back(prep_lane, S);
+        }
         else
             for (int i = 0; i < o.small_lanes; ++i) S->threads.emplace_back(small_lane, S);
         for (int i = 0; i < o.big_lanes; ++i) S->threads.emplace_back(big_lane, S);
@@ -464,8 +520,13 @@ int hubbard_server_create(const hubbard_server_opts* opts, hubbard_server_t* out
         }
         S->cv_work.notify_all();
         for (auto& th : S->threads) th.join();
+        hubbard_queue_destroy(S->queue);
         delete S;
         return fail(HUB_ENOMEM, "server: threads");
+    }
+    if (S->queued_small) {
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->cv_done.wait_for(lk, std::chrono::seconds(30), [&] { return S->queue_ready; });
     }
     *out = S;
     return HUB_OK;
@@ -496,11 +557,12 @@ int hubbard_server_submit(hubbard_server_t S, const hubbard_request* req, uint64
         return fail(HUB_EINVAL, "no lane serves this request size");
     r->ticket = S->next_ticket++;
     r->out.t_submit = S->now();
-    (r->path == kPathBatch ? S->small_q : S->big_q).push_back(r.get());
+    (r->path == kPathBatch ? (S->queued_small ? S->prep_q : S->small_q) : S->big_q).push_back(r.get());
     *ticket = r->ticket;
     S->reqs.emplace(r->ticket, std::move(r));
     S->st.submitted += 1;
-    S->st.max_backlog = std::max<int64_t>(S->st.max_backlog, (int64_t)(S->small_q.size() + S->big_q.size()));
+    S->st.max_backlog =
+        std::max<int64_t>(S->st.max_backlog, (int64_t)(S->prep_q.size() + S->small_q.size() + S->big_q.size()));
     S->cv_work.notify_all();
     return HUB_OK;
 }
@@ -540,7 +602,7 @@ int hubbard_server_stats_get(hubbard_server_t S, hubbard_server_stats* out) {
     if (S == nullptr || out == nullptr) return fail(HUB_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(S->mu);
     *out = S->st;
-    out->queued = (int64_t)(S->small_q.size() + S->big_q.size());
+    out->queued = (int64_t)(S->prep_q.size() + S->small_q.size() + S->big_q.size());
     out->peak_bytes = (double)S->peak;
     out->free_bytes = (double)S->free_bytes;
     return HUB_OK;
@@ -554,6 +616,7 @@ void hubbard_server_destroy(hubbard_server_t S) {
     }
     S->cv_work.notify_all();
     for (auto& th : S->threads) th.join();      // running requests finish first
+    hubbard_queue_destroy(S->queue);
     delete S;
 }
 

@@ -43,15 +43,17 @@ class Request:
 class SolveServer:
     """hbm_budget: bytes of device memory for requests (0: 80 % of the free
     memory); n_slots: big lanes (binary64 / refined solves in flight);
-    small_lanes: concurrent micro-batches; solver (tests without a GPU): a
+    small_lanes: lanes of the small queue (with a GPU one lane posts to the
+    queued solver of small_ctas CTAs, 0: 16; small_ctas < 0 or a host solver:
+    concurrent micro-batches); solver (tests without a GPU): a
     callable (ticket, request_dict, path) -> result dict run by the lanes
     instead of the CUDA solvers."""
 
     def __init__(self, hbm_budget=0.0, n_slots=8, small_lanes=2, small_max_dim=20_000, mid_max_dim=200_000,
-                 batch_max=1024, store_vectors=128, max_iters=1000, tol=1e-10, solver=None):
+                 batch_max=1024, store_vectors=128, max_iters=1000, tol=1e-10, solver=None, small_ctas=0):
         from paper_1204_3425_gb300 import Server
         self.srv = Server(hbm_budget, small_lanes, n_slots, small_max_dim, mid_max_dim, max_iters, batch_max,
-                          store_vectors, tol, host_solver=solver)
+                          store_vectors, tol, host_solver=solver, small_ctas=small_ctas)
         self.small_max_dim, self.mid_max_dim, self.n_slots, self.small_lanes = (small_max_dim, mid_max_dim, n_slots,
                                                                                small_lanes)
 
