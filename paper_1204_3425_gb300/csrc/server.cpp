@@ -6,10 +6,12 @@
 // hubbard_server_poll / hubbard_server_wait.  The paper motivates the design
 // (Sec. 5): a small sector alone leaves most of the GPU idle, so work from
 // many requests has to share the device.
-//   * small lanes: every small request waiting when the lane frees up joins
-//     one launch of the batched persistent solver (hubbard_batch_*; a task-only
-//     batch occupies just one CTA per sector, leaving the rest of the GPU to
-//     the other lanes);
+//   * small requests: with a GPU, a prep lane makes their hop tables and one
+//     lane posts them, as they arrive, to a queued persistent solver
+//     (hubbard_queue_*) whose CTAs take each new sector while they run, and
+//     answers what it finishes; without one (host solver) or with
+//     small_ctas < 0, every small request waiting when a small lane frees up
+//     joins one task-only launch of the batched solver (hubbard_batch_*);
 //   * big lanes: one request each, on the lane's own stream -- mid-sized
 //     sectors by the binary64 Lanczos (device-resident steps), larger ones by
 //     the binary32 Lanczos with binary64 refinement, keeping binary32 Lanczos
