@@ -497,7 +497,8 @@ int hubbard_queue_create(int capacity, int64_t max_dim, int max_iters, double to
  * the seed of its start vector; *ticket numbers the posts from 0.  Returns
  * HUB_EPENDING without posting when the oldest unfinished task still holds
  * the slot this post needs (the queue is full: poll, then post again);
- * HUB_EINVAL for a bad sector, more than 127 hops per state or D > max_dim. */
+ * HUB_EINVAL for a bad sector, more than 127 hops per state or D > max_dim;
+ * HUB_ENOMEM after 2^31 - 1 posts to one queue. */
 int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* sector, uint64_t seed, int64_t* ticket);
 
 /* Builds and uploads the hop tables of a sector's two spin species, if not

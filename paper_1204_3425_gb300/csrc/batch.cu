@@ -1909,6 +1909,7 @@ int hubbard_queue_post(hubbard_queue_t Q, const hubbard_sector_desc* d, uint64_t
     hubbard_queue::Cached cu{}, cd{};
     if ((rc = queue_spin(Q, d->ns, bl, d->nup, &cu)) || (rc = queue_spin(Q, d->ns, bl, d->ndn, &cd))) return rc;
     std::lock_guard<std::mutex> lk(Q->mu);
+    if (Q->posted >= 0x7FFFFFFFull) return fail(HUB_ENOMEM, "queue: 2^31 - 1 posts made");   // task numbers are 31-bit
     if ((rc = queue_harvest(Q))) return rc;
     const int k = (int)(Q->posted % (uint64_t)Q->cap);
     if (Q->slot_ticket[(size_t)k] >= 0) return HUB_EPENDING;     // full: the oldest task's slot is still in use
