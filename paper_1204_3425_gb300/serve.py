@@ -92,12 +92,18 @@ class SolveServer:
                 key = f'{r.path}:{r.result["status"]}'
                 failures[key] = failures.get(key, 0) + 1
         verified = [r for r in ok if r.result["err_bound"] <= 1e-9 * max(1.0, abs(r.result["energy"]))]
+        by_path = {}
+        for pth in sorted({r.path for r in requests}):
+            lp = np.array([r.t_done - r.t_submit for r in requests if r.path == pth])
+            by_path[pth] = dict(requests=int(lp.size), p50_ms=1e3 * float(np.percentile(lp, 50)),
+                                p99_ms=1e3 * float(np.percentile(lp, 99)))
         nat = self.srv.stats()
         return dict(requests=len(requests), wall_s=wall, solves_per_s=len(ok) / wall,
                     verified_solves_per_s=len(verified) / wall, verified=len(verified), failed=len(requests) - len(ok),
                     failures=failures,
                     p50_ms=1e3 * float(np.percentile(lat, 50)), p99_ms=1e3 * float(np.percentile(lat, 99)),
-                    max_ms=1e3 * float(lat.max()), max_backlog=nat["max_backlog"], peak_bytes=nat["peak_bytes"],
+                    max_ms=1e3 * float(lat.max()), latency_by_path=by_path, max_backlog=nat["max_backlog"],
+                    peak_bytes=nat["peak_bytes"],
                     budget_bytes=nat["budget_bytes"], n_batches=nat["batches"],
                     mean_batch=(nat["batched_requests"] / nat["batches"]) if nat["batches"] else 0.0,
                     binary64=nat["binary64_solves"], refined=nat["refined_solves"], big_lanes=self.n_slots,
