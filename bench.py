@@ -527,7 +527,7 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune
     ws = torch.empty(B.workspace_bytes(max_iters), dtype=torch.uint8, device=dev)
     t0 = time.perf_counter()
     if autotune:
-        chosen = B.autotune(v0, 40, tol, ws)        # short solves (40 steps) rank the schedules
+        chosen = B.autotune(v0, max_iters, tol, ws)  # full solves rank the schedules
     else:
         chosen = 16384                              # the library's default threshold
         B.set_schedule(chosen)
@@ -550,6 +550,7 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune
     ms = ev[0].elapsed_time(ev[1])
     res = B.results(ws, max_iters, stream=stream)
     table = B.schedule_table()
+    _, task_ctas = B.get_schedule()
     B.close()
     mode_name = {3: "smem", 2: "rows-staged", 0: "rows-L2"}
     by = {}
@@ -564,7 +565,7 @@ def bench_batch(hub, torch, dev, count=2048, max_iters=1000, tol=1e-10, autotune
     ok = sum(1 for r in res if r["status"] == 0)
     return dict(sectors=count, ms=ms, solves_per_s=ok / (ms * 1e-3), converged=ok, elems_per_cta=chosen,
                 autotune_s=tune_s, create_s=create_s, iters_total=sum(r["iters"] for r in res),
-                schedule_table=schedule_table,
+                schedule_table=schedule_table, task_ctas=task_ctas,
                 launches_per_batch=1, timed="CUDA graph replay", tol="rho < 1e-10 max(1,|theta|)",
                 _energies=[r["energy"] if r["status"] == 0 else None for r in res])
 

@@ -436,7 +436,9 @@ int hubbard_selftest_wait_timeout(void* stream);
  * the L2 copy with or without the row staged in shared memory for the
  * down-hops -- and the fastest (the default unless another is 3 % faster) is
  * kept in the batch's schedule table.  Then full solves for elems_per_cta in
- * {2^12 .. 2^17} pick the sweep/task threshold (written to *chosen).  The
+ * {2^12 .. 2^17} pick the sweep/task threshold (written to *chosen), and
+ * then the number of CTAs that start on the tasks while the rest sweep
+ * (hubbard_batch_set_task_ctas; 0, 16, 32, 48 or 64).  The
  * table persists in the batch and is used by every later solve (including a
  * graph-captured one).  Each sector's arithmetic depends only on its own
  * shape's entry and on whether it is swept, so results stay independent of
@@ -461,6 +463,16 @@ int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int*
  * measured earlier; the next solve uploads the descriptors synchronously.
  * HUB_EINVAL on a null batch or an out-of-range shape or mode. */
 int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode);
+
+/* CTAs (0 by default) that start on the one-CTA tasks at once while the rest
+ * of the grid runs the sweep (the sweep CTAs join the tasks when it ends);
+ * capped at the number of tasks, and at half the grid.  A sector's arithmetic
+ * does not depend on it.  HUB_EINVAL on a null batch or a negative count. */
+int hubbard_batch_set_task_ctas(hubbard_batch_t B, int task_ctas);
+
+/* The batch's current sweep/task threshold and task-CTA count (either
+ * pointer may be NULL).  HUB_EINVAL on a null batch. */
+int hubbard_batch_get_schedule(hubbard_batch_t B, int64_t* elems_per_cta, int* task_ctas);
 
 /* ---------------------------------------------------------------------------
  * Queued solver: the batch kernel's one-CTA task path kept running while

@@ -103,6 +103,8 @@ SIGNATURES = {
     "hubbard_queue_collect": (ctypes.c_int, [P, P, P, ctypes.c_int, P]),
     "hubbard_queue_prepare": (ctypes.c_int, [P, P]),
     "hubbard_batch_set_shape_mode": (ctypes.c_int, [P, ctypes.c_int, ctypes.c_int]),
+    "hubbard_batch_set_task_ctas": (ctypes.c_int, [P, ctypes.c_int]),
+    "hubbard_batch_get_schedule": (ctypes.c_int, [P, P, P]),
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
@@ -460,6 +462,15 @@ class Batch:
                                                      _ptr(workspace), workspace.numel(), _stream(stream),
                                                      ctypes.byref(chosen)))
         return chosen.value
+
+    def get_schedule(self):
+        """(elems_per_cta, task_ctas) currently in use."""
+        e, t = I64(), ctypes.c_int()
+        _check(load_library().hubbard_batch_get_schedule(self.handle, ctypes.byref(e), ctypes.byref(t)))
+        return e.value, t.value
+
+    def set_task_ctas(self, n):
+        _check(load_library().hubbard_batch_set_task_ctas(self.handle, int(n)))
 
     def set_shape_mode(self, shape, mode):
         _check(load_library().hubbard_batch_set_shape_mode(self.handle, int(shape), int(mode)))

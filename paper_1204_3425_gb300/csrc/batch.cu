@@ -82,6 +82,7 @@ struct BatchParams {
     long long spin_limit;  // bounded waits
     // grid-synchronous sweep (sectors above the schedule's size threshold)
     int nswp;
+    int sweep_ctas;        // the first sweep_ctas CTAs run the sweep; the others start on the tasks at once
     const int* swp;        // [nswp] sector ids
     const int64_t* rowoff; // [nswp + 1] prefix sums of their D_up
     const int32_t* rowsec; // [rowoff[nswp]] sweep index k of each row
@@ -232,13 +233,15 @@ __device__ double cta_lowest_eig(const double* a, const double* b, int m, double
     for (int round = 0; round < 12; ++round) {
         if (!(hi - lo > 4e-16 * fmax(fabs(lo), fabs(hi)))) break;
         const double x = lo + (hi - lo) * (double)(tid + 1) / (double)(nt + 1);
-        flags[tid] = d_sturm(a, b, m, x) >= 1;
+        // the first point with a positive count bounds the eigenvalue; taken as the
+        // smallest such thread index (computed counts need not be monotone in x
+        // near an eigenvalue, and the choice must not depend on timing)
+        int* kmin = reinterpret_cast<int*>(sh2);
+        if (tid == 0) *kmin = nt;
         __syncthreads();
-        // counts are monotone in x: the first thread with a positive count bounds the eigenvalue
-        if (flags[tid] && (tid == 0 || !flags[tid - 1])) sh2[0] = (double)tid;
-        if (tid == nt - 1 && !flags[tid]) sh2[0] = (double)nt;
+        if (d_sturm(a, b, m, x) >= 1) atomicMin(kmin, tid);
         __syncthreads();
-        const int k = (int)sh2[0];
+        const int k = *kmin;
         const double nlo = k == 0 ? lo : lo + (hi - lo) * (double)k / (double)(nt + 1);
         const double nhi = k == nt ? hi : lo + (hi - lo) * (double)(k + 1) / (double)(nt + 1);
         lo = nlo;
@@ -390,12 +393,13 @@ __device__ __forceinline__ double warp_sum(double v) {
 __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double* red, int* flag, int* sh_flags,
                                          double* sh_k, int* sh_stop, double* sh_out) {
     unsigned ggen = 0;
+    const int G = P.sweep_ctas;                        // CTAs of the sweep: blockIdx.x < G
     auto gsync = [&]() -> bool {
         ++ggen;
-        return grid_barrier(P.gbar, (int)gridDim.x, ggen, P.spin_limit, P.err, flag);
+        return grid_barrier(P.gbar, G, ggen, P.spin_limit, P.err, flag);
     };
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw_all = (int64_t)gridDim.x * nwarps;
+    const int64_t gw = (int64_t)blockIdx.x * nwarps + warp, nw_all = (int64_t)G * nwarps;
     const int64_t nrows = P.rowoff[P.nswp];
     auto locate = [&](int64_t r) -> int { return __ldg(P.rowsec + r); };   // k: rowoff[k] <= r < rowoff[k + 1]
     if (blockIdx.x == 0 && threadIdx.x == 0) *P.nactive = P.nswp;
@@ -423,7 +427,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         if (lane == 0) P.rowpart[3 * r] = nn;
     }
     if (!gsync()) return false;
-    for (int k = blockIdx.x; k < P.nswp; k += gridDim.x) {
+    for (int k = blockIdx.x; k < P.nswp; k += G) {
         const SectorDesc S = P.sec[P.swp[k]];
         double nn = 0.0;
         for (int64_t u = threadIdx.x; u < S.Dup; u += blockDim.x) nn += __ldcg(P.rowpart + 3 * (P.rowoff[k] + u));
@@ -488,7 +492,7 @@ __device__ __noinline__ bool sweep_solve(const BatchParams& P, int2* xs, double*
         if (!gsync()) return false;
         // R
         if (blockIdx.x == 0 && threadIdx.x == 0) P.claim[1] = 0ull;   // U of this step starts after a barrier
-        for (int k = blockIdx.x; k < P.nswp; k += gridDim.x) {
+        for (int k = blockIdx.x; k < P.nswp; k += G) {
             SweepState st = P.sst[k];
             if (!st.active) continue;
             const int sid = P.swp[k];
@@ -606,7 +610,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) k_batch_lanczos(BatchParams 
     __shared__ double sh_out[2];
     // the larger sectors first, in lock step over the whole grid; then the
     // smaller ones, one CTA each
-    if (P.nswp > 0 && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out)) return;
+    if (P.nswp > 0 && (int)blockIdx.x < P.sweep_ctas && !sweep_solve(P, xs, red, &flag, sh_flags, sh_k, &stop, sh_out))
+        return;
     __shared__ int sh_task;
     const bool queued = P.q_posted != nullptr;
     while (true) {
@@ -840,6 +845,7 @@ struct hubbard_batch {
     uint16_t* d_be = nullptr;
     // schedule
     int64_t elems_per_cta = 1 << 14;
+    int task_ctas = 0;                         // CTAs that start on the one-CTA tasks while the rest sweep
     int* d_tasks = nullptr;
     int ntasks = 0;
     size_t tasks_cap = 0;
@@ -1056,6 +1062,11 @@ int batch_launch(hubbard_batch* B, const double* v0_all, int max_iters, double t
     P.mode_force = mode_force;
     P.spin_limit = 20000000;            // ~2.5 s of 128 ns sleeps per barrier
     P.nswp = sweep ? B->nswp : 0;
+    {
+        const int g = B->nswp == 0 ? 0 : B->grid;
+        P.sweep_ctas = std::max(1, g - std::min(B->task_ctas, std::max(0, B->ntasks)));
+        if (B->task_ctas >= g) P.sweep_ctas = std::max(1, g / 2);
+    }
     P.swp = B->d_swp;
     P.rowoff = B->d_rowoff;
     P.rowsec = B->d_rowsec;
@@ -1418,11 +1429,43 @@ int hubbard_batch_autotune(hubbard_batch_t B, const double* v0_all, int max_iter
             best_e = c;
         }
     }
+    B->elems_per_cta = best_e;
+    // 3. how many CTAs start on the one-CTA tasks while the rest sweep
+    //    (the tasks then overlap the sweep's lightly loaded last steps)
+    int best_t = 0;
+    if (rc == HUB_OK) {
+        float best_t_ms = 1e30f;
+        for (int tcand : {0, 16, 32, 48, 64}) {
+            B->task_ctas = tcand;
+            const float ms =
+                timed([&] { return hubbard_batch_solve_async(B, v0_all, max_iters, tol, workspace, ws_bytes, stream); });
+            if (rc != HUB_OK) break;
+            if (ms < best_t_ms) {
+                best_t_ms = ms;
+                best_t = tcand;
+            }
+        }
+    }
+    B->task_ctas = best_t;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    B->elems_per_cta = best_e;
     if (chosen) *chosen = best_e;
     return rc;
+}
+
+int hubbard_batch_get_schedule(hubbard_batch_t B, int64_t* elems_per_cta, int* task_ctas) {
+    clear_error();
+    if (B == nullptr) return fail(HUB_EINVAL, "null batch");
+    if (elems_per_cta) *elems_per_cta = B->elems_per_cta;
+    if (task_ctas) *task_ctas = B->task_ctas;
+    return HUB_OK;
+}
+
+int hubbard_batch_set_task_ctas(hubbard_batch_t B, int task_ctas) {
+    clear_error();
+    if (B == nullptr || task_ctas < 0) return fail(HUB_EINVAL, "bad task CTA count");
+    B->task_ctas = task_ctas;
+    return HUB_OK;
 }
 
 int hubbard_batch_set_shape_mode(hubbard_batch_t B, int shape, int mode) {
