@@ -1509,10 +1509,10 @@ int hubbard_batch_schedule_table(hubbard_batch_t B, int64_t* rows, int cap, int*
 // result and then the slot's done word (task number + 1) to host-mapped memory.
 // The kernel runs as up to 8 workers (launches on the queue's streams), one
 // more started while unfinished tasks outnumber the running workers' CTAs; a
-// worker leaves ~2 ms after the last task was claimed (the first after
-// ~20 ms) or at destroy; a task number is
-// only ever taken once posted, so leaving loses none.  Hop tables are cached per (lattice, particle number)
-// in device pools that grow (between launches) as new ones are needed.
+// worker leaves ~2 ms after it last claimed a task (the first after ~20 ms)
+// or at destroy; a task number is only ever taken once posted, so leaving
+// loses none.  Hop tables are cached per (lattice, particle number) in device
+// pools that grow (with the workers stopped) as new ones are needed.
 struct hubbard_queue {
     int device = 0;
     int cap = 0;
