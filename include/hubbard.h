@@ -77,7 +77,8 @@ typedef enum { HUB_F64 = 0, HUB_F32 = 1 } hub_dtype;
  *   Nup,Ndn 0..Ns electrons of each spin
  *   t, U    finite hopping amplitude and on-site interaction of Eq. (1)
  *   out     receives the handle (NULL on failure)
- * Errors: HUB_EINVAL for any violated rule above or D_sigma > 2^30;
+ * Errors: HUB_EINVAL for any violated rule above or D_sigma > 2^30 (never
+ * binding: with Ns <= 32, D_sigma <= C(32, 16) = 601080390 < 2^30);
  *         HUB_ENOMEM / HUB_ECUDA on allocation or copy failure.
  * The handle is tied to the device that was current at creation; every later
  * call must run with that device current.  Not thread-safe per handle.
