@@ -17,4 +17,8 @@ Modules
   closed_forms dimer, t = 0 and U = 0 ground-state energies.
   kron         plain-C Kronecker-sum H*v (Eq. H-Kroneckersum, the CPU
                scheme of Sec. 5) for sectors too large for explicit H.
+  propagate    exp(-iHt) v (the time propagation Sec. 6 names as the other
+               use of H*v) by the eigendecomposition of the dense H, by
+               expm_multiply on the sparse H, and the closed forms and
+               series that pin them.
 """
