@@ -369,6 +369,66 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
                                  size_t ws_bytes, void* psi_out, void* stream, lanczos_refined_result* out);
 
 /* ---------------------------------------------------------------------------
+ * Time propagation psi(t) = exp(-i H t) v (the other use of the H*v kernel
+ * the paper names, Sec. 6; the paper gives no scheme).  Short iterative
+ * Lanczos: from a real start p the Lanczos vectors f_j of Algorithm 1 (the
+ * binary64 H*v and step kernels of lanczos_ground_state) give
+ *   exp(-i H tau) p ~ |p| sum_{j<m} y_j f_j,   y = exp(-i T_m tau) e_1,
+ * with T_m the Lanczos tridiagonal (Eq. Tmatrix; its eigendecomposition by
+ * implicit-shift QR on the host) and the a-posteriori error estimate
+ *   est(tau) = |p| b_{m+1} |y_{m-1}|.
+ * A complex v = v_re + i v_im is propagated as its two real parts (H is real).
+ * Steps: the Lanczos run of each real part stops once est(remaining time) is
+ * within its share of tol * |v| * remaining / |t| (checked every 4 steps), or
+ * at krylov_max steps; then the step tau is the longest that meets that
+ * budget for both parts (bisection), the state becomes exp(-i H tau) v, and
+ * the loop repeats until |t| is used up.  The summed estimates are therefore
+ * about tol * |v|; the estimate is not a proven bound.
+ *   v_re, v_im  binary64 device vectors of D elements (v_im may be NULL: a
+ *               real v), 16-byte aligned, not inside the workspace
+ *   t           propagation time (any sign; 0 copies v)
+ *   krylov_max  1 .. 1024: Lanczos steps per propagation step at most
+ *   tol         > 0: relative accuracy target, see above
+ *   workspace   >= hubbard_evolve_workspace_bytes(H, krylov_max, 0) bytes
+ *               (6 vectors: two Lanczos vectors, the H*v scratch, the current
+ *               state), 256-aligned.  With hubbard_evolve_workspace_bytes(H,
+ *               krylov_max, 1) bytes the Lanczos vectors of both real parts
+ *               are stored and combined in one pass; with less, each part's
+ *               recurrence is replayed to combine them (twice the H*v count,
+ *               bit-identical result)
+ *   out_re, out_im  binary64 device vectors receiving psi(t), 16-byte
+ *               aligned, disjoint from each other and the workspace; they may
+ *               alias v_re / v_im (v is copied into the workspace first)
+ *   info        steps taken, H*v count, largest Krylov dimension, summed
+ *               error estimates, |psi(t)|, status
+ * Errors: HUB_EINVAL (arguments, non-finite t or tol, more than 127 hops per
+ * state), HUB_ENOMEM (workspace too small), HUB_ENOTCONV (the tridiagonal QR
+ * did not converge, or a step would have to be shorter than 1e-12 |t|:
+ * tol too strict for krylov_max), HUB_ECUDA.  Synchronises stream.
+ * ------------------------------------------------------------------------- */
+typedef struct {
+    int32_t steps;             /* propagation steps (Krylov restarts + 1) */
+    int32_t hv;                /* H*v applications, replays included */
+    int32_t krylov_dim;        /* largest Lanczos run of any step */
+    int32_t status;
+    double err_estimate;       /* sum over steps and parts of est(tau) */
+    double norm;               /* |psi(t)|_2 */
+} hubbard_evolve_info;
+
+size_t hubbard_evolve_workspace_bytes(hubbard_t H, int krylov_max, int store_basis);
+
+int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double t, int krylov_max, double tol,
+                        void* workspace, size_t ws_bytes, void* out_re, void* out_im, void* stream,
+                        hubbard_evolve_info* info);
+
+/* Host-only helper of hubbard_time_evolve, for testing without a GPU:
+ * y = exp(-i T tau) e_1 for the m x m symmetric tridiagonal T with diagonal
+ * a[0..m) and off-diagonal b[0..m-1) (y_re, y_im: m each).  m in 1..4096.
+ * HUB_EINVAL for bad arguments or non-finite inputs, HUB_ENOTCONV if the QR
+ * iteration does not converge. */
+int hubbard_host_krylov_exp(const double* a, const double* b, int m, double tau, double* y_re, double* y_im);
+
+/* ---------------------------------------------------------------------------
  * Many sectors solved in one persistent launch (Algorithm 1 for every
  * sector, entirely on the device; the paper notes that small sectors leave
  * the GPU idle, Sec. 5).  A batch owns the hopping tables of all its sectors

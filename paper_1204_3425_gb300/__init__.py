@@ -108,6 +108,9 @@ SIGNATURES = {
     "hubbard_selftest_wait_timeout": (ctypes.c_int, [P]),
     "hubbard_autotune_schedule": (ctypes.c_int, [P, P, P, ctypes.c_int, P, P]),
     "lanczos_ground_state_refined": (ctypes.c_int, [P, P, ctypes.c_int, D, P, SZ, P, P, P]),
+    "hubbard_evolve_workspace_bytes": (SZ, [P, ctypes.c_int, ctypes.c_int]),
+    "hubbard_time_evolve": (ctypes.c_int, [P, P, P, D, ctypes.c_int, D, P, SZ, P, P, P, P]),
+    "hubbard_host_krylov_exp": (ctypes.c_int, [P, P, ctypes.c_int, D, P, P]),
     "hubbard_server_create": (ctypes.c_int, [P, P]),
     "hubbard_server_submit": (ctypes.c_int, [P, P, P]),
     "hubbard_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, P]),
@@ -406,6 +409,56 @@ def lanczos_ground_state_refined(H, v0, max_iters=1000, tol=1e-10, workspace=Non
     if rc != HUB_OK and not (rc == HUB_ENOTCONV and not raise_on_notconv):
         _check(rc)
     return {f: getattr(res, f) for f, _ in RefinedResult._fields_}
+
+
+class EvolveInfo(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int32), ("hv", ctypes.c_int32), ("krylov_dim", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("err_estimate", ctypes.c_double), ("norm", ctypes.c_double)]
+
+
+def hubbard_evolve_workspace_bytes(H, krylov_max=40, store_basis=True):
+    """Workspace of hubbard_time_evolve: 6 vectors, plus 2 * krylov_max stored
+    Lanczos vectors when store_basis (else the recurrence is replayed)."""
+    return int(load_library().hubbard_evolve_workspace_bytes(H.handle, int(krylov_max), 1 if store_basis else 0))
+
+
+def hubbard_time_evolve(H, v_re, v_im, t, krylov_max=40, tol=1e-10, workspace=None, out_re=None, out_im=None,
+                        store_basis=True, stream=None):
+    """psi(t) = exp(-i H t) (v_re + i v_im) in binary64 (v_im may be None).
+    Returns (out_re, out_im, info dict).  Without a workspace, one is allocated
+    (with room for the Lanczos vectors when store_basis)."""
+    import torch
+    lib = load_library()
+    _vec_pair(H, v_re, v_re, (torch.float64,))
+    if v_im is not None:
+        _vec_pair(H, v_im, v_im, (torch.float64,))
+    if out_re is None:
+        out_re = torch.empty_like(v_re)
+    if out_im is None:
+        out_im = torch.empty_like(v_re)
+    _vec_pair(H, out_re, out_im, (torch.float64,))
+    if workspace is None:
+        workspace = torch.empty(hubbard_evolve_workspace_bytes(H, krylov_max, store_basis), dtype=torch.uint8,
+                                device=v_re.device)
+    info = EvolveInfo()
+    rc = lib.hubbard_time_evolve(H.handle, _ptr(v_re), _ptr(v_im) if v_im is not None else None, float(t),
+                                 int(krylov_max), float(tol), _ptr(workspace),
+                                 workspace.numel() * workspace.element_size(), _ptr(out_re), _ptr(out_im),
+                                 _stream(stream), ctypes.byref(info))
+    _check(rc)
+    return out_re, out_im, {f: getattr(info, f) for f, _ in EvolveInfo._fields_}
+
+
+def hubbard_host_krylov_exp(a, b, tau):
+    """Host helper: y = exp(-i T tau) e_1 for the tridiagonal T (diagonal a, off-diagonal b)."""
+    import numpy as np
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    m = len(a)
+    yr, yi = np.zeros(m), np.zeros(m)
+    _check(load_library().hubbard_host_krylov_exp(a.ctypes.data, b.ctypes.data if len(b) else None, m, float(tau),
+                                                  yr.ctypes.data, yi.ctypes.data))
+    return yr + 1j * yi
 
 
 def hubbard_selftest_wait_timeout(stream=None):

@@ -4,6 +4,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <list>
 #include <map>
 #include <mutex>
@@ -936,11 +937,15 @@ struct LanczosRun {
     bool broke = false, converged = false;
 };
 
+// A caller's own stop test, run after each recorded step (in place of the
+// residual tests, which then need tol = rel_tol = 0); true ends the run.
+using LanczosStop = std::function<bool(const LanczosRun&)>;
+
 // store (optional): f_j is also copied to store + j * store_stride bytes for
 // j < store_cap (the Ritz vector is then one pass over the stored vectors).
 static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype,
                              void* f, void* g, cudaStream_t s, LanczosRun& R, double rel_tol, char* store,
-                             size_t store_stride, int store_cap);
+                             size_t store_stride, int store_cap, const LanczosStop* stop);
 
 // The handle's device-resident Lanczos control block and a/b history for
 // cap steps (grown on demand; freed with the handle).
@@ -958,7 +963,8 @@ static int ensure_lz(hubbard_sector* H, int cap) {
 
 // Records step m-1 (a_m, b_{m+1} appended to R) and applies the run's stop
 // tests in the order of Algorithm 1's loop; returns true when the run ends.
-static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol, double rel_tol) {
+static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol, double rel_tol,
+                                const LanczosStop* stop = nullptr) {
     R.a.push_back(aj);
     double s_last = 1.0;
     tridiag_lowest(R.a.data(), R.b.data(), (int)R.a.size(), &R.theta, &s_last);
@@ -973,6 +979,10 @@ static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol,
         return true;
     }
     if ((tol > 0.0 && R.rho < tol) || (rel_tol > 0.0 && R.rho < rel_tol * std::max(1.0, std::fabs(R.theta)))) {
+        R.converged = true;
+        return true;
+    }
+    if (stop != nullptr && (*stop)(R)) {
         R.converged = true;
         return true;
     }
@@ -999,14 +1009,14 @@ static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol,
 // whose H*v kernels do not fuse the reductions take the host-driven loop.
 static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype, void* f,
                         void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0, char* store = nullptr,
-                        size_t store_stride = 0, int store_cap = 0) {
+                        size_t store_stride = 0, int store_cap = 0, const LanczosStop* stop = nullptr) {
     // steps per chunk: about 4e6 / D (a round trip is worth a few steps of a small sector)
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(4e6 / (double)H->D)));
     // one step per round trip gains nothing over the host-driven loop, whose
     // explicit branch costs no launches when unused (same results either way)
     if (chunk == 1 || !hv_phases_fuse(H, dtype) || H->fx_bytes < (size_t)H->D * 16)
         return lanczos_core_host(H, v0, v0_dtype, max_iters, tol, dtype, f, g, s, R, rel_tol, store, store_stride,
-                                 store_cap);
+                                 store_cap, stop);
     int rc;
     const int m_cap = (int)std::min<int64_t>(max_iters, H->D);
     if ((rc = ensure_lz(H, m_cap))) return rc;
@@ -1108,7 +1118,8 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
                             s) != cudaSuccess)
             return fail(HUB_ECUDA, "Lanczos history download");
         if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
-        for (int q = 0; q < j1 - j0 && !done; ++q) done = lanczos_record_step(R, ab[(size_t)q], ab[(size_t)chunk + q], tol, rel_tol);
+        for (int q = 0; q < j1 - j0 && !done; ++q)
+            done = lanczos_record_step(R, ab[(size_t)q], ab[(size_t)chunk + q], tol, rel_tol, stop);
     }
     if (tol <= 0.0 && rel_tol <= 0.0) R.converged = true;
     if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
@@ -1117,7 +1128,7 @@ static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters
 
 static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype,
                              void* f, void* g, cudaStream_t s, LanczosRun& R, double rel_tol, char* store,
-                             size_t store_stride, int store_cap) {
+                             size_t store_stride, int store_cap, const LanczosStop* stop) {
     int rc;
     double n0 = 0.0;
     if ((rc = launch_dot(H, v0, v0, H->D, v0_dtype, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
@@ -1147,7 +1158,7 @@ static int lanczos_core_host(hubbard_t H, const void* v0, int v0_dtype, int max_
         if (j >= 1 && j < store_cap &&
             cudaMemcpyAsync(store + (size_t)j * store_stride, f, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             return fail(HUB_ECUDA, "store f_j");
-        if (lanczos_record_step(R, aj, bn, tol, rel_tol)) break;
+        if (lanczos_record_step(R, aj, bn, tol, rel_tol, stop)) break;
         if (pending) {
             upd = RowUpdate{f, -aj, 1.0 / bn};
             have_upd = true;
@@ -1424,6 +1435,228 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
     }
     out->status = (out->error_bound <= tol * std::max(1.0, std::fabs(out->energy))) ? HUB_OK : HUB_ENOTCONV;
     if (out->status != HUB_OK) return fail(HUB_ENOTCONV, "refined energy bound above tol");
+    return HUB_OK;
+}
+
+}  // extern "C"
+
+// ---- time propagation (Sec. 6: the other use of H*v; short iterative Lanczos) ----
+
+// A <- A + sum_j ca_j f_j, B <- B + sum_j cb_j f_j over the Lanczos vectors of a
+// finished lanczos_core run from p, by replaying its recurrence as
+// replay_ritz_vector does (same kernels and operands, hence the same f_j bit
+// for bit); the accumulation is the one launch_combine2_f64 does over stored
+// vectors, so both routes give the same A, B.
+static int replay_combine2(hubbard_t H, const void* p, const LanczosRun& R, const std::vector<double>& ca,
+                           const std::vector<double>& cb, double* A, double* B, void* f, void* g, cudaStream_t s) {
+    int rc;
+    const int m = (int)R.a.size();
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, p, p, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+    if ((rc = launch_copy_normalise(p, f, H->D, HUB_F64, 1.0 / std::sqrt(n0), s))) return rc;
+    if (cudaMemsetAsync(g, 0, (size_t)H->D * 8, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    if ((rc = launch_acc2_f64((const double*)f, A, B, H->D, ca[0], cb[0], s))) return rc;
+    RowUpdate ru{};
+    bool have = false;
+    for (int j = 0; j + 1 < m; ++j) {
+        const double bj = j == 0 ? 0.0 : R.b[(size_t)j - 1];
+        if ((rc = launch_hv_fast(H, f, g, HUB_F64, bj, g, 1023, s, nullptr, nullptr, have ? &ru : nullptr))) return rc;
+        if (have && (rc = launch_acc2_f64((const double*)f, A, B, H->D, ca[(size_t)j], cb[(size_t)j], s))) return rc;
+        ru = RowUpdate{f, -R.a[(size_t)j], 1.0 / R.b[(size_t)j]};
+        have = true;
+        std::swap(f, g);
+    }
+    if (have) {
+        if ((rc = launch_axpy_scale(ru.a, ru.inv, ru.fo, f, H->D, HUB_F64, s))) return rc;
+        if ((rc = launch_acc2_f64((const double*)f, A, B, H->D, ca[(size_t)m - 1], cb[(size_t)m - 1], s))) return rc;
+    }
+    return HUB_OK;
+}
+
+static size_t evolve_vec_bytes(hubbard_t H) { return align_up((size_t)H->D * 8, 256); }
+
+extern "C" {
+
+size_t hubbard_evolve_workspace_bytes(hubbard_t H, int krylov_max, int store_basis) {
+    if (H == nullptr || krylov_max < 1 || krylov_max > 1024) return 0;
+    const size_t vec = evolve_vec_bytes(H);
+    const int k = (int)std::min<int64_t>(krylov_max, H->D);
+    return 6 * vec + (store_basis ? 2 * (size_t)k * vec : 0);
+}
+
+int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double t, int krylov_max, double tol,
+                        void* workspace, size_t ws_bytes, void* out_re, void* out_im, void* stream,
+                        hubbard_evolve_info* info) {
+    clear_error();
+    int rc;
+    if ((rc = check_handle(H))) return rc;
+    if (info == nullptr) return fail(HUB_EINVAL, "info is null");
+    std::memset(info, 0, sizeof(*info));
+    info->status = HUB_EINVAL;
+    if (v_re == nullptr || !aligned16(v_re) || (v_im != nullptr && !aligned16(v_im)))
+        return fail(HUB_EINVAL, "v_re null, or v_re / v_im not 16-byte aligned");
+    if (out_re == nullptr || out_im == nullptr || !aligned16(out_re) || !aligned16(out_im))
+        return fail(HUB_EINVAL, "out_re / out_im null or not 16-byte aligned");
+    if (!std::isfinite(t)) return fail(HUB_EINVAL, "t must be finite");
+    if (krylov_max < 1 || krylov_max > 1024) return fail(HUB_EINVAL, "krylov_max must be in 1..1024");
+    if (!(tol > 0.0) || !std::isfinite(tol)) return fail(HUB_EINVAL, "tol must be positive and finite");
+    if (workspace == nullptr || (reinterpret_cast<uintptr_t>(workspace) & 255u))
+        return fail(HUB_EINVAL, "workspace null or not 256-byte aligned");
+    if (!fixed_point_ok(H)) return fail(HUB_EINVAL, "time evolution: more than 127 hops per state is not supported");
+    const size_t vbytes = (size_t)H->D * 8;
+    auto overlap = [&](const void* x, size_t nx, const void* y, size_t ny) {
+        const char* a = (const char*)x;
+        const char* b = (const char*)y;
+        return a < b + ny && b < a + nx;
+    };
+    if (overlap(out_re, vbytes, out_im, vbytes)) return fail(HUB_EINVAL, "out_re and out_im overlap");
+    for (const void* q : {v_re, v_im, (const void*)out_re, (const void*)out_im})
+        if (q != nullptr && overlap(q, vbytes, workspace, ws_bytes)) return fail(HUB_EINVAL, "a vector overlaps the workspace");
+    info->status = HUB_ENOMEM;
+    if (ws_bytes < hubbard_evolve_workspace_bytes(H, krylov_max, 0)) return fail(HUB_ENOMEM, "workspace too small");
+    info->status = HUB_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int kmax = (int)std::min<int64_t>(krylov_max, H->D);
+    const size_t vec = evolve_vec_bytes(H);
+    char* ws = (char*)workspace;
+    void* f = ws;
+    void* g = ws + vec;
+    ScratchGuard guard(H, ws + 2 * vec, (size_t)H->D * 16);
+    double* part[2] = {(double*)(ws + 4 * vec), (double*)(ws + 5 * vec)};   // state: real, imaginary part
+    char* store = ws + 6 * vec;
+    const bool stored = ws_bytes >= hubbard_evolve_workspace_bytes(H, krylov_max, 1);
+    double* A = (double*)out_re;
+    double* B = (double*)out_im;
+
+    if (cudaMemcpyAsync(part[0], v_re, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(HUB_ECUDA, "copy v_re");
+    bool has_im = v_im != nullptr;
+    if (has_im && cudaMemcpyAsync(part[1], v_im, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return fail(HUB_ECUDA, "copy v_im");
+    double nn[2] = {0.0, 0.0};
+    for (int q = 0; q < (has_im ? 2 : 1); ++q)
+        if ((rc = launch_dot(H, part[q], part[q], H->D, HUB_F64, H->red, s)) ||
+            (rc = reduce_partials_host(H->red, s, &nn[q])))
+            return rc;
+    const double nv = std::sqrt(nn[0] + nn[1]);
+    if (!std::isfinite(nv)) return fail(HUB_EINVAL, "v has non-finite elements");
+    if (t == 0.0 || nv == 0.0) {
+        if (cudaMemcpyAsync(A, part[0], vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+            (has_im ? cudaMemcpyAsync(B, part[1], vbytes, cudaMemcpyDeviceToDevice, s)
+                    : cudaMemsetAsync(B, 0, vbytes, s)) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return fail(HUB_ECUDA, "copy v");
+        info->norm = nv;
+        return HUB_OK;
+    }
+    const double tabs = std::fabs(t), sgn = t > 0.0 ? 1.0 : -1.0;
+    double rem = tabs;
+    constexpr int kMaxSteps = 100000;
+    struct Run {
+        int q = 0;
+        double nu = 0.0;
+        LanczosRun R;
+        KrylovEnds E;
+    };
+    while (rem > 0.0) {
+        if (info->steps >= kMaxSteps) return fail(HUB_ENOTCONV, "time evolution: too many steps");
+        // norms of the parts of the current state; each part's share of the budget
+        for (int q = 0; q < 2; ++q) {
+            nn[q] = 0.0;
+            if (q == 1 && !has_im) continue;
+            if ((rc = launch_dot(H, part[q], part[q], H->D, HUB_F64, H->red, s)) ||
+                (rc = reduce_partials_host(H->red, s, &nn[q])))
+                return rc;
+            nn[q] = std::sqrt(nn[q]);
+        }
+        const double nsum = nn[0] + nn[1];
+        std::vector<Run> runs;
+        for (int q = 0; q < 2; ++q) {
+            if (!(nn[q] > 0.0)) continue;
+            Run run;
+            run.q = q;
+            run.nu = nn[q];
+            // budget of this part for a step tau: tol |v| (tau / |t|) (nu / sum of the parts' nu)
+            const double share = tol * nv * (nn[q] / nsum) / tabs;
+            const double target = rem;
+            const LanczosStop stop = [&, share, target](const LanczosRun& Rr) {
+                const int m = (int)Rr.a.size();
+                if (m % 4 != 0 && m < kmax) return false;
+                KrylovEnds E;
+                if (!krylov_exp_ends(Rr.a.data(), Rr.b.data(), m, E)) return false;
+                return run.nu * Rr.b.back() * krylov_last_coeff(E, sgn * target) <= share * target;
+            };
+            char* st = stored ? store + (size_t)q * kmax * vec : nullptr;
+            if ((rc = lanczos_core(H, part[q], HUB_F64, kmax, 0.0, HUB_F64, f, g, s, run.R, 0.0, st, vec,
+                                   stored ? kmax : 0, &stop)))
+                return rc;
+            const int m = (int)run.R.a.size();
+            if (!krylov_exp_ends(run.R.a.data(), run.R.b.data(), m, run.E))
+                return fail(HUB_ENOTCONV, "time evolution: tridiagonal QR did not converge");
+            info->hv += m;
+            info->krylov_dim = std::max(info->krylov_dim, m);
+            runs.push_back(std::move(run));
+        }
+        // the longest step every part's estimate allows
+        double tau = rem;
+        for (const Run& r : runs) {
+            const double share = tol * nv * (r.nu / nsum) / tabs;
+            auto est = [&](double x) { return r.nu * r.R.b.back() * krylov_last_coeff(r.E, sgn * x); };
+            if (est(tau) <= share * tau) continue;
+            double lo = 0.0, hi = tau;
+            for (int it = 0; it < 80; ++it) {
+                const double mid = 0.5 * (lo + hi);
+                if (est(mid) <= share * mid) lo = mid;
+                else hi = mid;
+            }
+            tau = lo;
+        }
+        if (!(tau > 1e-12 * tabs)) return fail(HUB_ENOTCONV, "time evolution: tol too strict for krylov_max");
+        if (tau > rem) tau = rem;
+        // psi(tau) = sum over parts of i^q nu_q sum_j y_j f_j into (A, B)
+        if (cudaMemsetAsync(A, 0, vbytes, s) != cudaSuccess || cudaMemsetAsync(B, 0, vbytes, s) != cudaSuccess)
+            return fail(HUB_ECUDA, "memset");
+        for (const Run& r : runs) {
+            const int m = (int)r.R.a.size();
+            std::vector<double> yre((size_t)m), yim((size_t)m), ca((size_t)m), cb((size_t)m);
+            if (!krylov_exp_coeffs(r.R.a.data(), r.R.b.data(), m, sgn * tau, yre.data(), yim.data()))
+                return fail(HUB_ENOTCONV, "time evolution: tridiagonal QR did not converge");
+            info->err_estimate += r.nu * r.R.b.back() * std::hypot(yre[(size_t)m - 1], yim[(size_t)m - 1]);
+            for (int j = 0; j < m; ++j) {
+                // real part: (re, im) += nu (Re y, Im y) f_j; imaginary part: i nu y f_j = nu (-Im y, Re y) f_j
+                ca[(size_t)j] = r.nu * (r.q == 0 ? yre[(size_t)j] : -yim[(size_t)j]);
+                cb[(size_t)j] = r.nu * (r.q == 0 ? yim[(size_t)j] : yre[(size_t)j]);
+            }
+            if (stored) {
+                std::vector<double> c(2 * (size_t)m);
+                std::copy(ca.begin(), ca.end(), c.begin());
+                std::copy(cb.begin(), cb.end(), c.begin() + m);
+                if (cudaMemcpyAsync(H->red, c.data(), c.size() * sizeof(double), cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess)
+                    return fail(HUB_ECUDA, "upload coefficients");
+                const double* base = (const double*)(store + (size_t)r.q * kmax * vec);
+                if ((rc = launch_combine2_f64(base, (int64_t)(vec / 8), m, H->red, A, B, H->D, s))) return rc;
+            } else {
+                if ((rc = replay_combine2(H, part[r.q], r.R, ca, cb, A, B, f, g, s))) return rc;
+                info->hv += m - 1;
+            }
+        }
+        ++info->steps;
+        rem -= tau;
+        if (rem <= 1e-15 * tabs) rem = 0.0;
+        if (rem > 0.0) {
+            if (cudaMemcpyAsync(part[0], A, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+                cudaMemcpyAsync(part[1], B, vbytes, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                return fail(HUB_ECUDA, "copy state");
+            has_im = true;
+        }
+    }
+    double pr = 0.0, pi = 0.0;
+    if ((rc = launch_dot(H, A, A, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pr)) ||
+        (rc = launch_dot(H, B, B, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &pi)))
+        return rc;
+    info->norm = std::sqrt(pr + pi);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "time evolution synchronise");
     return HUB_OK;
 }
 

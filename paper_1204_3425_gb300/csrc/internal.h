@@ -236,6 +236,30 @@ int launch_psi_accumulate_f64(const double* f, double* psi, int64_t n, double sj
 int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_dev, double* psi, int64_t n,
                      cudaStream_t s);
 
+// A <- A + ca f, B <- B + cb f (binary64)
+int launch_acc2_f64(const double* f, double* A, double* B, int64_t n, double ca, double cb, cudaStream_t s);
+// A <- A + sum_{j<m} c_j f_j, B <- B + sum_{j<m} c_{m+j} f_j, f_j = base + j * stride
+// (binary64), c on the device; bit-identical to m successive launch_acc2_f64 calls
+int launch_combine2_f64(const double* base, int64_t stride, int m, const double* c_dev, double* A, double* B,
+                        int64_t n, cudaStream_t s);
+
+// krylov.cpp ------------------------------------------------------------------
+// Eigenvalues lam[0..m) of the symmetric tridiagonal T (diag a, off-diag
+// b[0..m-2]) by implicit-shift QR, and rows rows[0..zrows) of its eigenvector
+// matrix: Z[r * m + k] = component rows[r] of the eigenvector of lam[k].
+// false if the iteration does not converge.
+bool tridiag_eigen(const double* a, const double* b, int m, double* lam, double* Z, int zrows, const int* rows);
+// eigenvalues and the first and last rows of the eigenvector matrix of T_m,
+// from which |e_m^T exp(-i T_m tau) e_1| is evaluated at any tau in O(m)
+struct KrylovEnds {
+    int m = 0;
+    std::vector<double> lam, z0, zl;
+};
+bool krylov_exp_ends(const double* a, const double* b, int m, KrylovEnds& out);
+double krylov_last_coeff(const KrylovEnds& K, double tau);
+// y = exp(-i T_m tau) e_1 (real and imaginary parts, m each)
+bool krylov_exp_coeffs(const double* a, const double* b, int m, double tau, double* yre, double* yim);
+
 // tridiag.cpp -----------------------------------------------------------------
 // Lowest eigenvalue of the symmetric tridiagonal T (diag a[0..m-1], off-diag
 // b[0..m-2]) and the last component of its normalised eigenvector.

@@ -388,6 +388,34 @@ __global__ void k_psi_multi(const float* __restrict__ base, int64_t stride, int 
     }
 }
 
+// A <- A + ca f, B <- B + cb f (binary64): one Lanczos vector's share of the
+// real and imaginary parts of a Krylov propagation
+__global__ void k_acc2_f64(const double* __restrict__ f, double* __restrict__ A, double* __restrict__ B, int64_t n,
+                           double ca, double cb) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = __ldcs(f + i);
+        A[i] = fma(ca, x, A[i]);
+        B[i] = fma(cb, x, B[i]);
+    }
+}
+
+// A <- A + sum_j c[j] f_j, B <- B + sum_j c[m + j] f_j over m stored binary64
+// vectors f_j = base + j * stride, per element in j order with the operations
+// of m successive k_acc2_f64 launches (so the result is bit-identical to them)
+__global__ void k_combine2_f64(const double* __restrict__ base, int64_t stride, int m, const double* __restrict__ c,
+                               double* __restrict__ A, double* __restrict__ B, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double a = A[i], b = B[i];
+        for (int j = 0; j < m; ++j) {
+            const double x = __ldcs(base + (int64_t)j * stride + i);
+            a = fma(c[j], x, a);
+            b = fma(c[m + j], x, b);
+        }
+        A[i] = a;
+        B[i] = b;
+    }
+}
+
 // Seeded uniform [-1, 1) start vector (splitmix.cuh), elements start .. start + n
 __global__ void k_fill_splitmix(void* v, int64_t n, unsigned long long seed, int64_t start, int dtype) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -628,6 +656,23 @@ int launch_psi_multi(const float* base, int64_t stride, int m, const double* s_d
                      cudaStream_t s) {
     const int g = grid_for(n, kThreads * 8, sm_count() * 8);
     k_psi_multi<<<g, kThreads, 0, s>>>(base, stride, m, s_dev, psi, n);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_acc2_f64(const double* f, double* A, double* B, int64_t n, double ca, double cb, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_acc2_f64<<<g, kThreads, 0, s>>>(f, A, B, n, ca, cb);
+    HUB_CUDA(cudaGetLastError());
+    count_launches(1);
+    return HUB_OK;
+}
+
+int launch_combine2_f64(const double* base, int64_t stride, int m, const double* c_dev, double* A, double* B,
+                        int64_t n, cudaStream_t s) {
+    const int g = grid_for(n, kThreads * 8, sm_count() * 8);
+    k_combine2_f64<<<g, kThreads, 0, s>>>(base, stride, m, c_dev, A, B, n);
     HUB_CUDA(cudaGetLastError());
     count_launches(1);
     return HUB_OK;
