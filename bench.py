@@ -289,6 +289,8 @@ def run_ours(args):
 
     if args.workload == "sq4x4_n8_8_U8_f64":
         extra["hv_sq4x4_f32"] = bench_hv_f32(hub, torch, H, v_host, args.steps, args.warmup)
+        if args.evolve:
+            extra["time_evolve"] = bench_evolve(hub, torch, dev, H, v)
     H.close()
     del v, w, v_pin
     torch.cuda.empty_cache()
@@ -396,6 +398,35 @@ def bench_hv_f32(hub, torch, H, v_host, steps, warmup):
     out["dtype"] = "f32"
     del v, w
     return out
+
+
+def bench_evolve(hub, torch, dev, H, v, t=0.05, krylov_max=30, tol=1e-10, reps=3):
+    """Time propagation exp(-iHt) v of the normalised start vector on the
+    bench sector (binary64, Lanczos vectors stored in the workspace), timed
+    whole (the call synchronises); one untimed warm-up call."""
+    torch.cuda.empty_cache()
+    ws = torch.empty(hub.hubbard_evolve_workspace_bytes(H, krylov_max, True), dtype=torch.uint8, device=dev)
+    ore, oim = torch.empty_like(v), torch.empty_like(v)
+    times, info = [], None
+    for k in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, info = hub.hubbard_time_evolve(H, v, None, t, krylov_max=krylov_max, tol=tol, workspace=ws,
+                                             out_re=ore, out_im=oim)
+        dt = time.perf_counter() - t0
+        if k > 0:
+            times.append(dt)
+    # reversibility: evolving back by -t returns v (a property that holds at any size)
+    bre, bim, _ = hub.hubbard_time_evolve(H, ore, oim, -t, krylov_max=krylov_max, tol=tol, workspace=ws)
+    back = float(torch.sqrt(torch.sum((bre - v) ** 2) + torch.sum(bim ** 2)))
+    del ws, ore, oim, bre, bim
+    torch.cuda.empty_cache()
+    ms = 1e3 * float(np.median(times))
+    return dict(workload="sq4x4_n8_8_U8 exp(-iHt) v, |v| = 1", t=t, krylov_max=krylov_max, tol=tol,
+                basis="stored in the workspace", ms=ms, steps=info["steps"], hv=info["hv"],
+                krylov_dim=info["krylov_dim"], ms_per_hv=ms / max(1, info["hv"]),
+                err_estimate=info["err_estimate"], norm_drift=abs(info["norm"] - 1.0), return_error=back,
+                includes="Lanczos steps with the stop test, the tridiagonal QR, the one-pass combination")
 
 
 def bench_ring18(hub, torch, dev, U, cpu=True):
@@ -731,6 +762,7 @@ def main():
     ap.add_argument("--serve", type=int, default=2000, help="requests in the serving trace (0: skip)")
     ap.add_argument("--serve-lanes", type=int, default=8, help="big lanes of the server")
     ap.add_argument("--ring18", type=int, default=1, help="also time config 3, the 18-site ring (0: skip)")
+    ap.add_argument("--evolve", type=int, default=1, help="also time exp(-iHt) v on the bench sector (0: skip)")
     ap.add_argument("--ring18-U", type=float, default=4.0, choices=[2.0, 4.0, 8.0])
     args = ap.parse_args()
     if args.impl == "reference":
