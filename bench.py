@@ -290,7 +290,8 @@ def run_ours(args):
     if args.workload == "sq4x4_n8_8_U8_f64":
         extra["hv_sq4x4_f32"] = bench_hv_f32(hub, torch, H, v_host, args.steps, args.warmup)
         if args.evolve:
-            extra["time_evolve"] = bench_evolve(hub, torch, dev, H, v)
+            extra["time_evolve"] = bench_evolve(hub, torch, dev, H, v,
+                                                cpu=(rank == 0 and ws == 1 and not args.no_cpu_baseline))
     H.close()
     del v, w, v_pin
     torch.cuda.empty_cache()
@@ -400,7 +401,7 @@ def bench_hv_f32(hub, torch, H, v_host, steps, warmup):
     return out
 
 
-def bench_evolve(hub, torch, dev, H, v, t=0.05, krylov_max=30, tol=1e-10, reps=3):
+def bench_evolve(hub, torch, dev, H, v, t=0.05, krylov_max=30, tol=1e-10, reps=3, cpu=True):
     """Time propagation exp(-iHt) v of the normalised start vector on the
     bench sector (binary64, Lanczos vectors stored in the workspace), timed
     whole (the call synchronises); one untimed warm-up call."""
@@ -422,11 +423,46 @@ def bench_evolve(hub, torch, dev, H, v, t=0.05, krylov_max=30, tol=1e-10, reps=3
     del ws, ore, oim, bre, bim
     torch.cuda.empty_cache()
     ms = 1e3 * float(np.median(times))
-    return dict(workload="sq4x4_n8_8_U8 exp(-iHt) v, |v| = 1", t=t, krylov_max=krylov_max, tol=tol,
-                basis="stored in the workspace", ms=ms, steps=info["steps"], hv=info["hv"],
-                krylov_dim=info["krylov_dim"], ms_per_hv=ms / max(1, info["hv"]),
-                err_estimate=info["err_estimate"], norm_drift=abs(info["norm"] - 1.0), return_error=back,
-                includes="Lanczos steps with the stop test, the tridiagonal QR, the one-pass combination")
+    out = dict(workload="sq4x4_n8_8_U8 exp(-iHt) v, |v| = 1", t=t, krylov_max=krylov_max, tol=tol,
+               basis="stored in the workspace", ms=ms, steps=info["steps"], hv=info["hv"],
+               krylov_dim=info["krylov_dim"], ms_per_hv=ms / max(1, info["hv"]),
+               err_estimate=info["err_estimate"], norm_drift=abs(info["norm"] - 1.0), return_error=back,
+               includes="Lanczos steps with the stop test, the tridiagonal QR, the one-pass combination")
+    if cpu:
+        out["oracle_side_by_side"] = evolve_vs_oracle(hub, torch, dev)
+    return out
+
+
+def evolve_vs_oracle(hub, torch, dev, t=0.25):
+    """The oracle's propagation (expm_multiply on the explicit sparse H, host
+    cores) beside the GPU on the ring 12 (5,5) U = 4 sector (6.3e5 elements,
+    complex start), with their largest difference."""
+    from oracle import propagate as pr
+    from oracle.basis import Sector
+    from workload import lattice_by_name, start_vector
+    ns, bonds = lattice_by_name("ring12")
+    H = hub.hubbard_sector_create(ns, bonds, 5, 5, 1.0, 4.0)
+    vr = torch.from_numpy(start_vector(H.D, seed=21)).to(dev)
+    vi = torch.from_numpy(start_vector(H.D, seed=1021)).to(dev)
+    times = []
+    for k in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ore, oim, info = hub.hubbard_time_evolve(H, vr, vi, t, krylov_max=40, tol=1e-10)
+        if k > 0:
+            times.append(time.perf_counter() - t0)
+    got = ore.cpu().numpy() + 1j * oim.cpu().numpy()
+    S = Sector(ns, bonds, 5, 5, 1.0, 4.0)
+    v = vr.cpu().numpy() + 1j * vi.cpu().numpy()
+    t0 = time.perf_counter()
+    want = pr.evolve_sparse(S, v, t)
+    cpu_s = time.perf_counter() - t0
+    H.close()
+    return dict(workload="ring12_n5_5_U4 exp(-iHt) v, complex v, t = 0.25, tol 1e-10", dim=S.D,
+                gpu_ms=1e3 * float(np.median(times)), gpu_hv=info["hv"],
+                oracle_s=cpu_s, oracle="oracle.propagate.evolve_sparse: explicit sparse H built, then scipy "
+                "expm_multiply (host cores; both timed)", max_abs_diff=float(np.abs(got - want).max()),
+                norm_v=float(np.linalg.norm(v)))
 
 
 def bench_ring18(hub, torch, dev, U, cpu=True):
