@@ -378,10 +378,38 @@ __global__ void k_psi_acc_f64(const double* __restrict__ f, double* __restrict__
 
 // psi = sum_j s_j f_j over m stored binary32 vectors f_j = base + j * stride,
 // accumulated per element in j order with the same operations as successive
-// k_psi_acc launches (so the result is bit-identical to that sequence)
+// k_psi_acc launches (so the result is bit-identical to that sequence).  Two
+// elements per thread and eight vectors' loads issued before their
+// multiply-adds (the loop is bound by the latency of m scattered streams);
+// base and stride must keep f_j 8-byte aligned, psi 16-byte aligned.
 __global__ void k_psi_multi(const float* __restrict__ base, int64_t stride, int m, const double* __restrict__ s,
                             double* __restrict__ psi, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int U = 8;
+    const int64_t n2 = n / 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const float* p = base + 2 * i;
+        const float2 x0 = *reinterpret_cast<const float2*>(p);
+        double ax = s[0] * (double)x0.x, ay = s[0] * (double)x0.y;
+        int j = 1;
+        for (; j + U <= m; j += U) {
+            float2 x[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) x[q] = __ldcs(reinterpret_cast<const float2*>(p + (int64_t)(j + q) * stride));
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                ax = fma(s[j + q], (double)x[q].x, ax);
+                ay = fma(s[j + q], (double)x[q].y, ay);
+            }
+        }
+        for (; j < m; ++j) {
+            const float2 x = __ldcs(reinterpret_cast<const float2*>(p + (int64_t)j * stride));
+            ax = fma(s[j], (double)x.x, ax);
+            ay = fma(s[j], (double)x.y, ay);
+        }
+        reinterpret_cast<double2*>(psi)[i] = make_double2(ax, ay);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t i = n - 1;
         double acc = s[0] * (double)base[i];
         for (int j = 1; j < m; ++j) acc = fma(s[j], (double)__ldcs(base + (int64_t)j * stride + i), acc);
         psi[i] = acc;
@@ -401,10 +429,43 @@ __global__ void k_acc2_f64(const double* __restrict__ f, double* __restrict__ A,
 
 // A <- A + sum_j c[j] f_j, B <- B + sum_j c[m + j] f_j over m stored binary64
 // vectors f_j = base + j * stride, per element in j order with the operations
-// of m successive k_acc2_f64 launches (so the result is bit-identical to them)
+// of m successive k_acc2_f64 launches (so the result is bit-identical to them).
+// Two elements per thread, four vectors' loads issued before their
+// multiply-adds; base, stride, A and B must keep 16-byte alignment.
 __global__ void k_combine2_f64(const double* __restrict__ base, int64_t stride, int m, const double* __restrict__ c,
                                double* __restrict__ A, double* __restrict__ B, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    constexpr int U = 4;
+    const int64_t n2 = n / 2;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n2; i += (int64_t)gridDim.x * blockDim.x) {
+        const double* p = base + 2 * i;
+        double2 a = reinterpret_cast<const double2*>(A)[i];
+        double2 b = reinterpret_cast<const double2*>(B)[i];
+        int j = 0;
+        for (; j + U <= m; j += U) {
+            double2 x[U];
+#pragma unroll
+            for (int q = 0; q < U; ++q) x[q] = __ldcs(reinterpret_cast<const double2*>(p + (int64_t)(j + q) * stride));
+#pragma unroll
+            for (int q = 0; q < U; ++q) {
+                const double ca = c[j + q], cb = c[m + j + q];
+                a.x = fma(ca, x[q].x, a.x);
+                a.y = fma(ca, x[q].y, a.y);
+                b.x = fma(cb, x[q].x, b.x);
+                b.y = fma(cb, x[q].y, b.y);
+            }
+        }
+        for (; j < m; ++j) {
+            const double2 x = __ldcs(reinterpret_cast<const double2*>(p + (int64_t)j * stride));
+            a.x = fma(c[j], x.x, a.x);
+            a.y = fma(c[j], x.y, a.y);
+            b.x = fma(c[m + j], x.x, b.x);
+            b.y = fma(c[m + j], x.y, b.y);
+        }
+        reinterpret_cast<double2*>(A)[i] = a;
+        reinterpret_cast<double2*>(B)[i] = b;
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+        const int64_t i = n - 1;
         double a = A[i], b = B[i];
         for (int j = 0; j < m; ++j) {
             const double x = __ldcs(base + (int64_t)j * stride + i);
