@@ -1611,7 +1611,9 @@ int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double 
             }
             tau = lo;
         }
-        if (!(tau > 1e-12 * tabs)) return fail(HUB_ENOTCONV, "time evolution: tol too strict for krylov_max");
+        // a step shorter than 1e-12 |t| (unless it ends the propagation) means tol cannot be met
+        if (!(tau >= std::min(rem, 1e-12 * tabs)) || !(tau > 0.0))
+            return fail(HUB_ENOTCONV, "time evolution: tol too strict for krylov_max");
         if (tau > rem) tau = rem;
         // psi(tau) = sum over parts of i^q nu_q sum_j y_j f_j into (A, B)
         if (cudaMemsetAsync(A, 0, vbytes, s) != cudaSuccess || cudaMemsetAsync(B, 0, vbytes, s) != cudaSuccess)
