@@ -423,11 +423,21 @@ def bench_evolve(hub, torch, dev, H, v, t=0.05, krylov_max=30, tol=1e-10, reps=3
     del ws, ore, oim, bre, bim
     torch.cuda.empty_cache()
     ms = 1e3 * float(np.median(times))
+    # algorithmic bytes: each Lanczos step 3 D s (read f_j, read and write the
+    # other vector), the combining pass m + 4 vectors (m stored, both parts
+    # read and written; m = krylov_dim, exact for the one-step, one-part call
+    # timed here); the copies into the stored basis are not counted
+    D8 = H.D * 8
+    alg = info["hv"] * 3 * D8 + (info["krylov_dim"] + 4) * D8 * info["steps"]
+    peak, src = peaks()
     out = dict(workload="sq4x4_n8_8_U8 exp(-iHt) v, |v| = 1", t=t, krylov_max=krylov_max, tol=tol,
                basis="stored in the workspace", ms=ms, steps=info["steps"], hv=info["hv"],
                krylov_dim=info["krylov_dim"], ms_per_hv=ms / max(1, info["hv"]),
                err_estimate=info["err_estimate"], norm_drift=abs(info["norm"] - 1.0), return_error=back,
-               includes="Lanczos steps with the stop test, the tridiagonal QR, the one-pass combination")
+               includes="Lanczos steps with the stop test, the tridiagonal QR, the one-pass combination",
+               roofline={"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": src,
+                         "algorithmic_bytes_per_call": alg})
     if cpu:
         out["oracle_side_by_side"] = evolve_vs_oracle(hub, torch, dev)
     return out
