@@ -864,14 +864,18 @@ int hubbard_vec_axpy(double a, const void* x, void* y, int64_t n, int dtype, voi
 // upd (may be null): the previous step's pending update, applied to f first.
 static int lanczos_step_impl(hubbard_t H, const void* f, void* g, double beta_j, int dtype, cudaStream_t s,
                              double* alpha, double* beta_next, bool normalise, int fixed_emax,
-                             bool* pending = nullptr, const RowUpdate* upd = nullptr) {
+                             bool* pending = nullptr, const RowUpdate* upd = nullptr,
+                             const void* w_old = nullptr) {
     int rc;
     if (dtype == HUB_F64 && !fixed_point_ok(H))
         return fail(HUB_EINVAL, "lanczos step: more than 127 hops per state is not supported");
     bool fused = false;
     // g <- H f - beta_j g  (Eqs. split1), fused into the H*v kernels with the
-    // reductions; upd: f itself is first completed by the previous step's update
-    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, g, fixed_emax, s, H->red, &fused, upd))) return rc;
+    // reductions; upd: f itself is first completed by the previous step's update.
+    // w_old != nullptr: g <- H f - beta_j w_old (the same operations per element)
+    if ((rc = launch_hv_fast(H, f, g, dtype, beta_j, w_old != nullptr ? w_old : g, fixed_emax, s, H->red, &fused,
+                             upd)))
+        return rc;
     double a = 0.0, b2 = 0.0;
     bool pend = false;
     if (fused) {
@@ -1007,14 +1011,24 @@ static bool lanczos_record_step(LanczosRun& R, double aj, double bn, double tol,
 // Chunks are longer for small sectors (where a round trip costs more than a
 // step); sectors of more than 2.7e6 elements (one step per chunk) and those
 // whose H*v kernels do not fuse the reductions take the host-driven loop.
+// steps per chunk of the device-resident loop: about 4e6 / D (a round trip is
+// worth a few steps of a small sector)
+static int lanczos_chunk(hubbard_t H) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(4e6 / (double)H->D)));
+}
+
+// whether lanczos_core takes the host-driven loop: one step per round trip
+// gains nothing over it (its explicit branch costs no launches when unused;
+// same results either way), and it needs fused reductions and the scratch
+static bool lanczos_host_driven(hubbard_t H, int dtype) {
+    return lanczos_chunk(H) == 1 || !hv_phases_fuse(H, dtype) || H->fx_bytes < (size_t)H->D * 16;
+}
+
 static int lanczos_core(hubbard_t H, const void* v0, int v0_dtype, int max_iters, double tol, int dtype, void* f,
                         void* g, cudaStream_t s, LanczosRun& R, double rel_tol = 0.0, char* store = nullptr,
                         size_t store_stride = 0, int store_cap = 0, const LanczosStop* stop = nullptr) {
-    // steps per chunk: about 4e6 / D (a round trip is worth a few steps of a small sector)
-    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(16, (int64_t)(4e6 / (double)H->D)));
-    // one step per round trip gains nothing over the host-driven loop, whose
-    // explicit branch costs no launches when unused (same results either way)
-    if (chunk == 1 || !hv_phases_fuse(H, dtype) || H->fx_bytes < (size_t)H->D * 16)
+    const int chunk = lanczos_chunk(H);
+    if (lanczos_host_driven(H, dtype))
         return lanczos_core_host(H, v0, v0_dtype, max_iters, tol, dtype, f, g, s, R, rel_tol, store, store_stride,
                                  store_cap, stop);
     int rc;
@@ -1442,6 +1456,52 @@ int lanczos_ground_state_refined(hubbard_t H, const void* v0, int max_iters, dou
 
 // ---- time propagation (Sec. 6: the other use of H*v; short iterative Lanczos) ----
 
+// Algorithm 1 (binary64, host-driven) with the Lanczos vectors kept in the
+// stored basis itself: f_j is slot j (store + j * stride bytes) from the
+// start, step j writes H f_j - b_j f_{j-1} into slot j+1 (into spare past the
+// last slot) and reads f_{j-1} from slot j-1, and the next step's row phase
+// completes that slot into f_{j+1} in place, so no vector is copied.  The
+// kernels and their operands are those of lanczos_core_host (per element the
+// same operations whether or not w_old is the output vector), hence the same
+// a_j, b_{j+1} and f_j bit for bit.  At most `slots` steps.
+static int lanczos_core_in_store(hubbard_t H, const void* v0, int slots, char* store, size_t stride, void* spare,
+                                 cudaStream_t s, LanczosRun& R, const LanczosStop* stop) {
+    int rc;
+    double n0 = 0.0;
+    if ((rc = launch_dot(H, v0, v0, H->D, HUB_F64, H->red, s)) || (rc = reduce_partials_host(H->red, s, &n0))) return rc;
+    n0 = std::sqrt(n0);
+    if (!(n0 > 0.0) || !std::isfinite(n0)) return fail(HUB_EINVAL, "start vector has zero or non-finite norm");
+    auto slot = [&](int j) -> void* { return j < slots ? (void*)(store + (size_t)j * stride) : spare; };
+    if ((rc = launch_copy_normalise(v0, slot(0), H->D, HUB_F64, 1.0 / n0, s))) return rc;
+    if (cudaMemsetAsync(slot(1), 0, (size_t)H->D * 8, s) != cudaSuccess) return fail(HUB_ECUDA, "memset");
+    const int m_cap = (int)std::min<int64_t>(slots, H->D);
+    double bj = 0.0;
+    RowUpdate upd{};
+    bool have_upd = false;
+    for (int j = 0; j < m_cap; ++j) {
+        void* f = slot(j);
+        void* w = slot(j + 1);
+        const void* w_old = j == 0 ? w : slot(j - 1);
+        double aj = 0.0, bn = 0.0;
+        bool pending = false;
+        if ((rc = lanczos_step_impl(H, f, w, bj, HUB_F64, s, &aj, &bn, false, 1023, &pending,
+                                    have_upd ? &upd : nullptr, w_old)))
+            return rc;
+        have_upd = false;
+        if (lanczos_record_step(R, aj, bn, 0.0, 0.0, stop)) break;
+        if (pending) {
+            upd = RowUpdate{f, -aj, 1.0 / bn};
+            have_upd = true;
+        } else if ((rc = launch_scale(1.0 / bn, w, H->D, HUB_F64, s))) {
+            return rc;
+        }
+        bj = bn;
+    }
+    R.converged = true;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(HUB_ECUDA, "lanczos synchronise");
+    return HUB_OK;
+}
+
 // A <- A + sum_j ca_j f_j, B <- B + sum_j cb_j f_j over the Lanczos vectors of a
 // finished lanczos_core run from p, by replaying its recurrence as
 // replay_ritz_vector does (same kernels and operands, hence the same f_j bit
@@ -1525,6 +1585,8 @@ int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double 
     double* part[2] = {(double*)(ws + 4 * vec), (double*)(ws + 5 * vec)};   // state: real, imaginary part
     char* store = ws + 6 * vec;
     const bool stored = ws_bytes >= hubbard_evolve_workspace_bytes(H, krylov_max, 1);
+    // large sectors (host-driven steps): the recurrence runs in the stored basis, no copies
+    const bool in_store = stored && lanczos_host_driven(H, HUB_F64);
     double* A = (double*)out_re;
     double* B = (double*)out_im;
 
@@ -1587,9 +1649,10 @@ int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double 
                 return run.nu * Rr.b.back() * krylov_last_coeff(E, sgn * target) <= share * target;
             };
             char* st = stored ? store + (size_t)q * kmax * vec : nullptr;
-            if ((rc = lanczos_core(H, part[q], HUB_F64, kmax, 0.0, HUB_F64, f, g, s, run.R, 0.0, st, vec,
-                                   stored ? kmax : 0, &stop)))
-                return rc;
+            if (in_store) rc = lanczos_core_in_store(H, part[q], kmax, st, vec, g, s, run.R, &stop);
+            else rc = lanczos_core(H, part[q], HUB_F64, kmax, 0.0, HUB_F64, f, g, s, run.R, 0.0, st, vec,
+                                   stored ? kmax : 0, &stop);
+            if (rc) return rc;
             const int m = (int)run.R.a.size();
             if (!krylov_exp_ends(run.R.a.data(), run.R.b.data(), m, run.E))
                 return fail(HUB_ENOTCONV, "time evolution: tridiagonal QR did not converge");

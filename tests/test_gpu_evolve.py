@@ -137,6 +137,33 @@ def test_full_size_sq4x4_invariants(dev):
     H.close()
 
 
+def test_large_sector_stored_basis_equals_replay(dev):
+    """Ring 14 (6,7), 1.0e7 elements: large enough for the host-driven steps,
+    where the recurrence runs inside the stored basis (no copies); it equals
+    the replayed route bit for bit, conserves the norm and the energy (oracle
+    Kronecker-sum H*v), and a second, complex step goes through both parts."""
+    from oracle.kron import KronHamiltonian
+    ns, bonds = lattice_by_name("ring14")
+    H = hub.hubbard_sector_create(ns, bonds, 6, 7, 1.0, 5.0)
+    assert H.D > 4_000_000
+    v = torch.from_numpy(start_vector(H.D, seed=8)).to(dev)
+    v /= torch.linalg.vector_norm(v)
+    outs = []
+    for store in (True, False):
+        ore, oim, info = hub.hubbard_time_evolve(H, v, None, 0.3, krylov_max=24, tol=TOL, store_basis=store)
+        outs.append((ore.clone(), oim.clone(), info))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
+    ore, oim, info = outs[0]
+    assert info["steps"] >= 2 and abs(info["norm"] - 1.0) <= 1e-9, info
+    K = KronHamiltonian(ns, bonds, 6, 7, 1.0, 5.0)
+    vh = v.cpu().numpy()
+    e0 = float(np.dot(vh, K.hv(vh)))
+    a, b = ore.cpu().numpy(), oim.cpu().numpy()
+    e1 = float(np.dot(a, K.hv(a)) + np.dot(b, K.hv(b)))
+    assert abs(e1 - e0) <= 1e-8 * max(1.0, abs(e0)), (e0, e1, info)
+    H.close()
+
+
 def test_ground_state_only_gains_its_phase(dev):
     """The Ritz vector of lanczos_ground_state on ring 12 (5,6) evolves as
     exp(-i E0 t) psi0 up to its residual times t."""
