@@ -152,3 +152,37 @@ def test_host_krylov_exp_refuses_bad_input():
                                        y.ctypes.data) == hub.HUB_EINVAL
     bad = np.array([1.0, float("inf"), 1.0, 1.0])
     assert lib.hubbard_host_krylov_exp(bad.ctypes.data, a.ctypes.data, 4, 1.0, y.ctypes.data, y.ctypes.data) == hub.HUB_EINVAL
+
+
+def test_host_krylov_coefficients_propagate_a_lanczos_basis():
+    """The library's host coefficients y = exp(-i T_m tau) e_1 applied to a
+    Lanczos basis of the oracle's explicit H (the plain recurrence of
+    Algorithm 1, written out here in numpy) reproduce exp(-iH tau) v of the
+    oracle's eigendecomposition, and Saad's estimate b_{m+1} |y_{m-1}| is of
+    the size of the actual error (the step-size rule of the propagator)."""
+    import numpy as np
+    from oracle import propagate as pr
+    from oracle.basis import Sector
+    from workload import lattice_by_name, start_vector
+    ns, bonds = lattice_by_name("ring8")
+    S = Sector(ns, bonds, 4, 4, 1.0, 4.0)
+    Hx = S.explicit()
+    v = start_vector(S.D, seed=5)
+    v /= np.linalg.norm(v)
+    F, a, b = [], [], []
+    f, g, beta = v.copy(), np.zeros_like(v), 0.0
+    for _ in range(30):
+        w = Hx @ f - beta * g
+        al = float(w @ f)
+        w -= al * f
+        be = float(np.linalg.norm(w))
+        F.append(f)
+        a.append(al)
+        b.append(be)
+        g, f, beta = f, w / be, be
+    V = np.array(F).T
+    for tau in (0.2, 0.6, -0.45):
+        y = hub.hubbard_host_krylov_exp(np.array(a), np.array(b[:-1]), tau)
+        err = np.abs(V @ y - pr.evolve_dense(S, v, tau)).max()
+        est = b[-1] * abs(y[-1])
+        assert err <= 1e-8 and err <= 10 * est + 1e-13, (tau, err, est)
