@@ -15,7 +15,7 @@ writes out the definition of the exact result:
                  explicit sparse H, for sectors too large for a dense
                  eigendecomposition.
 
-Independent routes that pin them (tests/test_oracle_pins.py):
+Independent routes that pin them (tests/test_oracle_propagate.py):
 
   evolve_taylor            the exponential series sum_k (-i tau H)^k v / k!
                            summed term by term until the terms vanish, in
@@ -27,7 +27,13 @@ Independent routes that pin them (tests/test_oracle_pins.py):
                            whose plane-wave closed form is written out;
   dimer_evolution          two sites, one bond, N = (1, 1): the four-state
                            problem in closed form (cos / sin of the
-                           singlet frequency).
+                           singlet frequency);
+  slater_evolution         U = 0 with several electrons per spin: a product
+                           of Slater determinants stays one, its orbitals
+                           propagated by the one-body exp(-i h t); the
+                           amplitude of a basis state is the product of the
+                           two determinants of its occupied rows (creators
+                           in ascending site order, up before down).
 """
 import math
 
@@ -139,3 +145,29 @@ def dimer_evolution(t_hop, U, v, time):
 def dimer_sector(t_hop, U):
     """The sector dimer_evolution describes, as an oracle Sector."""
     return Sector(2, [(0, 1)], 1, 1, t_hop, U)
+
+
+def slater_state(ns, nup, ndn, phi_up, phi_dn):
+    """The sector vector of the Slater determinant product with orbitals
+    phi_up (ns x nup) and phi_dn (ns x ndn): amplitude of (up word, down word)
+    = det(phi_up[up sites, :]) * det(phi_dn[down sites, :]), sites ascending."""
+    from oracle.basis import spin_states
+    ups, dns = spin_states(ns, nup), spin_states(ns, ndn)
+
+    def dets(words, phi, n):
+        out = np.empty(len(words), dtype=np.complex128)
+        for k, wd in enumerate(words):
+            rows = [i for i in range(ns) if (int(wd) >> i) & 1]
+            out[k] = np.linalg.det(phi[rows, :]) if n > 0 else 1.0
+        return out
+
+    return np.outer(dets(ups, phi_up, nup), dets(dns, phi_dn, ndn)).reshape(-1)
+
+
+def slater_evolution(ns, bonds, t_hop, nup, ndn, phi_up, phi_dn, time):
+    """U = 0: exp(-iHt) of slater_state(phi_up, phi_dn) is slater_state of the
+    orbitals exp(-i h t) phi (h the one-body hopping matrix of the bonds)."""
+    from oracle.closed_forms import hopping_matrix
+    e, u = np.linalg.eigh(hopping_matrix(ns, bonds, t_hop))
+    P = (u * np.exp(-1j * e * time)) @ u.T
+    return slater_state(ns, nup, ndn, P @ phi_up, P @ phi_dn)

@@ -51,6 +51,22 @@ def test_sparse_route_matches_dense(name, nup, ndn, U, time):
     assert np.abs(got - pr.evolve_dense(S, v, time)).max() <= 1e-11 * np.linalg.norm(v)
 
 
+@pytest.mark.parametrize("name,nup,ndn,time", [("ring6", 3, 2, 0.9), ("sq2x3", 2, 3, -1.4), ("ring7", 3, 3, 2.1),
+                                              ("sq3x3", 2, 2, 0.6)])
+def test_dense_matches_slater_determinants_at_u0(name, nup, ndn, time):
+    """U = 0 with several electrons of a spin: the Jordan-Wigner signs of the
+    many-body propagation against determinants of propagated orbitals."""
+    ns, bonds = lattice_by_name(name)
+    rng = np.random.default_rng(7)
+    phi_up = rng.normal(size=(ns, nup)) + 1j * rng.normal(size=(ns, nup))
+    phi_dn = rng.normal(size=(ns, ndn)) + 1j * rng.normal(size=(ns, ndn))
+    S = Sector(ns, bonds, nup, ndn, 1.0, 0.0)
+    v = pr.slater_state(ns, nup, ndn, phi_up, phi_dn)
+    want = pr.slater_evolution(ns, bonds, 1.0, nup, ndn, phi_up, phi_dn, time)
+    got = pr.evolve_dense(S, v, time)
+    assert np.abs(got - want).max() <= 1e-11 * np.linalg.norm(v)
+
+
 def test_invariants_of_the_propagator():
     """Unitarity, energy conservation, the group property, time reversal and
     (real H, real v) psi(-t) = conj(psi(t)); an eigenvector only gains its phase."""
@@ -123,3 +139,9 @@ def test_planted_bosonic_sign_is_caught(monkeypatch):
     monkeypatch.setattr(Sector, "_hop", bosonic)
     got = pr.evolve_dense(Sector(ns, bonds, 2, 1, 1.0, 3.0), v, 0.9)
     assert np.abs(got - want).max() > 1e-3
+    # and the determinant pin fails for it at U = 0
+    rng = np.random.default_rng(7)
+    phi_up, phi_dn = rng.normal(size=(ns, 2)), rng.normal(size=(ns, 1))
+    vs = pr.slater_state(ns, 2, 1, phi_up, phi_dn)
+    bos = pr.evolve_dense(Sector(ns, bonds, 2, 1, 1.0, 0.0), vs, 0.9)
+    assert np.abs(bos - pr.slater_evolution(ns, bonds, 1.0, 2, 1, phi_up, phi_dn, 0.9)).max() > 1e-3
