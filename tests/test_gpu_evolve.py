@@ -137,6 +137,28 @@ def test_full_size_sq4x4_invariants(dev):
     H.close()
 
 
+def test_u0_slater_state_full_size_sq4x4(dev):
+    """U = 0 on the 4x4 (8,8) sector (1.66e8 elements): a product of Slater
+    determinants of orthonormal orbitals propagates as the determinants of its
+    orbitals under the one-body exp(-iht) (the oracle's closed form); every
+    element is compared."""
+    ns, bonds = lattice_by_name("sq4x4")
+    rng = np.random.default_rng(3)
+    pu = np.linalg.qr(rng.normal(size=(ns, 8)))[0]
+    pd = np.linalg.qr(rng.normal(size=(ns, 8)))[0]
+    v = pr.slater_state(ns, 8, 8, pu, pd).real.copy()
+    H = hub.hubbard_sector_create(ns, bonds, 8, 8, 1.0, 0.0)
+    vd = torch.from_numpy(v).to(dev)
+    del v
+    ws = torch.empty(hub.hubbard_evolve_workspace_bytes(H, 30, store_basis=False), dtype=torch.uint8, device=dev)
+    ore, oim, info = hub.hubbard_time_evolve(H, vd, None, 0.05, krylov_max=30, tol=TOL, workspace=ws,
+                                             store_basis=False)
+    want = pr.slater_evolution(ns, bonds, 1.0, 8, 8, pu, pd, 0.05)
+    err = max(np.abs(ore.cpu().numpy() - want.real).max(), np.abs(oim.cpu().numpy() - want.imag).max())
+    assert err <= 10 * TOL + 1e-12, (err, info)
+    H.close()
+
+
 def test_large_sector_stored_basis_equals_replay(dev):
     """Ring 14 (6,7), 1.0e7 elements: large enough for the host-driven steps,
     where the recurrence runs inside the stored basis (no copies); it equals
