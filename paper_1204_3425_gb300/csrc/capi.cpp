@@ -1549,10 +1549,10 @@ int hubbard_time_evolve(hubbard_t H, const void* v_re, const void* v_im, double 
                         hubbard_evolve_info* info) {
     clear_error();
     int rc;
-    if ((rc = check_handle(H))) return rc;
     if (info == nullptr) return fail(HUB_EINVAL, "info is null");
     std::memset(info, 0, sizeof(*info));
     info->status = HUB_EINVAL;
+    if ((rc = check_handle(H))) return rc;
     if (v_re == nullptr || !aligned16(v_re) || (v_im != nullptr && !aligned16(v_im)))
         return fail(HUB_EINVAL, "v_re null, or v_re / v_im not 16-byte aligned");
     if (out_re == nullptr || out_im == nullptr || !aligned16(out_re) || !aligned16(out_im))

@@ -91,8 +91,10 @@ def test_time_evolve_checks_before_the_library():
                                 workspace=torch.zeros(16, dtype=torch.uint8))
     lib = hub.load_library()
     info = hub.EvolveInfo()
+    info.steps, info.norm = 7, 3.0
     assert lib.hubbard_time_evolve(None, None, None, 0.5, 10, 1e-10, None, 0, None, None, None,
                                    ctypes.byref(info)) == hub.HUB_EINVAL
+    assert info.status == hub.HUB_EINVAL and info.steps == 0 and info.norm == 0.0
     assert lib.hubbard_evolve_workspace_bytes(None, 10, 1) == 0
 
 
